@@ -1,0 +1,361 @@
+"""Benchmark of the backward ray-shooting hot path (direct-sum deflection, Eq. 3;
+beta = theta - alpha, Eq. 2; binning into a uint32 source map, Algorithm 1) on GB300.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+                  [--workload paper|tiny|precision] [--precision fp32|fp32_naive|fp64]
+
+One step = one whole magnification map of the workload (every ray of the grid against
+every star, binned).  Default workload: 10^4 power-law stars (kappa_*=0.3,
+kappa_c=0.2, gamma=(0.3,0)), 8192^2 rays over the 1.5x lens box, 1024^2 map.
+
+Prints ONE JSON line (rank 0).  `value` = ray-star interactions per second over the
+timed steps (device time, CUDA events on the launch stream, max over ranks);
+`e2e` = the same metric through the public C ABI from host buffers (star upload,
+shoot, map download, context teardown inside the timed region).
+`--impl reference` times the FP64 CPU oracle (the reference arm of this build) on a
+bounded ray sample of the same workload.
+
+Under torchrun (N > 1) every rank shoots its own independent field of the same size
+(weak scaling, no data-path collective; the process group only carries the barrier
+and the max-over-ranks timing).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "ray-star interactions/s (direct-sum deflection + binning, one map per step)"
+N_SM_GB300 = 152
+MUFU_RCP_PER_SM_CLK = 16  # MUFU.RCP issue rate per SM per clock (one reciprocal per interaction)
+SM_MAX_MHZ = 2070.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", default="paper", choices=["paper", "tiny", "precision"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_naive", "fp64"])
+    ap.add_argument("--rays-per-thread", type=int, default=8, choices=[4, 8])
+    ap.add_argument("--rays-scale", type=float, default=1.0,
+                    help="shrink the ray grid per axis (same field, boxes and map) for profiling runs")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+def workload_config(name, wl, precision, note_l2):
+    f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
+    return {
+        "workload": f"{name}: {f.n} stars, {rays.nx}x{rays.ny} rays, {src.nx}x{src.ny} map",
+        "stars": f.n, "rays": [rays.nx, rays.ny], "map": [src.nx, src.ny],
+        "ray_box": [rays.x0, rays.x1, rays.y0, rays.y1], "src_box": [src.x0, src.x1, src.y0, src.y1],
+        "kappa_star": f.kappa_star, "kappa_c": f.kappa_c, "gamma": [f.gamma1, f.gamma2],
+        "precision": precision, "l2": note_l2,
+    }
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- profiles
+def profile_traffic(kernel_key: str, src_file: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        ent = d[kernel_key]
+        h = hashlib.sha256(open(src_file, "rb").read()).hexdigest()[:16]
+        if ent.get("source_sha256_16") != h:
+            return None, ent
+        return float(ent["dram_bytes_per_launch"]), ent
+    except (OSError, KeyError, ValueError):
+        return None, None
+
+
+# ------------------------------------------------------------ cpu baseline
+def cpu_oracle_rate(field, rays, target_s: float, seed: int = 11):
+    """Time the FP64 oracle (as it stands, all host cores) on a random ray sample
+    sized for about target_s seconds; returns (interactions/s, cores, sample note)."""
+    import oracle
+    oracle.build()
+    cores = oracle.max_threads()
+    n = max(field.n, 1)
+    probe = W.ray_sample(rays, 2000, seed)
+    t0 = time.perf_counter()
+    oracle.beta_rays(rays, probe, field)
+    dt = max(time.perf_counter() - t0, 1e-4)
+    k = int(min(rays.n, max(2000, 2000 * target_s / dt)))
+    idx = W.ray_sample(rays, k, seed + 1)
+    t0 = time.perf_counter()
+    oracle.beta_rays(rays, idx, field)
+    dt = time.perf_counter() - t0
+    return k * n / dt, cores, f"{k} random rays of the grid x all {field.n} stars, FP64, {dt:.1f} s"
+
+
+# ------------------------------------------------------------------- main
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = W.config(args.workload)
+    f, rays = wl.fields[0], wl.rays[0]
+    import oracle
+    oracle.build()
+    cores = oracle.max_threads()
+    n = max(f.n, 1)
+    # per step: a bounded sample of the workload, sized so the whole run stays short
+    per_step_s = max(1.0, min(10.0, 60.0 / max(1, args.steps + args.warmup)))
+    probe = W.ray_sample(rays, 1000, 5)
+    t0 = time.perf_counter()
+    oracle.beta_rays(rays, probe, f)
+    dt = max(time.perf_counter() - t0, 1e-4)
+    k = int(min(rays.n, max(1000, 1000 * per_step_s / dt)))
+    for w in range(args.warmup):
+        oracle.beta_rays(rays, W.ray_sample(rays, max(1000, k // 10), 100 + w), f)
+    times = []
+    for s in range(args.steps):
+        idx = W.ray_sample(rays, k, 1000 + s)
+        t0 = time.perf_counter()
+        oracle.beta_rays(rays, idx, f)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = k * n * args.steps / tot
+    sample = f"{k} random rays x all {f.n} stars per step (FP64 oracle, {cores} threads)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args.workload, wl, "fp64 (CPU oracle)", "n/a (CPU)"),
+        "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_mine(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1703_09707_gb300 import build as B
+    from paper_1703_09707_gb300 import mlens as M
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU path)")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    M.load()
+    prec = M.PRECISIONS[args.precision]
+
+    wl = W.config(args.workload, rays_scale=args.rays_scale)
+    f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
+    if world > 1 and rank > 0:  # an independent field of the same size per rank
+        f = W.random_field(W.SEED_BASE + 100 + rank, f.n, f.kappa_star, f.kappa_c, f.gamma1, f.gamma2)
+    n_inter = rays.n * f.n
+
+    ctx = M.mlens_create(f.xy, f.m, f.kappa_c, f.gamma1, f.gamma2, prec)
+    M.mlens_set_tuning(ctx, args.rays_per_thread)
+    counts = torch.empty(src.n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    st = M.mlens_shoot(ctx, rays, src, counts, stats=True)  # checks the call works; warm the module
+    assert st["rays_binned"] + st["rays_out"] + st["rays_nan"] == rays.n
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        M.mlens_shoot(ctx, rays, src, counts)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))  # > L2 (129 MB) write between steps, outside the events
+        ev[i][0].record(stream)
+        M.mlens_shoot(ctx, rays, src, counts)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([dev_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_s = float(t.item())
+    value = n_inter * args.steps * world / dev_s
+    kernel_ms = statistics.mean(step_ms)
+
+    # ------------------------------------------------ end to end through the C ABI
+    # host star arrays -> mlens_create (upload) -> shoot -> map to host -> destroy
+    host_counts = torch.empty(src.n, dtype=torch.int32, pin_memory=True)
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        c2 = M.mlens_create(f.xy, f.m, f.kappa_c, f.gamma1, f.gamma2, prec)
+        M.mlens_set_tuning(c2, args.rays_per_thread)
+        M.mlens_shoot(c2, rays, src, counts)
+        host_counts.copy_(counts, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        c2.close()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = n_inter * e2e_steps * world / e2e_s
+    n_pad = (f.n + 255) // 256 * 256
+    e2e = {"value": e2e_value, "unit": "interactions/s", "h2d_bytes_per_step": int(16 * n_pad),
+           "d2h_bytes_per_step": int(4 * src.n), "steps": e2e_steps,
+           "note": "mlens_create from host arrays + mlens_shoot + map download + mlens_destroy, wall clock"}
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    # ----------------------------------------------------------------- roofline
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    peak = n_sm * MUFU_RCP_PER_SM_CLK * SM_MAX_MHZ * 1e6
+    achieved = n_inter / (kernel_ms / 1e3)
+    kern_src = os.path.join(ROOT, "paper_1703_09707_gb300", "csrc", "shoot_fp32.cu")
+    key = f"shoot_fp32_{args.workload}_rpt{args.rays_per_thread}"
+    traffic, _ = profile_traffic(key, kern_src) if args.precision != "fp64" else (None, None)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "interactions/s", "frac": achieved / peak,
+            "traffic": traffic,
+            "peak_basis": f"MUFU.RCP {MUFU_RCP_PER_SM_CLK}/SM/clk x {n_sm} SMs x {SM_MAX_MHZ:.0f} MHz (max SM clock)",
+            "kernel": "k_shoot_fp32" if args.precision != "fp64" else "k_fp64",
+            "kernel_ms": kernel_ms}
+    if clk and clk.get("sm_mhz"):
+        roof["frac_at_measured_clock"] = achieved / (n_sm * MUFU_RCP_PER_SM_CLK * clk["sm_mhz"] * 1e6)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64",
+        "data": "synthetic (seeded star field, paper-shaped)",
+        "config": workload_config(args.workload, wl, args.precision,
+                                  f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write, outside the events)"),
+        "maps_per_s": args.steps * world / dev_s,
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "wall_s_timed": t_wall,
+        "device": props.name,
+    }
+    line["config"]["rays_per_thread"] = args.rays_per_thread
+    if not args.no_cpu_baseline and world == 1:
+        v, cores, sample = cpu_oracle_rate(f, rays, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": "interactions/s", "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mine(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,181 @@
+/*
+ * mlens.h -- C ABI of libmlens, a GB300 (sm_103a) backward ray-shooter for
+ * gravitational microlensing by a random star field.
+ *
+ * The method (arXiv:1703.09707, Section 1 and Section 2.2):
+ *   Eq. (3)      alpha(theta) = [[kc+g1, g2], [g2, kc-g1]] theta
+ *                               + sum_i m_i (theta - theta_i) / |theta - theta_i|^2
+ *   Eq. (2)      beta = theta - alpha
+ *   Algorithm 1  for every ray theta_ij of a uniform lens-plane grid: compute
+ *                alpha and beta, convert beta to source-pixel coordinates and
+ *                add one to mag[j_s][i_s] when the pixel is in the window.
+ * Angles are in Einstein radii of a 1 M_sun lens and masses in M_sun (Eq. 4).
+ *
+ * Conventions shared by every entry point
+ *   - Status: 0 (MLENS_OK) on success, a negative MLENS_ERR_* code otherwise;
+ *     mlens_last_error() returns a message for the calling thread's last
+ *     failure.  No C++ exception crosses this boundary.
+ *   - Pointers named *_dev are CUDA device pointers owned by the caller; the
+ *     library never frees them.  Pointers named *_host are ordinary host memory.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     enqueued asynchronously on it; a call returns before the GPU finishes
+ *     unless it says otherwise (any call given a non-NULL stats_host waits for
+ *     the stream, because the counters are read back).
+ *   - Ray grids and source maps are mlens_grid boxes [x0,x1) x [y0,y1) cut into
+ *     nx x ny cells.  Rays sit at cell centres:
+ *         theta_x(i) = x0 + (i + 1/2) (x1 - x0) / nx,  0 <= i < nx (same for y).
+ *     The source pixel of beta is floor((beta_x - x0) * nx / (x1 - x0)) (same
+ *     for y), lower edge inclusive, upper edge exclusive.  Counts are uint32,
+ *     row-major, row = y pixel: counts[j_s * nx + i_s] (mag[j_s, i_s] of
+ *     Algorithm 1).  A ray with a non-finite beta (a ray exactly on a star) is
+ *     not binned and is counted in rays_nan; a finite beta outside the window
+ *     is counted in rays_out.
+ *   - Star coordinates and masses are stored as float32 on the device (the
+ *     double inputs are rounded once); every precision variant, FP64 included,
+ *     works on those rounded values.
+ */
+#ifndef MLENS_H
+#define MLENS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define MLENS_OK               0
+#define MLENS_ERR_ARG         -1  /* invalid argument: NULL pointer, bad size, non-finite value */
+#define MLENS_ERR_CUDA        -2  /* a CUDA runtime call or a launch failed */
+#define MLENS_ERR_NOMEM       -3  /* a device allocation failed */
+#define MLENS_ERR_STATE       -4  /* the call is not valid in the context's current state */
+#define MLENS_ERR_UNSUPPORTED -5  /* no usable sm_103a device, or an option this build lacks */
+
+/* ------------------------------------------------------ precision variants */
+/* FP32 direct sum with star and ray coordinates re-centred on each ray tile,
+ * plain FP32 accumulation inside chunks of 32 stars and Kahan-compensated
+ * addition of the chunk partials; beta carried as an unevaluated float pair
+ * and binned exactly.  The default. */
+#define MLENS_PREC_FP32        0
+/* FP32 with absolute coordinates and one running FP32 sum per component
+ * (the textbook single-precision loop; kept to show its error). */
+#define MLENS_PREC_FP32_NAIVE  1
+/* IEEE FP64 with the operations in the order of Eq. (3) and stars in input
+ * order; its beta and maps equal the FP64 oracle's bit for bit. */
+#define MLENS_PREC_FP64        2
+
+/* ---------------------------------------------------------- shoot flags */
+#define MLENS_ACCUMULATE 1u       /* add into counts_dev instead of overwriting it */
+
+typedef struct mlens_ctx mlens_ctx;
+
+/* Box [x0,x1) x [y0,y1) cut into nx x ny cells (a ray grid or a source map). */
+typedef struct {
+    double x0, x1, y0, y1;
+    int32_t nx, ny;
+} mlens_grid;
+
+/* Ray bookkeeping of one call: rays_total = rays_binned + rays_out + rays_nan. */
+typedef struct {
+    uint64_t rays_total, rays_binned, rays_out, rays_nan;
+} mlens_stats;
+
+/*
+ * mlens_create -- upload one star field and the smooth lens terms of Eq. (1).
+ * Section 2.2: the star field is generated on the host and copied to the
+ * accelerator once.
+ *   out        receives the new context (set to NULL on failure).
+ *   xy_host    n x 2 star positions (x0, y0, x1, y1, ...), finite, |x|,|y| < 1e12.
+ *   m_host     n masses, finite, >= 0.
+ *   n          number of stars, 0 <= n < 2^31 (n = 0 is a pure kappa/gamma sheet).
+ *   kappa_c, gamma1, gamma2   smooth convergence and external shear (finite).
+ *   precision  one of MLENS_PREC_*.
+ * Allocates device memory on the current CUDA device (about 16 bytes per star
+ * plus a few hundred bytes) and synchronises that device.  The context is tied
+ * to that device; use it from one host thread at a time.
+ * Errors: MLENS_ERR_ARG, MLENS_ERR_NOMEM, MLENS_ERR_UNSUPPORTED, MLENS_ERR_CUDA.
+ */
+int mlens_create(mlens_ctx **out, const double *xy_host, const double *m_host, int64_t n,
+                 double kappa_c, double gamma1, double gamma2, int32_t precision);
+
+/* Choose the precision variant used by later calls on this context. */
+int mlens_set_precision(mlens_ctx *ctx, int32_t precision);
+
+/*
+ * mlens_set_tuning -- launch shape of the FP32 kernels for later calls on this
+ * context: rays_per_thread in {4, 8} (tile 64 x 16 or 64 x 32 rays per CTA of
+ * 256 threads).  Different shapes put tile centres in different places, so beta
+ * can differ in its last bits between shapes (never by more than the error bar);
+ * a given shape is deterministic.  Default 8.
+ */
+int mlens_set_tuning(mlens_ctx *ctx, int32_t rays_per_thread);
+
+/*
+ * mlens_shoot -- Algorithm 1 over a whole ray grid: deflect every ray by Eq. (3),
+ * map it to the source plane by Eq. (2) and count it in its source pixel.
+ *   rays       ray grid; 1 <= nx, ny <= 2^20 and nx*ny <= 2^40.
+ *   src        source map; 1 <= nx, ny and nx*ny <= 2^30.
+ *   counts_dev src.ny x src.nx uint32, device, caller-owned, 4-byte aligned.
+ *              Overwritten (zeroed first, on the stream) unless flags has
+ *              MLENS_ACCUMULATE.  Counts do not saturate: a pixel past 2^32-1
+ *              rays wraps (never reached at the ray densities of the paper).
+ *   flags      0 or MLENS_ACCUMULATE.
+ *   stats_host optional; when non-NULL the call waits for the stream and fills it.
+ *   stream     cudaStream_t or NULL.
+ * Errors: MLENS_ERR_ARG (bad grid, NULL counts), MLENS_ERR_CUDA.
+ */
+int mlens_shoot(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid *src, uint32_t *counts_dev,
+                uint32_t flags, mlens_stats *stats_host, void *stream);
+
+/*
+ * mlens_shoot_beta -- mlens_shoot that also writes every ray's source position,
+ * for verification.  beta_dev holds rays.nx*rays.ny records in ray order
+ * (j*nx + i):
+ *   FP32 variants: float4 {x_hi, y_hi, x_lo, y_lo}; beta_x = x_hi + x_lo
+ *                  exactly as a real number (x_lo = 0 for MLENS_PREC_FP32_NAIVE),
+ *                  and the pixel is the exact floor of that real number
+ *                  (to about 1e-14 relative) -- the float32 rule spelled out in
+ *                  the library's documentation of its binning step;
+ *   MLENS_PREC_FP64: double2 {x, y}.
+ * beta_dev must be 16-byte aligned and hold 16 * nx * ny bytes.
+ */
+int mlens_shoot_beta(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid *src, uint32_t *counts_dev,
+                     void *beta_dev, uint32_t flags, mlens_stats *stats_host, void *stream);
+
+/*
+ * mlens_trace -- FP64 deflection at arbitrary image positions (Eq. 2-3), for
+ * verification and for generating exact targets.  Uses the IEEE FP64 kernel
+ * whatever the context's precision.
+ *   theta_host k x 2 positions; beta_host receives k x 2 source positions.
+ * Synchronous (copies in, runs on `stream`, waits, copies out).  Allocates and
+ * frees a device buffer of 32*k bytes.
+ */
+int mlens_trace(mlens_ctx *ctx, const double *theta_host, int64_t k, double *beta_host, void *stream);
+
+/*
+ * mlens_bin -- the binning step of Algorithm 1 alone: count float-pair source
+ * positions (the records mlens_shoot_beta writes for the FP32 variants) into a
+ * source map with the same exact rule and the same privatised histogram.
+ *   beta_dev   n float4 records {x_hi, y_hi, x_lo, y_lo}, device, 16-byte aligned.
+ *   n          number of records, 0 <= n < 2^40.
+ *   counts_dev as for mlens_shoot.
+ * Needs no context: the scratch counters live in a per-device buffer the
+ * library allocates on first use.
+ */
+int mlens_bin(const void *beta_dev, int64_t n, const mlens_grid *src, uint32_t *counts_dev, uint32_t flags,
+              mlens_stats *stats_host, void *stream);
+
+/* Free a context's device memory (waits for its device).  NULL is ignored. */
+void mlens_destroy(mlens_ctx *ctx);
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+const char *mlens_last_error(void);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int mlens_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLENS_H */

@@ -54,6 +54,8 @@ def _load(path: str):
     u64p = C.POINTER(C.c_uint64)
     gp = C.POINTER(OrcGrid)
     L.orc_alpha.argtypes = [dp, C.c_int64, dp, dp, C.c_int64, C.c_double, C.c_double, C.c_double, dp, C.c_int]
+    L.orc_alpha_scale.argtypes = [dp, C.c_int64, dp, dp, C.c_int64, C.c_double, C.c_double, C.c_double, dp,
+                                  C.c_int]
     L.orc_pixels.argtypes = [dp, C.c_int64, gp, ip]
     L.orc_ray_theta.argtypes = [gp, ip, C.c_int64, dp]
     L.orc_shoot.argtypes = [gp, gp, dp, dp, C.c_int64, C.c_double, C.c_double, C.c_double, up, u64p, C.c_int]
@@ -140,6 +142,16 @@ def alpha(theta: np.ndarray, field, nthreads: int = 0) -> np.ndarray:
     out = np.empty_like(th)
     lib().orc_alpha(pth, th.shape[0], pxy, pm, field.n, field.kappa_c, field.gamma1, field.gamma2,
                     out.ctypes.data_as(C.POINTER(C.c_double)), int(nthreads))
+    return out
+
+
+def alpha_scale(theta: np.ndarray, field, nthreads: int = 0) -> np.ndarray:
+    """|alpha_0| + sum_k m_k/|theta-theta_k|: the magnitude scale of the terms of Eq. (3)."""
+    th, pth = _d(np.asarray(theta).reshape(-1, 2))
+    xy, pxy, m, pm = _stars(field)
+    out = np.empty(th.shape[0])
+    lib().orc_alpha_scale(pth, th.shape[0], pxy, pm, field.n, field.kappa_c, field.gamma1, field.gamma2,
+                          out.ctypes.data_as(C.POINTER(C.c_double)), int(nthreads))
     return out
 
 

@@ -78,6 +78,31 @@ void orc_alpha(const double *theta, int64_t k, const double *xy, const double *m
         alpha_one(theta[2 * r], theta[2 * r + 1], xy, m, n, kc, g1, g2, &alpha[2 * r], &alpha[2 * r + 1]);
 }
 
+/* Scale of the terms of Eq. (3) at theta: |alpha_0| + sum_k m_k / |theta - theta_k|.
+ * Any floating-point evaluation of the sum has an absolute error proportional to
+ * this, so |alpha_computed - alpha| / scale is the error measure that stays
+ * meaningful where alpha itself nearly cancels. */
+void orc_alpha_scale(const double *theta, int64_t k, const double *xy, const double *m, int64_t n,
+                     double kc, double g1, double g2, double *scale, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+    for (int64_t r = 0; r < k; ++r) {
+        double tx = theta[2 * r], ty = theta[2 * r + 1];
+        double sx = (kc + g1) * tx + g2 * ty;
+        double sy = g2 * tx + (kc - g1) * ty;
+        double acc = sqrt(sx * sx + sy * sy);
+        for (int64_t s = 0; s < n; ++s) {
+            double dx = tx - xy[2 * s];
+            double dy = ty - xy[2 * s + 1];
+            acc += m[s] / sqrt(dx * dx + dy * dy);
+        }
+        scale[r] = acc;
+    }
+}
+
 /* ------------------------------------------------------ grid and binning */
 
 static double ray_x(const orc_grid *g, int64_t i) { return g->x0 + ((double)i + 0.5) * ((g->x1 - g->x0) / g->nx); }

@@ -1,0 +1,146 @@
+// mlens_dev.cuh -- device helpers shared by the libmlens kernels:
+// float-pair arithmetic, the exact float-pair binning rule (the source-pixel
+// conversion of Algorithm 1) and the privatised, warp-aggregated histogram
+// epilogue that performs its "mag[j_s, i_s] += 1".
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mlens_internal.h"
+
+namespace mlens {
+
+// ------------------------------------------------------------ float pairs
+// Knuth's error-free TwoSum: s + e == a + b exactly, s = fl(a + b).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    float x = __fadd_rn(a, b);
+    float bb = __fsub_rn(x, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(x, bb)), __fsub_rn(b, bb));
+    s = x;
+}
+
+// MUFU reciprocal (max error 1 ulp; 1/0 = +inf).
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// ------------------------------------------------------- exact binning rule
+// Pixel of one axis for beta = bh + bl (an unevaluated float pair):
+// floor((bh + bl - x0) * s) with x0 = x0h + x0l, s = sh + sl, evaluated as
+// float pairs and floored exactly; -1 when outside [0, n).  The operation
+// sequence is part of the library's contract (a CPU re-binning with the same
+// float32 operations reproduces the GPU map bit for bit).
+__device__ __forceinline__ int pair_axis(float bh, float bl, const AxisPair &A)
+{
+    float dh, dl;
+    two_sum(bh, -A.x0h, dh, dl);
+    float t = __fsub_rn(bl, A.x0l);
+    dl = __fadd_rn(dl, t);
+    two_sum(dh, dl, dh, dl);
+    float uh = __fmul_rn(dh, A.sh);
+    float ul = __fmaf_rn(dh, A.sh, -uh);
+    ul = __fmaf_rn(dh, A.sl, ul);
+    ul = __fmaf_rn(dl, A.sh, ul);
+    two_sum(uh, ul, uh, ul);
+    if (!(uh == uh) || isinf(uh)) return -1;
+    float p = floorf(uh);
+    if (p == uh && ul < 0.0f) p = __fsub_rn(p, 1.0f);
+    if (p < 0.0f || p >= (float)A.n) return -1;
+    return (int)p;
+}
+
+// Unclamped floor of the hi part (used only to place the histogram window).
+__device__ __forceinline__ int pair_axis_rough(float bh, const AxisPair &A)
+{
+    float u = (bh - A.x0h) * A.sh;
+    u = fminf(fmaxf(u, -1.0e9f), 1.0e9f);
+    return (int)floorf(u);
+}
+
+// Classify one float-pair beta: returns linear pixel j*nx + i, -1 (out), -2 (non-finite).
+__device__ __forceinline__ int pair_pixel(float xh, float yh, float xl, float yl, const BinGrid &g, int &px,
+                                          int &py)
+{
+    if (!isfinite(xh) || !isfinite(yh) || !isfinite(xl) || !isfinite(yl)) return -2;
+    px = pair_axis(xh, xl, g.ax);
+    py = pair_axis(yh, yl, g.ay);
+    if (px < 0 || py < 0) return -1;
+    return py * g.nx + px;
+}
+
+// ------------------------------------------------ privatised histogram epilogue
+// A CTA's rays come from one compact tile of the lens plane, so almost all of
+// them land in a small patch of the source map.  The CTA counts that patch in
+// a W x W shared-memory window (placed on the pixel of one of its rays), merges
+// equal pixels across a warp with __match_any_sync before touching memory, and
+// adds the window to the global map at the end; rays outside the window go
+// straight to global atomics.
+constexpr int kWin = 64;
+constexpr uint32_t kNoKey = 0xffffffffu;
+
+struct WinHist {
+    uint32_t *h;   // kWin*kWin counters in shared memory
+    int wx0, wy0;  // window origin in pixels
+};
+
+// key: < kWin*kWin for the window, kWin*kWin + pixel for a global pixel, kNoKey for none.
+__device__ __forceinline__ uint32_t hist_key(int pix, int px, int py, const WinHist &W, const BinGrid &g)
+{
+    if (pix < 0) return kNoKey;
+    int wx = px - W.wx0, wy = py - W.wy0;
+    if ((unsigned)wx < (unsigned)kWin && (unsigned)wy < (unsigned)kWin) return (uint32_t)(wy * kWin + wx);
+    return (uint32_t)(kWin * kWin) + (uint32_t)pix;
+}
+
+// Warp-cooperative increment: every lane of the warp must call this together.
+__device__ __forceinline__ void hist_add_warp(uint32_t key, const WinHist &W, uint32_t *counts)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (key != kNoKey && lane == (unsigned)(__ffs(peers) - 1)) {
+        unsigned c = __popc(peers);
+        if (key < (uint32_t)(kWin * kWin))
+            atomicAdd(&W.h[key], c);
+        else
+            atomicAdd(&counts[key - (uint32_t)(kWin * kWin)], c);
+    }
+}
+
+// Add the window to the global map (bins outside the map are never filled).
+__device__ __forceinline__ void hist_flush(const WinHist &W, const BinGrid &g, uint32_t *counts)
+{
+    for (int b = threadIdx.x; b < kWin * kWin; b += blockDim.x) {
+        uint32_t v = W.h[b];
+        if (v) {
+            int gx = W.wx0 + (b % kWin), gy = W.wy0 + (b / kWin);
+            atomicAdd(&counts[(int64_t)gy * g.nx + gx], v);
+        }
+    }
+}
+
+// Block-wide sum of three per-thread counters into global 64-bit stats.
+__device__ __forceinline__ void stats_add_block(unsigned binned, unsigned out, unsigned nan, unsigned *sred,
+                                                unsigned long long *stats)
+{
+    binned = __reduce_add_sync(0xffffffffu, binned);
+    out = __reduce_add_sync(0xffffffffu, out);
+    nan = __reduce_add_sync(0xffffffffu, nan);
+    if ((threadIdx.x & 31u) == 0) {
+        if (binned) atomicAdd(&sred[0], binned);
+        if (out) atomicAdd(&sred[1], out);
+        if (nan) atomicAdd(&sred[2], nan);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && stats) {
+        if (sred[0]) atomicAdd(&stats[0], (unsigned long long)sred[0]);
+        if (sred[1]) atomicAdd(&stats[1], (unsigned long long)sred[1]);
+        if (sred[2]) atomicAdd(&stats[2], (unsigned long long)sred[2]);
+    }
+}
+
+}  // namespace mlens

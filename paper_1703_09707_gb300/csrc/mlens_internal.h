@@ -1,0 +1,80 @@
+// mlens_internal.h -- host-side structures shared by the translation units of
+// libmlens (not part of the public ABI; see include/mlens.h for that).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/mlens.h"
+
+namespace mlens {
+
+// Stars are padded on the device to a multiple of this many records with
+// massless stars far away (they add exactly zero to every sum).
+constexpr int kStarPad = 256;
+constexpr float kPadCoord = 1.0e15f;
+
+// Float-pair constants of one source-map axis: x0 = x0h + x0l and
+// s = n / (x1 - x0) = sh + sl, each split from its double value.
+struct AxisPair {
+    float x0h, x0l, sh, sl;
+    int n;
+};
+
+struct BinGrid {
+    AxisPair ax, ay;
+    double x0, x1, y0, y1;  // the double box, for the FP64 rule
+    int nx, ny;
+};
+
+// Ray grid with its spacing split into float pairs.
+struct RayGrid {
+    double x0, x1, y0, y1;
+    int nx, ny;
+    double dx, dy;          // (x1-x0)/nx, (y1-y0)/ny
+    float dxh, dxl, dyh, dyl;
+};
+
+// Smooth + shear part of Eq. (1): beta = A theta - star sum, A = I - M,
+// M = [[kc+g1, g2], [g2, kc-g1]].
+struct LensTerms {
+    double kc, g1, g2;
+    double a11, a12, a22;   // A in double
+    float fa11, fa12, fa22; // A rounded to float
+    float fm11, fm12, fm22; // M rounded to float (naive variant)
+};
+
+struct ShootArgs {
+    const float4 *stars;    // (x, y, m, 0), padded
+    int64_t nstars;         // padded count, multiple of kStarPad
+    RayGrid rays;
+    BinGrid bin;
+    LensTerms lens;
+    uint32_t *counts;
+    unsigned long long *stats;  // [binned, out, nan]
+    void *beta_out;         // nullable: float4 pairs or double2 (FP64)
+};
+
+struct BinArgs {
+    const float4 *beta;
+    int64_t n;
+    BinGrid bin;
+    uint32_t *counts;
+    unsigned long long *stats;
+};
+
+// launchers (defined in the .cu files)
+cudaError_t launch_shoot_fp32(const ShootArgs &a, int pairs_per_thread, bool naive, cudaStream_t s);
+cudaError_t launch_shoot_fp64(const ShootArgs &a, cudaStream_t s);
+cudaError_t launch_trace_fp64(const float4 *stars, int64_t nstars, const LensTerms &lens, const double2 *theta,
+                              double2 *beta, int64_t k, cudaStream_t s);
+cudaError_t launch_bin(const BinArgs &a, cudaStream_t s);
+
+// helpers (api.cu)
+BinGrid make_bin_grid(const mlens_grid &g);
+RayGrid make_ray_grid(const mlens_grid &g);
+LensTerms make_lens_terms(double kc, double g1, double g2);
+
+}  // namespace mlens

@@ -1,0 +1,217 @@
+"""Thin ctypes binding of libmlens (include/mlens.h).
+
+Argument marshalling only: every function here forwards to the C entry point of the
+same name; all computation runs in the library's CUDA kernels.  Device buffers are
+torch CUDA tensors (their data pointers are passed through); the stream defaults to
+torch's current stream so CUDA events recorded by torch bracket the kernels.
+
+The binding fails loudly when the library has not been built: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from .build import LIB
+
+MLENS_OK = 0
+MLENS_ERR_ARG = -1
+MLENS_ERR_CUDA = -2
+MLENS_ERR_NOMEM = -3
+MLENS_ERR_STATE = -4
+MLENS_ERR_UNSUPPORTED = -5
+
+MLENS_PREC_FP32 = 0
+MLENS_PREC_FP32_NAIVE = 1
+MLENS_PREC_FP64 = 2
+
+MLENS_ACCUMULATE = 1
+
+PRECISIONS = {"fp32": MLENS_PREC_FP32, "fp32_naive": MLENS_PREC_FP32_NAIVE, "fp64": MLENS_PREC_FP64}
+
+
+class MlensError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libmlens error {code}: {msg}")
+        self.code = code
+
+
+class mlens_grid(C.Structure):
+    _fields_ = [("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double),
+                ("nx", C.c_int32), ("ny", C.c_int32)]
+
+
+class mlens_stats(C.Structure):
+    _fields_ = [("rays_total", C.c_uint64), ("rays_binned", C.c_uint64), ("rays_out", C.c_uint64),
+                ("rays_nan", C.c_uint64)]
+
+    def asdict(self):
+        return dict(rays_total=int(self.rays_total), rays_binned=int(self.rays_binned),
+                    rays_out=int(self.rays_out), rays_nan=int(self.rays_nan))
+
+
+_lib = None
+_lock = threading.Lock()
+
+# name -> (restype, argtypes); mirrors include/mlens.h
+_vp = C.c_void_p
+_gp = C.POINTER(mlens_grid)
+_sp = C.POINTER(mlens_stats)
+_dp = C.POINTER(C.c_double)
+SIGNATURES = {
+    "mlens_create": (C.c_int, [C.POINTER(_vp), _dp, _dp, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int32]),
+    "mlens_set_precision": (C.c_int, [_vp, C.c_int32]),
+    "mlens_set_tuning": (C.c_int, [_vp, C.c_int32]),
+    "mlens_shoot": (C.c_int, [_vp, _gp, _gp, _vp, C.c_uint32, _sp, _vp]),
+    "mlens_shoot_beta": (C.c_int, [_vp, _gp, _gp, _vp, _vp, C.c_uint32, _sp, _vp]),
+    "mlens_trace": (C.c_int, [_vp, _dp, C.c_int64, _dp, _vp]),
+    "mlens_bin": (C.c_int, [_vp, C.c_int64, _gp, _vp, C.c_uint32, _sp, _vp]),
+    "mlens_destroy": (None, [_vp]),
+    "mlens_last_error": (C.c_char_p, []),
+    "mlens_version": (C.c_int, []),
+}
+
+
+def load(path: Optional[str] = None):
+    """Open libmlens.so (built by build.py) and declare its signatures."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB
+        if not os.path.exists(p):
+            raise RuntimeError(f"libmlens.so not found at {p}: build it first (python -m paper_1703_09707_gb300.build "
+                               "or __graft_entry__.build()); there is no fallback")
+        L = C.CDLL(p)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        if path is None:
+            _lib = L
+        return L
+
+
+def _check(rc: int):
+    if rc != MLENS_OK:
+        raise MlensError(rc, mlens_last_error())
+
+
+def mlens_last_error() -> str:
+    return load().mlens_last_error().decode()
+
+
+def mlens_version() -> int:
+    return load().mlens_version()
+
+
+def grid(g) -> mlens_grid:
+    if isinstance(g, mlens_grid):
+        return g
+    if hasattr(g, "astuple"):
+        g = g.astuple()
+    x0, x1, y0, y1, nx, ny = g
+    return mlens_grid(float(x0), float(x1), float(y0), float(y1), int(nx), int(ny))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _dev_ptr(t) -> C.c_void_p:
+    if t is None:
+        return C.c_void_p(0)
+    if hasattr(t, "data_ptr"):
+        if not t.is_cuda:
+            raise ValueError("device buffer must be a CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError("device buffer must be contiguous")
+        return C.c_void_p(t.data_ptr())
+    return C.c_void_p(int(t))
+
+
+class Ctx:
+    """Owns one mlens_ctx*."""
+
+    def __init__(self, handle: int):
+        self.handle = C.c_void_p(handle)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def close(self):
+        if self.handle and self.handle.value:
+            load().mlens_destroy(self.handle)
+            self.handle = C.c_void_p(0)
+
+
+def mlens_create(xy: np.ndarray, m: np.ndarray, kappa_c: float, gamma1: float, gamma2: float,
+                 precision=MLENS_PREC_FP32) -> Ctx:
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
+    m = np.ascontiguousarray(m, dtype=np.float64).reshape(-1)
+    if xy.shape[0] != m.shape[0]:
+        raise ValueError("xy and m disagree on the number of stars")
+    h = C.c_void_p(0)
+    _check(load().mlens_create(C.byref(h), xy.ctypes.data_as(_dp), m.ctypes.data_as(_dp), m.shape[0],
+                               float(kappa_c), float(gamma1), float(gamma2), int(precision)))
+    return Ctx(h.value)
+
+
+def mlens_set_precision(ctx: Ctx, precision):
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    _check(load().mlens_set_precision(ctx.handle, int(precision)))
+
+
+def mlens_set_tuning(ctx: Ctx, rays_per_thread: int):
+    _check(load().mlens_set_tuning(ctx.handle, int(rays_per_thread)))
+
+
+def mlens_shoot(ctx: Ctx, rays, src, counts, flags: int = 0, stats: bool = False, stream=None):
+    st = mlens_stats()
+    g, s = grid(rays), grid(src)
+    _check(load().mlens_shoot(ctx.handle, C.byref(g), C.byref(s), _dev_ptr(counts), int(flags),
+                              C.byref(st) if stats else None, _stream_ptr(stream)))
+    return st.asdict() if stats else None
+
+
+def mlens_shoot_beta(ctx: Ctx, rays, src, counts, beta, flags: int = 0, stats: bool = False, stream=None):
+    st = mlens_stats()
+    g, s = grid(rays), grid(src)
+    _check(load().mlens_shoot_beta(ctx.handle, C.byref(g), C.byref(s), _dev_ptr(counts), _dev_ptr(beta),
+                                   int(flags), C.byref(st) if stats else None, _stream_ptr(stream)))
+    return st.asdict() if stats else None
+
+
+def mlens_trace(ctx: Ctx, theta: np.ndarray, stream=None) -> np.ndarray:
+    th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1, 2)
+    out = np.empty_like(th)
+    _check(load().mlens_trace(ctx.handle, th.ctypes.data_as(_dp), th.shape[0], out.ctypes.data_as(_dp),
+                              _stream_ptr(stream)))
+    return out
+
+
+def mlens_bin(beta, n: int, src, counts, flags: int = 0, stats: bool = False, stream=None):
+    st = mlens_stats()
+    s = grid(src)
+    _check(load().mlens_bin(_dev_ptr(beta), int(n), C.byref(s), _dev_ptr(counts), int(flags),
+                            C.byref(st) if stats else None, _stream_ptr(stream)))
+    return st.asdict() if stats else None
+
+
+def mlens_destroy(ctx: Ctx):
+    ctx.close()

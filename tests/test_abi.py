@@ -1,0 +1,76 @@
+"""CPU-side checks of the C ABI: libmlens.so builds, loads without a GPU, exports
+every function include/mlens.h declares with the binding's names, and rejects bad
+arguments with MLENS_ERR_ARG before touching a device.  No compute call runs here."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1703_09707_gb300 import build as B
+from paper_1703_09707_gb300 import mlens as M
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return M.load()
+
+
+def declared_functions():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(mlens_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_every_declared_symbol_is_exported_and_bound(lib):
+    names = declared_functions()
+    assert {"mlens_create", "mlens_shoot", "mlens_destroy", "mlens_last_error"} <= names
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+        assert n in M.SIGNATURES, f"{n} has no binding"
+    assert set(M.SIGNATURES) <= names
+
+
+def test_version(lib):
+    assert M.mlens_version() >= 10000
+
+
+def test_bad_arguments_are_rejected_before_any_device_call(lib):
+    dp = C.POINTER(C.c_double)
+    xy = np.zeros((2, 2))
+    m = np.ones(2)
+    h = C.c_void_p(0)
+    assert lib.mlens_create(None, xy.ctypes.data_as(dp), m.ctypes.data_as(dp), 2, 0.0, 0.0, 0.0, 0) == M.MLENS_ERR_ARG
+    assert lib.mlens_create(C.byref(h), xy.ctypes.data_as(dp), m.ctypes.data_as(dp), -1, 0, 0, 0, 0) == M.MLENS_ERR_ARG
+    assert lib.mlens_create(C.byref(h), None, None, 2, 0.0, 0.0, 0.0, 0) == M.MLENS_ERR_ARG
+    assert lib.mlens_create(C.byref(h), xy.ctypes.data_as(dp), m.ctypes.data_as(dp), 2, float("nan"), 0, 0,
+                            0) == M.MLENS_ERR_ARG
+    assert lib.mlens_create(C.byref(h), xy.ctypes.data_as(dp), m.ctypes.data_as(dp), 2, 0.0, 0.0, 0.0,
+                            7) == M.MLENS_ERR_ARG
+    bad = np.array([[0.0, np.inf], [1.0, 1.0]])
+    assert lib.mlens_create(C.byref(h), bad.ctypes.data_as(dp), m.ctypes.data_as(dp), 2, 0, 0, 0, 0) == M.MLENS_ERR_ARG
+    assert "star 0" in M.mlens_last_error()
+    negm = np.array([1.0, -1.0])
+    assert lib.mlens_create(C.byref(h), xy.ctypes.data_as(dp), negm.ctypes.data_as(dp), 2, 0, 0, 0,
+                            0) == M.MLENS_ERR_ARG
+    assert h.value is None
+    g = M.mlens_grid(-1.0, 1.0, -1.0, 1.0, 4, 4)
+    assert lib.mlens_shoot(None, C.byref(g), C.byref(g), C.c_void_p(16), 0, None, None) == M.MLENS_ERR_ARG
+    assert "context" in M.mlens_last_error()
+    assert lib.mlens_set_tuning(None, 8) == M.MLENS_ERR_ARG
+    assert lib.mlens_set_precision(None, 0) == M.MLENS_ERR_ARG
+    badg = M.mlens_grid(1.0, -1.0, -1.0, 1.0, 4, 4)
+    assert lib.mlens_bin(C.c_void_p(16), 4, C.byref(badg), C.c_void_p(16), 0, None, None) == M.MLENS_ERR_ARG
+    zg = M.mlens_grid(-1.0, 1.0, -1.0, 1.0, 0, 4)
+    assert lib.mlens_bin(C.c_void_p(16), 4, C.byref(zg), C.c_void_p(16), 0, None, None) == M.MLENS_ERR_ARG
+    assert lib.mlens_bin(C.c_void_p(16), 4, C.byref(g), C.c_void_p(18), 0, None, None) == M.MLENS_ERR_ARG
+    assert lib.mlens_bin(C.c_void_p(16), 4, C.byref(g), C.c_void_p(16), 8, None, None) == M.MLENS_ERR_ARG
+    lib.mlens_destroy(None)  # must be a no-op

@@ -1,0 +1,225 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Criteria (spec bar):
+  - bit-exact: the GPU map equals a CPU re-binning of the GPU's own beta with the
+    float32 pair rule, and the GPU's ray bookkeeping equals the re-binning's;
+  - misbinned fraction (GPU pixel != oracle FP64 pixel) <= 1e-4;
+  - per-ray relative deflection error <= 1e-5, measured against the scale of the
+    summed terms: |alpha_gpu - alpha_64| / (|alpha_0| + sum_k m_k/|theta-theta_k|).
+    Where alpha nearly cancels, no float32 evaluation has a small error relative to
+    |alpha| itself; the plain |alpha_gpu - alpha_64| / |alpha_64| is reported too
+    (median, 99.99th percentile and maximum over rays with |alpha_64| >= 1e-3 of
+    the median);
+  - the FP64 variant equals the oracle bit for bit (beta and map).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import workloads as W  # noqa: E402
+
+from gpu_util import compare_to_oracle, make_ctx, shoot_gpu  # noqa: E402
+from paper_1703_09707_gb300 import mlens as M  # noqa: E402
+
+MISBIN_MAX = 1e-4
+REL_MAX = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    M.load()
+    yield
+
+
+def assert_rebin_exact(c, st, b4, src):
+    c_re, st_re = oracle.rebin_pair(b4, src)
+    assert np.array_equal(c, c_re), f"map differs from CPU re-binning in {int((c != c_re).sum())} pixels"
+    assert st == st_re, (st, st_re)
+    assert st["rays_binned"] + st["rays_out"] + st["rays_nan"] == st["rays_total"]
+    assert int(c.sum(dtype=np.uint64)) == st["rays_binned"]
+
+
+@pytest.mark.parametrize("scale", [1.0, 0.333])
+def test_tiny_fp32_full_parity(scale):
+    """100 unit masses, 1000^2 (and a ragged 333^2) rays: every ray checked."""
+    wl = W.config("tiny", rays_scale=scale)
+    f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
+    c, st, b4 = shoot_gpu(f, rays, src)
+    assert_rebin_exact(c, st, b4, src)
+    e = compare_to_oracle(f, rays, src, b4)
+    print("tiny", scale, e)
+    assert e["misbinned_frac"] <= MISBIN_MAX, e
+    assert e["cond_max"] <= REL_MAX, e
+    c64, st64 = oracle.shoot(rays, src, f)
+    assert st["rays_total"] == st64["rays_total"]
+
+
+def test_paper_shaped_reduced_grid_parity():
+    """10^4 power-law stars, kappa_*=0.3, kappa_c=0.2, gamma=(0.3,0), full lens box,
+    1024^2 rays (1/8 of the full grid per axis), full 1024^2 map: every ray checked."""
+    wl = W.config("paper", rays_scale=0.125)
+    f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
+    c, st, b4 = shoot_gpu(f, rays, src)
+    assert_rebin_exact(c, st, b4, src)
+    e = compare_to_oracle(f, rays, src, b4)
+    print("paper 1024^2", e)
+    assert e["misbinned_frac"] <= MISBIN_MAX, e
+    assert e["cond_max"] <= REL_MAX, e
+
+
+def test_paper_full_size_bench_configuration():
+    """The bench workload itself (8192^2 rays, 10^4 stars, 1024^2 map, FP32, the
+    default launch shape): the whole map re-binned bit-exactly, 2*10^5 sampled rays
+    against the oracle."""
+    wl = W.config("paper")
+    f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
+    c, st, b4 = shoot_gpu(f, rays, src)
+    assert st["rays_total"] == 8192 * 8192
+    assert_rebin_exact(c, st, b4, src)
+    idx = W.ray_sample(rays, 200_000, seed=7)
+    e = compare_to_oracle(f, rays, src, b4, idx)
+    print("paper full", e)
+    assert e["misbinned_frac"] <= MISBIN_MAX, e
+    assert e["cond_max"] <= REL_MAX, e
+
+
+def test_fp64_equals_oracle_bit_for_bit():
+    for name, scale in (("tiny", 0.5), ("paper", 1 / 32)):
+        wl = W.config(name, rays_scale=scale)
+        f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
+        c, st, b = shoot_gpu(f, rays, src, prec=M.MLENS_PREC_FP64)
+        idx = np.arange(rays.n, dtype=np.int64)
+        b64 = oracle.beta_rays(rays, idx, f)
+        assert np.array_equal(b.view(np.uint64), b64.view(np.uint64)), name
+        c64, st64 = oracle.shoot(rays, src, f)
+        assert np.array_equal(c, c64), name
+        assert st == st64, (st, st64)
+
+
+def test_trace_fp64_equals_oracle():
+    wl = W.config("paper")
+    f = wl.fields[0]
+    rng = np.random.default_rng(3)
+    th = rng.uniform(-60, 60, (5000, 2))
+    ctx = make_ctx(f)
+    b = M.mlens_trace(ctx, th)
+    ctx.close()
+    assert np.array_equal(b, oracle.beta(th, f))
+
+
+def test_naive_fp32_rebins_exactly_and_reports_error():
+    wl = W.config("paper", rays_scale=0.125)
+    f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
+    c, st, b4 = shoot_gpu(f, rays, src, prec=M.MLENS_PREC_FP32_NAIVE)
+    assert np.all(b4[:, 2:] == 0)
+    assert_rebin_exact(c, st, b4, src)
+    e = compare_to_oracle(f, rays, src, b4)
+    print("naive", e)
+    # the naive loop is kept to show its error; it must still be a sane deflection
+    assert e["cond_max"] < 1e-3
+
+
+# ----------------------------------------------------------------- edge cases
+def test_sheet_exact_integer_counts_gpu():
+    """No stars (n=0), kappa_c=1/2, gamma=(1/4,0) on a dyadic lattice: every pixel
+    holds exactly 8 rays, in every precision."""
+    f = W.Field(xy=np.zeros((0, 2)), m=np.zeros(0), kappa_c=0.5, gamma1=0.25, gamma2=0.0)
+    d = 1.0 / 16.0
+    rays = W.Grid(-8.0, 8.0, -8.0, 8.0, 256, 256)
+    sx0, sy0 = (-8.0 + 40 * d) / 4.0, 0.75 * (-8.0 + 60 * d)
+    src = W.Grid(sx0, sx0 + 30 * 4 * d / 4.0, sy0, sy0 + 40 * 2 * 0.75 * d, 30, 40)
+    for prec in (M.MLENS_PREC_FP32, M.MLENS_PREC_FP32_NAIVE, M.MLENS_PREC_FP64):
+        c, st, _ = shoot_gpu(f, rays, src, prec=prec, want_beta=False)
+        assert np.all(c == 8), prec
+        assert st["rays_binned"] == 30 * 40 * 8
+
+
+def test_point_lens_matches_oracle_map():
+    f = W.Field(xy=np.zeros((1, 2)), m=np.ones(1), kappa_c=0.0, gamma1=0.0, gamma2=0.0)
+    rays = W.Grid(-10.0, 10.0, -10.0, 10.0, 2048, 2048)
+    src = W.Grid(-4.0, 4.0, -4.0, 4.0, 64, 64)
+    c, st, b4 = shoot_gpu(f, rays, src)
+    assert_rebin_exact(c, st, b4, src)
+    c64, st64 = oracle.shoot(rays, src, f)
+    e = compare_to_oracle(f, rays, src, b4)
+    assert e["misbinned_frac"] <= MISBIN_MAX
+    # each misbinned ray moves one count between two pixels
+    assert int(np.abs(c.astype(np.int64) - c64).sum()) <= 2 * e["misbinned"]
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (7, 5), (65, 33), (1000, 777), (64, 32)])
+def test_ragged_and_tiny_grids(nx, ny):
+    wl = W.config("tiny")
+    f = wl.fields[0]
+    rays = W.Grid(-3.0, 4.0, -2.5, 3.5, nx, ny)
+    src = W.Grid(-3.0, 3.0, -3.0, 3.0, 257, 129)  # odd map sizes
+    c, st, b4 = shoot_gpu(f, rays, src)
+    assert st["rays_total"] == nx * ny
+    assert_rebin_exact(c, st, b4, src)
+    e = compare_to_oracle(f, rays, src, b4)
+    assert e["misbinned"] == 0 or e["misbinned_frac"] <= MISBIN_MAX
+
+
+def test_ray_exactly_on_a_star_is_nan():
+    f = W.Field(xy=np.array([[0.5, 0.5], [3.0, 1.0]]), m=np.array([1.0, 0.5]), kappa_c=0.1, gamma1=0.0,
+                gamma2=0.0)
+    rays = W.Grid(0.0, 1.0, 0.0, 1.0, 1, 1)  # the one ray sits on the first star
+    src = W.Grid(-2.0, 2.0, -2.0, 2.0, 8, 8)
+    for prec in (M.MLENS_PREC_FP32, M.MLENS_PREC_FP32_NAIVE, M.MLENS_PREC_FP64):
+        c, st, _ = shoot_gpu(f, rays, src, prec=prec, want_beta=False)
+        assert st == dict(rays_total=1, rays_binned=0, rays_out=0, rays_nan=1), (prec, st)
+        assert c.sum() == 0
+
+
+def test_accumulate_and_determinism():
+    wl = W.config("paper", rays_scale=1 / 16)
+    f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
+    ctx = make_ctx(f)
+    counts = torch.empty(src.n, dtype=torch.int32, device="cuda")
+    M.mlens_shoot(ctx, rays, src, counts)
+    a = counts.clone()
+    M.mlens_shoot(ctx, rays, src, counts)
+    assert torch.equal(a, counts), "integer atomics commute: maps must be identical run to run"
+    M.mlens_shoot(ctx, rays, src, counts, flags=M.MLENS_ACCUMULATE)
+    assert torch.equal(counts, 2 * a)
+    ctx.close()
+
+
+def test_standalone_bin_matches_fused_map():
+    wl = W.config("paper", rays_scale=0.125)
+    f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
+    ctx = make_ctx(f)
+    counts = torch.empty(src.n, dtype=torch.int32, device="cuda")
+    beta = torch.empty(rays.n * 4, dtype=torch.float32, device="cuda")
+    st = M.mlens_shoot_beta(ctx, rays, src, counts, beta, stats=True)
+    counts2 = torch.empty_like(counts)
+    st2 = M.mlens_bin(beta, rays.n, src, counts2, stats=True)
+    assert torch.equal(counts, counts2)
+    assert st == st2
+    ctx.close()
+
+
+def test_launch_shapes_both_meet_the_bar():
+    """rays_per_thread 4 and 8 use different tiles (different centres), so beta may
+    differ in its last bits; both must meet the bar and nearly agree."""
+    wl = W.config("paper", rays_scale=1 / 8)
+    f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
+    maps = []
+    for rpt in (4, 8):
+        ctx = make_ctx(f)
+        M.mlens_set_tuning(ctx, rpt)
+        c, st, b4 = shoot_gpu(f, rays, src, ctx=ctx)
+        ctx.close()
+        assert_rebin_exact(c, st, b4, src)
+        e = compare_to_oracle(f, rays, src, b4)
+        assert e["misbinned_frac"] <= MISBIN_MAX and e["cond_max"] <= REL_MAX, (rpt, e)
+        maps.append(c.astype(np.int64))
+    assert np.abs(maps[0] - maps[1]).sum() <= 2 * MISBIN_MAX * rays.n

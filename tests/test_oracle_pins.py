@@ -326,3 +326,16 @@ def test_pair_rebin_matches_fp64_binning_of_the_same_values():
     # rays within that distance of a pixel edge, which the seeded inputs do not hit
     assert np.array_equal(c_pair, c64)
     assert st == st64
+
+
+def test_alpha_scale_bounds_alpha():
+    """The error scale |alpha_0| + sum m/|theta-theta_k| is >= |alpha| (triangle
+    inequality) and equals it for one star with no smooth terms (m/r)."""
+    rng = np.random.default_rng(8)
+    f = field(rng.uniform(-3, 3, (30, 2)), rng.uniform(0.1, 1, 30), 0.2, 0.1, -0.3)
+    th = rng.uniform(-3, 3, (200, 2))
+    a = np.linalg.norm(oracle.alpha(th, f), axis=1)
+    assert np.all(oracle.alpha_scale(th, f) >= a * (1 - 1e-14))
+    one = field([[1.0, 2.0]], [0.5])
+    th1 = np.array([[4.0, 6.0], [1.0, -1.0]])
+    assert np.allclose(oracle.alpha_scale(th1, one), [0.5 / 5.0, 0.5 / 3.0], rtol=1e-15)
