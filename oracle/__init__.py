@@ -56,6 +56,8 @@ def _load(path: str):
     L.orc_alpha.argtypes = [dp, C.c_int64, dp, dp, C.c_int64, C.c_double, C.c_double, C.c_double, dp, C.c_int]
     L.orc_alpha_scale.argtypes = [dp, C.c_int64, dp, dp, C.c_int64, C.c_double, C.c_double, C.c_double, dp,
                                   C.c_int]
+    L.orc_alpha_jacobian.argtypes = [dp, C.c_int64, dp, dp, C.c_int64, C.c_double, C.c_double, C.c_double, dp,
+                                     C.c_int]
     L.orc_pixels.argtypes = [dp, C.c_int64, gp, ip]
     L.orc_ray_theta.argtypes = [gp, ip, C.c_int64, dp]
     L.orc_shoot.argtypes = [gp, gp, dp, dp, C.c_int64, C.c_double, C.c_double, C.c_double, up, u64p, C.c_int]
@@ -152,6 +154,16 @@ def alpha_scale(theta: np.ndarray, field, nthreads: int = 0) -> np.ndarray:
     out = np.empty(th.shape[0])
     lib().orc_alpha_scale(pth, th.shape[0], pxy, pm, field.n, field.kappa_c, field.gamma1, field.gamma2,
                           out.ctypes.data_as(C.POINTER(C.c_double)), int(nthreads))
+    return out
+
+
+def alpha_jacobian(theta: np.ndarray, field, nthreads: int = 0) -> np.ndarray:
+    """d alpha / d theta of Eq. (3) as (k,3) = {J11, J12, J22}."""
+    th, pth = _d(np.asarray(theta).reshape(-1, 2))
+    xy, pxy, m, pm = _stars(field)
+    out = np.empty((th.shape[0], 3))
+    lib().orc_alpha_jacobian(pth, th.shape[0], pxy, pm, field.n, field.kappa_c, field.gamma1, field.gamma2,
+                             out.ctypes.data_as(C.POINTER(C.c_double)), int(nthreads))
     return out
 
 

@@ -103,6 +103,34 @@ void orc_alpha_scale(const double *theta, int64_t k, const double *xy, const dou
     }
 }
 
+/* Jacobian d alpha / d theta of Eq. (3): M + sum_k m_k (r^2 I - 2 d d^T) / r^4,
+ * d = theta - theta_k; out = {J11, J12, J22} per position (J is symmetric).
+ * It bounds how far alpha moves when a position is rounded. */
+void orc_alpha_jacobian(const double *theta, int64_t k, const double *xy, const double *m, int64_t n,
+                        double kc, double g1, double g2, double *jac, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+    for (int64_t r = 0; r < k; ++r) {
+        double tx = theta[2 * r], ty = theta[2 * r + 1];
+        double j11 = kc + g1, j12 = g2, j22 = kc - g1;
+        for (int64_t s = 0; s < n; ++s) {
+            double dx = tx - xy[2 * s];
+            double dy = ty - xy[2 * s + 1];
+            double r2 = dx * dx + dy * dy;
+            double w = m[s] / (r2 * r2);
+            j11 += w * (dy * dy - dx * dx);
+            j12 += w * (-2.0 * dx * dy);
+            j22 += w * (dx * dx - dy * dy);
+        }
+        jac[3 * r] = j11;
+        jac[3 * r + 1] = j12;
+        jac[3 * r + 2] = j22;
+    }
+}
+
 /* ------------------------------------------------------ grid and binning */
 
 static double ray_x(const orc_grid *g, int64_t i) { return g->x0 + ((double)i + 0.5) * ((g->x1 - g->x0) / g->nx); }

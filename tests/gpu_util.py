@@ -1,5 +1,7 @@
 """Helpers for the GPU parity tests: run the CUDA path through the C ABI and compare
 with the FP64 oracle.  Imported only by tests marked gpu."""
+import math
+
 import numpy as np
 import torch
 
@@ -42,9 +44,21 @@ def beta_pair_to_f64(b4):
     return b4[:, :2].astype(np.float64) + b4[:, 2:].astype(np.float64)
 
 
-def compare_to_oracle(f, rays, src, b4, idx=None, nthreads=0):
+def position_rounding(rays, rays_per_thread=8):
+    """Bound on the float32 rounding of ray and star positions taken relative to a
+    tile centre in the FP32 kernels: 2^-22 of the tile extent (tile = 64 x 4*rpt rays)."""
+    ext = max(64 * (rays.x1 - rays.x0) / rays.nx, 4 * rays_per_thread * (rays.y1 - rays.y0) / rays.ny)
+    return 2.0 ** -22 * ext
+
+
+def compare_to_oracle(f, rays, src, b4, idx=None, nthreads=0, rays_per_thread=8):
     """Per-ray comparison of GPU float-pair beta (rows idx of the grid, or all rays)
-    with the FP64 oracle.  Returns a dict of error statistics."""
+    with the FP64 oracle.  Returns a dict of error statistics.
+
+    `bound_ratio` is the deflection error over its allowance
+        1e-5 * (|alpha_0| + sum_k m_k/r_k)  +  ||d alpha/d theta||_F * sqrt(2) * eps_pos,
+    the first term a 1e-5 relative error of the summed terms, the second the effect
+    of rounding the ray/star offsets from the tile centre to float32 (eps_pos)."""
     if idx is None:
         idx = np.arange(rays.n, dtype=np.int64)
         bsel = b4
@@ -61,6 +75,10 @@ def compare_to_oracle(f, rays, src, b4, idx=None, nthreads=0):
     rel = err[ok] / amag[ok]
     scale = oracle.alpha_scale(th, f, nthreads)
     cond = err[fin] / scale[fin]
+    J = oracle.alpha_jacobian(th, f, nthreads)
+    jn = np.sqrt(J[:, 0] ** 2 + 2 * J[:, 1] ** 2 + J[:, 2] ** 2)
+    allow = 1e-5 * scale + jn * math.sqrt(2.0) * position_rounding(rays, rays_per_thread)
+    ratio = err[fin] / allow[fin]
     pix_o = oracle.pixels(b64, src)
     pix_g = oracle.pair_pixels(bsel, src)
     w = min((src.x1 - src.x0) / src.nx, (src.y1 - src.y0) / src.ny)
@@ -68,4 +86,5 @@ def compare_to_oracle(f, rays, src, b4, idx=None, nthreads=0):
     return dict(n=int(idx.shape[0]), misbinned=int(np.sum(pix_o != pix_g)), misbinned_frac=float(np.mean(pix_o != pix_g)),
                 rel_max=float(rel.max()), rel_p50=float(np.median(rel)), rel_p9999=float(np.quantile(rel, 0.9999)),
                 cond_max=float(cond.max()), cond_p50=float(np.median(cond)),
+                bound_ratio=float(ratio.max()),
                 dbeta_mean_px=float(dbeta[np.isfinite(dbeta).all(1)].mean() / w))

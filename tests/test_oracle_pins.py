@@ -339,3 +339,22 @@ def test_alpha_scale_bounds_alpha():
     one = field([[1.0, 2.0]], [0.5])
     th1 = np.array([[4.0, 6.0], [1.0, -1.0]])
     assert np.allclose(oracle.alpha_scale(th1, one), [0.5 / 5.0, 0.5 / 3.0], rtol=1e-15)
+
+
+def test_alpha_jacobian_matches_finite_differences():
+    """The analytic Jacobian equals central differences of alpha (and is symmetric
+    by construction, matching the curl-free star term)."""
+    rng = np.random.default_rng(9)
+    f = field(rng.uniform(-3, 3, (20, 2)), rng.uniform(0.1, 1, 20), 0.15, -0.2, 0.25)
+    th = rng.uniform(-3, 3, (200, 2))
+    dmin = np.min(np.hypot(th[:, None, 0] - f.xy[None, :, 0], th[:, None, 1] - f.xy[None, :, 1]), axis=1)
+    th = th[dmin > 0.2]
+    h = 1e-6
+    jx = (oracle.alpha(th + [h, 0], f) - oracle.alpha(th - [h, 0], f)) / (2 * h)
+    jy = (oracle.alpha(th + [0, h], f) - oracle.alpha(th - [0, h], f)) / (2 * h)
+    J = oracle.alpha_jacobian(th, f)
+    tol = 1e-6 * (1 + np.abs(J).max(1))
+    assert np.all(np.abs(J[:, 0] - jx[:, 0]) < tol)
+    assert np.all(np.abs(J[:, 1] - jx[:, 1]) < tol)
+    assert np.all(np.abs(J[:, 1] - jy[:, 0]) < tol)
+    assert np.all(np.abs(J[:, 2] - jy[:, 1]) < tol)
