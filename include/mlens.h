@@ -165,6 +165,40 @@ int mlens_trace(mlens_ctx *ctx, const double *theta_host, int64_t k, double *bet
 int mlens_bin(const void *beta_dev, int64_t n, const mlens_grid *src, uint32_t *counts_dev, uint32_t flags,
               mlens_stats *stats_host, void *stream);
 
+/*
+ * mlens_shoot_noalloc -- mlens_shoot for callers that must not allocate device
+ * memory: code that runs while a CUDA stream is being captured into a graph
+ * (cudaMalloc is not allowed there), plugins whose host application owns every
+ * device allocation, and real-time loops that may not enter the allocator.  It
+ * takes no context: the caller passes the stars already on the device, and the
+ * only working memory is a fixed array compiled into the library.
+ * The paper has no counterpart; it is a deployment variant of the same FP32
+ * kernel (MLENS_PREC_FP32, 8 rays per thread), so it produces the same map as
+ * mlens_create + mlens_shoot on the same float32 star values.
+ *   stars_dev  n records float4 {x, y, m, unused} on the current device,
+ *              16-byte aligned, caller-owned.  The values are not checked:
+ *              non-finite entries give non-finite beta for the rays they touch.
+ *   n          0 <= n <= MLENS_NOALLOC_MAX_STARS.
+ *   kappa_c, gamma1, gamma2, rays, src, counts_dev, flags, stats_host, stream
+ *              as for mlens_create / mlens_shoot.
+ * Working memory: one file-scope device array of MLENS_NOALLOC_MAX_STARS + 256
+ * star records plus three 64-bit counters (about 1 MiB), held on every device
+ * that loads the library until the process exits.  Each call copies the stars
+ * into it (padding the tail) and clears the counters on `stream` before the
+ * kernel runs; the array keeps the last call's contents afterwards.  All calls
+ * share that one array, so calls whose GPU work overlaps (different streams,
+ * or different host threads) race and corrupt each other's maps: serialise them.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture begins.
+ * Errors: MLENS_ERR_ARG (n above the maximum, bad grid, NULL or misaligned
+ * pointer, non-finite lens terms), MLENS_ERR_CUDA.
+ */
+#define MLENS_NOALLOC_MAX_STARS 65536
+int mlens_shoot_noalloc(const void *stars_dev, int64_t n, double kappa_c, double gamma1, double gamma2,
+                        const mlens_grid *rays, const mlens_grid *src, uint32_t *counts_dev, uint32_t flags,
+                        mlens_stats *stats_host, void *stream);
+
 /* Free a context's device memory (waits for its device).  NULL is ignored. */
 void mlens_destroy(mlens_ctx *ctx);
 

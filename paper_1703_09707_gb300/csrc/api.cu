@@ -160,6 +160,8 @@ int shoot_impl(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid *src, ui
 
 namespace mlens {
 
+void set_last_error(const std::string &msg) { g_err = msg; }
+
 BinGrid make_bin_grid(const mlens_grid &g)
 {
     BinGrid b;

@@ -73,6 +73,7 @@ cudaError_t launch_trace_fp64(const float4 *stars, int64_t nstars, const LensTer
 cudaError_t launch_bin(const BinArgs &a, cudaStream_t s);
 
 // helpers (api.cu)
+void set_last_error(const std::string &msg);
 BinGrid make_bin_grid(const mlens_grid &g);
 RayGrid make_ray_grid(const mlens_grid &g);
 LensTerms make_lens_terms(double kc, double g1, double g2);

@@ -70,6 +70,8 @@ SIGNATURES = {
     "mlens_shoot_beta": (C.c_int, [_vp, _gp, _gp, _vp, _vp, C.c_uint32, _sp, _vp]),
     "mlens_trace": (C.c_int, [_vp, _dp, C.c_int64, _dp, _vp]),
     "mlens_bin": (C.c_int, [_vp, C.c_int64, _gp, _vp, C.c_uint32, _sp, _vp]),
+    "mlens_shoot_noalloc": (C.c_int, [_vp, C.c_int64, C.c_double, C.c_double, C.c_double, _gp, _gp, _vp, C.c_uint32,
+                                      _sp, _vp]),
     "mlens_destroy": (None, [_vp]),
     "mlens_last_error": (C.c_char_p, []),
     "mlens_version": (C.c_int, []),
@@ -210,6 +212,17 @@ def mlens_bin(beta, n: int, src, counts, flags: int = 0, stats: bool = False, st
     s = grid(src)
     _check(load().mlens_bin(_dev_ptr(beta), int(n), C.byref(s), _dev_ptr(counts), int(flags),
                             C.byref(st) if stats else None, _stream_ptr(stream)))
+    return st.asdict() if stats else None
+
+
+def mlens_shoot_noalloc(stars, n: int, kappa_c: float, gamma1: float, gamma2: float, rays, src, counts,
+                        flags: int = 0, stats: bool = False, stream=None):
+    """stars: CUDA float32 tensor of n records (x, y, m, unused)."""
+    st = mlens_stats()
+    g, s = grid(rays), grid(src)
+    _check(load().mlens_shoot_noalloc(_dev_ptr(stars), int(n), float(kappa_c), float(gamma1), float(gamma2),
+                                      C.byref(g), C.byref(s), _dev_ptr(counts), int(flags),
+                                      C.byref(st) if stats else None, _stream_ptr(stream)))
     return st.asdict() if stats else None
 
 
