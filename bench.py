@@ -60,6 +60,8 @@ def parse():
                     help="shrink the ray grid per axis (same field, boxes and map) for profiling runs")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-fields measurement that rides along the main line")
     return ap.parse_args()
 
 
@@ -169,6 +171,57 @@ def cpu_oracle_rate(field, rays, target_s: float, seed: int = 11):
     oracle.beta_rays(rays, idx, field)
     dt = time.perf_counter() - t0
     return k * n / dt, cores, f"{k} random rays of the grid x all {field.n} stars, FP64, {dt:.1f} s"
+
+
+# --------------------------------------------------------------- batched
+def bench_batched(M, torch, steps: int, warmup: int, flush):
+    """256 independent fields (N_* log-uniform in [1e2, 1e4], 2048^2 rays, 512^2 maps):
+    one autotuned persistent launch replayed as a CUDA graph versus one mlens_shoot
+    launch per field with the same launch shape.  Device time, CUDA events."""
+    wl = W.batched_config()
+    ctxs = [M.mlens_create(f.xy, f.m, f.kappa_c, f.gamma1, f.gamma2, M.MLENS_PREC_FP32) for f in wl.fields]
+    counts = [torch.empty(s.n, dtype=torch.int32, device="cuda") for s in wl.srcs]
+    inter = sum(r.n * f.n for r, f in zip(wl.rays, wl.fields))
+    stream = torch.cuda.current_stream()
+    b = M.mlens_batch_create(ctxs, wl.rays, wl.srcs, counts)
+    t0 = time.perf_counter()
+    rpt, stage, tune_ms = M.mlens_batch_tune(b)
+    tune_s = time.perf_counter() - t0
+
+    def timed(fn):
+        for _ in range(warmup):
+            flush.fill_(0.0)
+            fn()
+        ms = []
+        for i in range(steps):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.mean(ms)
+
+    persistent_ms = timed(lambda: M.mlens_batch_run(b))
+    for c in ctxs:
+        M.mlens_set_tuning(c, rpt, stage)
+    per_field_ms = timed(lambda: [M.mlens_shoot(c, r, s, k) for c, r, s, k in zip(ctxs, wl.rays, wl.srcs, counts)])
+    b.close()
+    for c in ctxs:
+        c.close()
+    nf = len(wl.fields)
+    return {
+        "workload": f"batched: {nf} fields, N_* log-uniform [1e2,1e4] (mean {inter / (nf * wl.rays[0].n):.0f}), "
+                    f"{wl.rays[0].nx}^2 rays, {wl.srcs[0].nx}^2 maps",
+        "maps_per_s": nf / (persistent_ms / 1e3),
+        "maps_per_s_per_field_launches": nf / (per_field_ms / 1e3),
+        "speedup_vs_per_field_launches": per_field_ms / persistent_ms,
+        "interactions_per_s": inter / (persistent_ms / 1e3),
+        "ms_per_batch": persistent_ms, "ms_per_batch_per_field_launches": per_field_ms,
+        "tuned": {"rays_per_thread": rpt, "star_stage": stage, "tune_s": tune_s},
+        "gpu_launches_per_batch": 1,
+    }
 
 
 # ------------------------------------------------------------------- main
@@ -338,6 +391,11 @@ def run_mine(args):
         "device": props.name,
     }
     line["config"]["rays_per_thread"] = args.rays_per_thread
+    if not args.no_extras and world == 1 and args.workload == "paper" and args.rays_scale == 1.0:
+        bt = bench_batched(M, torch, max(2, min(args.steps, 5)), 2, flush)
+        peak_b = n_sm * MUFU_RCP_PER_SM_CLK * SM_MAX_MHZ * 1e6
+        bt["roofline_frac"] = bt["interactions_per_s"] / peak_b
+        line["batched"] = bt
     if not args.no_cpu_baseline and world == 1:
         v, cores, sample = cpu_oracle_rate(f, rays, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "interactions/s", "cores": cores, "kind": "oracle",

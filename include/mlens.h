@@ -104,11 +104,13 @@ int mlens_set_precision(mlens_ctx *ctx, int32_t precision);
 /*
  * mlens_set_tuning -- launch shape of the FP32 kernels for later calls on this
  * context: rays_per_thread in {4, 8} (tile 64 x 16 or 64 x 32 rays per CTA of
- * 256 threads).  Different shapes put tile centres in different places, so beta
- * can differ in its last bits between shapes (never by more than the error bar);
- * a given shape is deterministic.  Default 8.
+ * 256 threads) and star_stage in {128, 256, 512} stars staged through shared
+ * memory at a time (0 = 256).  The stage size never changes the arithmetic.
+ * Different tile shapes put tile centres in different places, so beta can
+ * differ in its last bits between shapes (never by more than the error bar); a
+ * given shape is deterministic.  Defaults: 8 rays per thread, 256 stars.
  */
-int mlens_set_tuning(mlens_ctx *ctx, int32_t rays_per_thread);
+int mlens_set_tuning(mlens_ctx *ctx, int32_t rays_per_thread, int32_t star_stage);
 
 /*
  * mlens_shoot -- Algorithm 1 over a whole ray grid: deflect every ray by Eq. (3),
@@ -181,7 +183,7 @@ int mlens_bin(const void *beta_dev, int64_t n, const mlens_grid *src, uint32_t *
  *   n          0 <= n <= MLENS_NOALLOC_MAX_STARS.
  *   kappa_c, gamma1, gamma2, rays, src, counts_dev, flags, stats_host, stream
  *              as for mlens_create / mlens_shoot.
- * Working memory: one file-scope device array of MLENS_NOALLOC_MAX_STARS + 256
+ * Working memory: one file-scope device array of MLENS_NOALLOC_MAX_STARS + 32
  * star records plus three 64-bit counters (about 1 MiB), held on every device
  * that loads the library until the process exits.  Each call copies the stars
  * into it (padding the tail) and clears the counters on `stream` before the
@@ -198,6 +200,60 @@ int mlens_bin(const void *beta_dev, int64_t n, const mlens_grid *src, uint32_t *
 int mlens_shoot_noalloc(const void *stars_dev, int64_t n, double kappa_c, double gamma1, double gamma2,
                         const mlens_grid *rays, const mlens_grid *src, uint32_t *counts_dev, uint32_t flags,
                         mlens_stats *stats_host, void *stream);
+
+/* ------------------------------------------------------------- batching */
+/*
+ * Many independent fields in one launch.  Section 2.2 runs grids of independent
+ * simulations over (<M*>, gamma, kappa_*, kappa_c), each its own map; a batch
+ * shoots them all in one persistent kernel that pulls (field, ray tile) items
+ * from a device work queue, heaviest fields first, captured once into a CUDA
+ * graph and replayed.  Every field uses MLENS_PREC_FP32 whatever its context's
+ * setting.  With the same launch shape (see mlens_set_tuning) a field's map is
+ * identical to mlens_shoot's on its own.
+ */
+typedef struct mlens_batch mlens_batch;
+
+/*
+ * mlens_batch_create -- describe a batch.
+ *   ctxs[nfields]        contexts created on the current device (1 <= nfields <= 2^20);
+ *   rays[nfields], srcs[nfields]  per-field ray grid and source map (limits as mlens_shoot);
+ *   counts_dev[nfields]  per-field maps (srcs[f].ny x srcs[f].nx uint32, device, caller-owned);
+ *   flags                0 or MLENS_ACCUMULATE.
+ * Contexts and maps must stay alive, and unchanged in size, while the batch exists.
+ * Allocates about 300 bytes per field of device tables and one private stream.
+ * Launch shape starts at 8 rays per thread and 256-star stages.
+ */
+int mlens_batch_create(mlens_batch **out, mlens_ctx *const *ctxs, int32_t nfields, const mlens_grid *rays,
+                       const mlens_grid *srcs, uint32_t *const *counts_dev, uint32_t flags);
+
+/* Set the launch shape (rays_per_thread 4 or 8; star_stage 0=256, 128, 256, 512).
+ * Waits for the device; the graph is captured again at the next run. */
+int mlens_batch_set_tuning(mlens_batch *b, int32_t rays_per_thread, int32_t star_stage);
+
+/*
+ * mlens_batch_tune -- the autotuner: time every launch shape on this batch (a
+ * warm-up and two timed replays each, CUDA events on `stream`), keep the fastest
+ * and report it (any output pointer may be NULL; *best_ms = -1 when the shape came
+ * from the cache).  Results are cached per process by device and workload
+ * signature (field count, ray grid, star counts bucketed by powers of two), and
+ * appended to / read from the text file named by the environment variable
+ * MLENS_TUNE_CACHE when it is set.  The maps are overwritten by the trial runs.
+ */
+int mlens_batch_tune(mlens_batch *b, void *stream, int32_t *rays_per_thread, int32_t *star_stage, double *best_ms);
+
+/*
+ * mlens_batch_run -- shoot every field (graph launch on `stream`; the first run of a
+ * launch shape captures the graph).  stats_host, if non-NULL, receives nfields
+ * records and makes the call wait for the stream.
+ */
+int mlens_batch_run(mlens_batch *b, mlens_stats *stats_host, void *stream);
+
+/* Free a batch (waits for its device).  NULL is ignored. */
+void mlens_batch_destroy(mlens_batch *b);
+
+/* One-shot batch: create, run once, wait for the stream, destroy. */
+int mlens_shoot_batch(mlens_ctx *const *ctxs, int32_t nfields, const mlens_grid *rays, const mlens_grid *srcs,
+                      uint32_t *const *counts_dev, uint32_t flags, mlens_stats *stats_host, void *stream);
 
 /* Free a context's device memory (waits for its device).  NULL is ignored. */
 void mlens_destroy(mlens_ctx *ctx);

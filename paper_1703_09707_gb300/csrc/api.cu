@@ -16,17 +16,6 @@
 
 using namespace mlens;
 
-struct mlens_ctx {
-    int device = -1;
-    int64_t n = 0;          // stars given
-    int64_t n_pad = 0;      // stars on the device (multiple of kStarPad)
-    float4 *d_stars = nullptr;
-    unsigned long long *d_stats = nullptr;  // [binned, out, nan]
-    LensTerms lens{};
-    int precision = MLENS_PREC_FP32;
-    int pairs_per_thread = 4;
-};
-
 namespace {
 
 thread_local std::string g_err;
@@ -150,7 +139,7 @@ int shoot_impl(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid *src, ui
     if (ctx->precision == MLENS_PREC_FP64)
         e = launch_shoot_fp64(a, s);
     else
-        e = launch_shoot_fp32(a, ctx->pairs_per_thread, ctx->precision == MLENS_PREC_FP32_NAIVE, s);
+        e = launch_shoot_fp32(a, ctx->pairs_per_thread, ctx->precision == MLENS_PREC_FP32_NAIVE, s, ctx->star_stage);
     if (e != cudaSuccess) return cuda_fail(e, "shoot kernel launch");
     if (stats) return read_stats(ctx->d_stats, (uint64_t)rays->nx * (uint64_t)rays->ny, stats, s);
     return MLENS_OK;
@@ -277,11 +266,14 @@ int mlens_set_precision(mlens_ctx *ctx, int32_t precision)
     return MLENS_OK;
 }
 
-int mlens_set_tuning(mlens_ctx *ctx, int32_t rays_per_thread)
+int mlens_set_tuning(mlens_ctx *ctx, int32_t rays_per_thread, int32_t star_stage)
 {
     if (!ctx) return fail(MLENS_ERR_ARG, "context is NULL");
     if (rays_per_thread != 4 && rays_per_thread != 8) return fail(MLENS_ERR_ARG, "rays_per_thread must be 4 or 8");
+    if (star_stage != 0 && star_stage != 128 && star_stage != 256 && star_stage != 512)
+        return fail(MLENS_ERR_ARG, "star_stage must be 0 (default), 128, 256 or 512");
     ctx->pairs_per_thread = rays_per_thread / 2;
+    ctx->star_stage = star_stage ? star_stage : 256;
     return MLENS_OK;
 }
 

@@ -11,9 +11,10 @@
 
 namespace mlens {
 
-// Stars are padded on the device to a multiple of this many records with
-// massless stars far away (they add exactly zero to every sum).
-constexpr int kStarPad = 256;
+// Stars are padded on the device to a multiple of this many records (one
+// compensated-summation chunk) with massless stars far away; they add exactly
+// zero to every sum.
+constexpr int kStarPad = 32;
 constexpr float kPadCoord = 1.0e15f;
 
 // Float-pair constants of one source-map axis: x0 = x0h + x0l and
@@ -65,8 +66,24 @@ struct BinArgs {
     unsigned long long *stats;
 };
 
+// Persistent multi-field launch: device tables built by the batch API.
+struct BatchLaunch {
+    int grid;                     // persistent CTAs (SMs x resident CTAs per SM)
+    const ShootArgs *fields;      // nfields descriptors (device)
+    const int *order;             // field processing order, heaviest first (device)
+    const int64_t *begin;         // nfields+1 item offsets in that order (device)
+    int nfields;
+    int64_t total;                // total (field, tile) items
+    unsigned long long *counter;  // work-queue counter, zero before each launch (device)
+};
+
 // launchers (defined in the .cu files)
-cudaError_t launch_shoot_fp32(const ShootArgs &a, int pairs_per_thread, bool naive, cudaStream_t s);
+// pairs_per_thread in {2, 4} (4 or 8 rays per thread); stage in {128, 256, 512} stars
+cudaError_t launch_shoot_fp32(const ShootArgs &a, int pairs_per_thread, bool naive, cudaStream_t s,
+                              int stage = 256);
+cudaError_t launch_shoot_batch(const BatchLaunch &b, int pairs_per_thread, int stage, cudaStream_t s);
+cudaError_t batch_grid_size(int pairs_per_thread, int stage, int *grid);
+int64_t tiles_of(const RayGrid &r, int pairs_per_thread);
 cudaError_t launch_shoot_fp64(const ShootArgs &a, cudaStream_t s);
 cudaError_t launch_trace_fp64(const float4 *stars, int64_t nstars, const LensTerms &lens, const double2 *theta,
                               double2 *beta, int64_t k, cudaStream_t s);
@@ -79,3 +96,16 @@ RayGrid make_ray_grid(const mlens_grid &g);
 LensTerms make_lens_terms(double kc, double g1, double g2);
 
 }  // namespace mlens
+
+// A star field on one device (definition shared by the API translation units).
+struct mlens_ctx {
+    int device = -1;
+    int64_t n = 0;          // stars given
+    int64_t n_pad = 0;      // stars on the device (multiple of kStarPad)
+    float4 *d_stars = nullptr;
+    unsigned long long *d_stats = nullptr;  // [binned, out, nan]
+    mlens::LensTerms lens{};
+    int precision = MLENS_PREC_FP32;
+    int pairs_per_thread = 4;
+    int star_stage = 256;
+};

@@ -1,26 +1,29 @@
 // shoot_fp32.cu -- the FP32 direct-sum ray-shooting kernels (Algorithm 1 with
 // the deflection of Eq. 3 and the source position of Eq. 2), fused with the
-// binning step.
+// binning step, for one field (a grid of tiles) and for many fields (one
+// persistent launch over a work queue of (field, tile) items).
 //
 // One CTA of 256 threads owns a 64 x (8*NP) tile of the ray grid; each thread
 // owns 2*NP rays of one grid column, processed as NP packed pairs with the
 // Blackwell f32x2 instructions (FADD2/FMUL2/FFMA2), so one instruction serves
-// two rays.  Stars stream through shared memory in stages of 256; each stage
-// is re-centred on the tile (star minus tile centre, once per star per CTA) and
+// two rays.  Stars stream through shared memory in stages of SC; each stage is
+// re-centred on the tile (star minus tile centre, once per star per CTA) and
 // stored duplicated as (-dx,-dx,-dy,-dy),(m,m) so that a single broadcast
 // LDS.128 + LDS.64 feeds every packed pair.  Per star and ray the work is
 // FADD, FFMA (r^2), MUFU.RCP, FMUL (m/r^2), 2 FFMA (accumulate): the MUFU
 // reciprocal (16 per SM per clock) is the only unit near saturation.
 //
 // Precision (MLENS_PREC_FP32): rays and stars are relative to an FP32 tile
-// centre c, so differences of nearby positions are exact and the summed terms
-// carry no absolute-coordinate rounding.  Terms are accumulated in plain FP32
-// over 32 stars and each 32-star partial is added to the running sum with
-// Kahan compensation.  The smooth+shear part A c of the tile centre is formed
-// in FP64 once per tile, and beta = A c + A delta - S is assembled as a float
-// pair, so the only rounding left at the full coordinate scale is the exact
-// binning rule's.  MLENS_PREC_FP32_NAIVE keeps absolute coordinates and one
-// running FP32 sum (Algorithm 1 written in single precision).
+// centre c, so differences of nearby positions carry no absolute-coordinate
+// rounding.  Terms are accumulated in plain FP32 over 32 stars and each 32-star
+// partial is added to the running sum with Kahan compensation.  The
+// smooth+shear part A c of the tile centre is formed in FP64 once per tile, and
+// beta = A c + A delta - S is assembled as a float pair, so the only rounding
+// left at the full coordinate scale is the exact binning rule's.  The stage
+// size SC does not change the arithmetic (the 32-star chunks are the same), the
+// tile shape NP does (it moves the tile centres).
+// MLENS_PREC_FP32_NAIVE keeps absolute coordinates and one running FP32 sum
+// (Algorithm 1 written in single precision).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -31,21 +34,26 @@ namespace mlens {
 constexpr int kThreads = 256;
 constexpr int kTileX = 64;                 // rays per tile row = threads per row group
 constexpr int kGroups = kThreads / kTileX; // row groups
-constexpr int kStage = 256;                // stars per shared-memory stage (one per thread)
 constexpr int kKahan = 32;                 // stars per compensated partial
 
-static_assert(kStage == kThreads, "one star per thread per stage");
-static_assert(kStage % kKahan == 0, "stage must hold whole Kahan chunks");
-static_assert(kStarPad % kStage == 0, "star padding must be whole stages");
+static_assert(kStarPad % kKahan == 0, "star padding must be whole Kahan chunks");
 
+template <int SC>
 struct StarStage {
-    float4 q[2][kStage];   // (-dx, -dx, -dy, -dy) relative to the tile centre
-    float2 mm[2][kStage];  // (m, m)
+    float4 q[2][SC];   // (-dx, -dx, -dy, -dy) relative to the tile centre
+    float2 mm[2][SC];  // (m, m)
 };
 
+template <int SC>
 union ShootSmem {
-    StarStage st;
+    StarStage<SC> st;
     uint32_t hist[kWin * kWin];
+};
+
+struct TileShared {
+    float tc[8];       // cx, cy, ex, ey, B0h.x, B0h.y, B0l.x, B0l.y
+    int win[2];
+    unsigned sred[3];
 };
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
@@ -62,20 +70,20 @@ __device__ __forceinline__ void kahan2(float2 &S, float2 &C, float2 v)
     S = t;
 }
 
-template <int NP, bool NAIVE>
-__global__ void __launch_bounds__(kThreads, 2) k_shoot_fp32(ShootArgs a)
-{
-    constexpr int kTileY = kGroups * 2 * NP;
-    __shared__ __align__(16) ShootSmem sm;
-    __shared__ float tc[8];        // cx, cy, ex, ey, B0h.x, B0h.y, B0l.x, B0l.y
-    __shared__ int win[2];
-    __shared__ unsigned sred[3];
+constexpr int tile_rows(int np) { return kGroups * 2 * np; }
 
+// One tile (bx, by) of the ray grid of `a`, start to finish: prologue, star
+// stages, beta, binning, counters.  Every thread of the CTA must call it.
+template <int NP, int SC, bool NAIVE>
+__device__ __forceinline__ void shoot_tile(const ShootArgs &a, int bx, int by, ShootSmem<SC> &sm, TileShared &ts)
+{
+    constexpr int kTileY = tile_rows(NP);
+    constexpr int kLoads = (SC + kThreads - 1) / kThreads;
     const int tid = threadIdx.x;
     const int tx = tid % kTileX;
     const int tg = tid / kTileX;
-    const int i0 = blockIdx.x * kTileX;
-    const int j0 = blockIdx.y * kTileY;
+    const int i0 = bx * kTileX;
+    const int j0 = by * kTileY;
     const RayGrid &R = a.rays;
 
     if (tid == 0) {
@@ -87,19 +95,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_shoot_fp32(ShootArgs a)
             float cx = (float)cxd, cy = (float)cyd;
             double ex = (R.x0 + ((double)i0 + 0.5) * R.dx) - (double)cx;
             double ey = (R.y0 + ((double)j0 + 0.5) * R.dy) - (double)cy;
-            double bx = a.lens.a11 * (double)cx + a.lens.a12 * (double)cy;
-            double by = a.lens.a12 * (double)cx + a.lens.a22 * (double)cy;
-            float bxh = (float)bx, byh = (float)by;
-            tc[0] = cx;
-            tc[1] = cy;
-            tc[2] = (float)ex;
-            tc[3] = (float)ey;
-            tc[4] = bxh;
-            tc[5] = byh;
-            tc[6] = (float)(bx - (double)bxh);
-            tc[7] = (float)(by - (double)byh);
+            double bxd = a.lens.a11 * (double)cx + a.lens.a12 * (double)cy;
+            double byd = a.lens.a12 * (double)cx + a.lens.a22 * (double)cy;
+            float bxh = (float)bxd, byh = (float)byd;
+            ts.tc[0] = cx;
+            ts.tc[1] = cy;
+            ts.tc[2] = (float)ex;
+            ts.tc[3] = (float)ey;
+            ts.tc[4] = bxh;
+            ts.tc[5] = byh;
+            ts.tc[6] = (float)(bxd - (double)bxh);
+            ts.tc[7] = (float)(byd - (double)byh);
         }
-        sred[0] = sred[1] = sred[2] = 0u;
+        ts.sred[0] = ts.sred[1] = ts.sred[2] = 0u;
     }
     __syncthreads();
 
@@ -111,15 +119,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_shoot_fp32(ShootArgs a)
     const float kx = (float)tx;
     float cx = 0.f, cy = 0.f;
     if (!NAIVE) {
-        cx = tc[0];
-        cy = tc[1];
-        float dxr = __fmaf_rn(kx, R.dxh, __fmaf_rn(kx, R.dxl, tc[2]));
+        cx = ts.tc[0];
+        cy = ts.tc[1];
+        float dxr = __fmaf_rn(kx, R.dxh, __fmaf_rn(kx, R.dxl, ts.tc[2]));
         rx = f2(dxr, dxr);
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
             float k0 = (float)(tg * 2 * NP + 2 * p), k1 = k0 + 1.0f;
-            ry[p] = f2(__fmaf_rn(k0, R.dyh, __fmaf_rn(k0, R.dyl, tc[3])),
-                       __fmaf_rn(k1, R.dyh, __fmaf_rn(k1, R.dyl, tc[3])));
+            ry[p] = f2(__fmaf_rn(k0, R.dyh, __fmaf_rn(k0, R.dyl, ts.tc[3])),
+                       __fmaf_rn(k1, R.dyh, __fmaf_rn(k1, R.dyl, ts.tc[3])));
             px[p] = py[p] = Sx[p] = Sy[p] = Cx[p] = Cy[p] = f2(0.f, 0.f);
         }
     } else {
@@ -135,28 +143,49 @@ __global__ void __launch_bounds__(kThreads, 2) k_shoot_fp32(ShootArgs a)
             // alpha_0 first (Algorithm 1), then every star is added to it
             px[p] = f2(a.lens.fm11 * thx + a.lens.fm12 * y0, a.lens.fm11 * thx + a.lens.fm12 * y1);
             py[p] = f2(a.lens.fm12 * thx + a.lens.fm22 * y0, a.lens.fm12 * thx + a.lens.fm22 * y1);
+            Sx[p] = Sy[p] = Cx[p] = Cy[p] = f2(0.f, 0.f);
         }
     }
 
     // ---------------------------------------------------------- star stages
-    const int nstage = (int)(a.nstars / kStage);
-    auto stage_store = [&](int buf, float4 q) {
-        float nx = NAIVE ? -q.x : __fsub_rn(cx, q.x);
-        float ny = NAIVE ? -q.y : __fsub_rn(cy, q.y);
-        sm.st.q[buf][tid] = make_float4(nx, nx, ny, ny);
-        sm.st.mm[buf][tid] = f2(q.z, q.z);
+    const int64_t nst = a.nstars;  // multiple of kKahan
+    const int nstage = (int)((nst + SC - 1) / SC);
+    float4 nxt[kLoads];
+    auto stage_load = [&](int s) {
+        const int64_t base = (int64_t)s * SC;
+#pragma unroll
+        for (int l = 0; l < kLoads; ++l) {
+            const int k = tid + l * kThreads;
+            nxt[l] = (k < SC && base + k < nst) ? __ldg(&a.stars[base + k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     };
-    if (nstage > 0) stage_store(0, __ldg(&a.stars[tid]));
+    auto stage_store = [&](int buf) {
+#pragma unroll
+        for (int l = 0; l < kLoads; ++l) {
+            const int k = tid + l * kThreads;
+            if (k < SC) {
+                const float4 q = nxt[l];
+                float nx = NAIVE ? -q.x : __fsub_rn(cx, q.x);
+                float ny = NAIVE ? -q.y : __fsub_rn(cy, q.y);
+                sm.st.q[buf][k] = make_float4(nx, nx, ny, ny);
+                sm.st.mm[buf][k] = f2(q.z, q.z);
+            }
+        }
+    };
+    if (nstage > 0) {
+        stage_load(0);
+        stage_store(0);
+    }
     __syncthreads();
 
     for (int s = 0; s < nstage; ++s) {
         const int buf = s & 1;
-        float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (s + 1 < nstage) nxt = __ldg(&a.stars[(int64_t)(s + 1) * kStage + tid]);
+        const int cnt = (int)min((int64_t)SC, nst - (int64_t)s * SC);
+        if (s + 1 < nstage) stage_load(s + 1);
         const float4 *Q = sm.st.q[buf];
         const float2 *M = sm.st.mm[buf];
 #pragma unroll 1
-        for (int k0 = 0; k0 < kStage; k0 += kKahan) {
+        for (int k0 = 0; k0 < cnt; k0 += kKahan) {
 #pragma unroll
             for (int k = k0; k < k0 + kKahan; ++k) {
                 const float4 q = Q[k];
@@ -183,7 +212,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_shoot_fp32(ShootArgs a)
                 }
             }
         }
-        if (s + 1 < nstage) stage_store(buf ^ 1, nxt);
+        if (s + 1 < nstage) stage_store(buf ^ 1);
         __syncthreads();
     }
 
@@ -202,11 +231,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_shoot_fp32(ShootArgs a)
                 const float lx = __fmaf_rn(a.lens.fa11, dxr, __fmul_rn(a.lens.fa12, dyr));
                 const float ly = __fmaf_rn(a.lens.fa12, dxr, __fmul_rn(a.lens.fa22, dyr));
                 float th, tl;
-                two_sum(tc[4], -sx, th, tl);
-                tl = __fadd_rn(tl, __fadd_rn(__fadd_rn(tc[6], ccx), lx));
+                two_sum(ts.tc[4], -sx, th, tl);
+                tl = __fadd_rn(tl, __fadd_rn(__fadd_rn(ts.tc[6], ccx), lx));
                 two_sum(th, tl, bxh[r], bxl[r]);
-                two_sum(tc[5], -sy, th, tl);
-                tl = __fadd_rn(tl, __fadd_rn(__fadd_rn(tc[7], ccy), ly));
+                two_sum(ts.tc[5], -sy, th, tl);
+                tl = __fadd_rn(tl, __fadd_rn(__fadd_rn(ts.tc[7], ccy), ly));
                 two_sum(th, tl, byh[r], byl[r]);
             } else {
                 const float thy = h ? ry[p].y : ry[p].x;
@@ -224,11 +253,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_shoot_fp32(ShootArgs a)
     __syncthreads();  // star stages are dead: reuse the memory as the window
     for (int b = tid; b < kWin * kWin; b += kThreads) sm.hist[b] = 0u;
     if (tid == 0) {
-        win[0] = pair_axis_rough(bxh[0], a.bin.ax) - kWin / 2;
-        win[1] = pair_axis_rough(byh[0], a.bin.ay) - kWin / 2;
+        ts.win[0] = pair_axis_rough(bxh[0], a.bin.ax) - kWin / 2;
+        ts.win[1] = pair_axis_rough(byh[0], a.bin.ay) - kWin / 2;
     }
     __syncthreads();
-    WinHist W{sm.hist, win[0], win[1]};
+    WinHist W{sm.hist, ts.win[0], ts.win[1]};
     unsigned nb = 0, no = 0, nn = 0;
 #pragma unroll
     for (int r = 0; r < 2 * NP; ++r) {
@@ -254,23 +283,125 @@ __global__ void __launch_bounds__(kThreads, 2) k_shoot_fp32(ShootArgs a)
     }
     __syncthreads();
     hist_flush(W, a.bin, a.counts);
-    stats_add_block(nb, no, nn, sred, a.stats);
+    stats_add_block(nb, no, nn, ts.sred, a.stats);
 }
 
-template <int NP, bool NAIVE>
+template <int NP, int SC, bool NAIVE>
+__global__ void __launch_bounds__(kThreads, 2) k_shoot_fp32(ShootArgs a)
+{
+    __shared__ __align__(16) ShootSmem<SC> sm;
+    __shared__ TileShared ts;
+    shoot_tile<NP, SC, NAIVE>(a, blockIdx.x, blockIdx.y, sm, ts);
+}
+
+// Persistent kernel over many fields: CTAs pull (field, tile) items from one
+// atomic counter until the queue is empty.  Items are numbered field by field in
+// the order `order` (heaviest field first, so the tail is made of light items);
+// begin[k] is the first item of the k-th field in that order (begin[nf] = total).
+template <int NP, int SC>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_shoot_batch(const ShootArgs *fields, const int *order, const int64_t *begin, int nf, int64_t total,
+                  unsigned long long *counter)
+{
+    __shared__ __align__(16) ShootSmem<SC> sm;
+    __shared__ TileShared ts;
+    __shared__ long long s_item;
+    for (;;) {
+        __syncthreads();  // everyone has finished with the previous item number
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= total) break;
+        int lo = 0, hi = nf - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (begin[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const ShootArgs &A = fields[order[lo]];
+        const int64_t t = item - begin[lo];
+        const int tiles_x = (A.rays.nx + kTileX - 1) / kTileX;
+        shoot_tile<NP, SC, false>(A, (int)(t % tiles_x), (int)(t / tiles_x), sm, ts);
+    }
+}
+
+template <int NP, int SC, bool NAIVE>
 static cudaError_t launch_t(const ShootArgs &a, cudaStream_t s)
 {
-    constexpr int kTileY = kGroups * 2 * NP;
-    dim3 grid((unsigned)((a.rays.nx + kTileX - 1) / kTileX), (unsigned)((a.rays.ny + kTileY - 1) / kTileY));
+    dim3 grid((unsigned)((a.rays.nx + kTileX - 1) / kTileX), (unsigned)((a.rays.ny + tile_rows(NP) - 1) / tile_rows(NP)));
     if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
-    k_shoot_fp32<NP, NAIVE><<<grid, kThreads, 0, s>>>(a);
+    k_shoot_fp32<NP, SC, NAIVE><<<grid, kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_shoot_fp32(const ShootArgs &a, int pairs_per_thread, bool naive, cudaStream_t s)
+template <bool NAIVE>
+static cudaError_t launch_sel(const ShootArgs &a, int np, int sc, cudaStream_t s)
 {
-    if (naive) return pairs_per_thread == 2 ? launch_t<2, true>(a, s) : launch_t<4, true>(a, s);
-    return pairs_per_thread == 2 ? launch_t<2, false>(a, s) : launch_t<4, false>(a, s);
+    if (np == 2) {
+        if (sc == 128) return launch_t<2, 128, NAIVE>(a, s);
+        if (sc == 512) return launch_t<2, 512, NAIVE>(a, s);
+        return launch_t<2, 256, NAIVE>(a, s);
+    }
+    if (sc == 128) return launch_t<4, 128, NAIVE>(a, s);
+    if (sc == 512) return launch_t<4, 512, NAIVE>(a, s);
+    return launch_t<4, 256, NAIVE>(a, s);
+}
+
+cudaError_t launch_shoot_fp32(const ShootArgs &a, int pairs_per_thread, bool naive, cudaStream_t s, int stage)
+{
+    return naive ? launch_sel<true>(a, pairs_per_thread, stage, s) : launch_sel<false>(a, pairs_per_thread, stage, s);
+}
+
+int64_t tiles_of(const RayGrid &r, int pairs_per_thread)
+{
+    const int ty = tile_rows(pairs_per_thread);
+    return (int64_t)((r.nx + kTileX - 1) / kTileX) * (int64_t)((r.ny + ty - 1) / ty);
+}
+
+template <int NP, int SC>
+static cudaError_t grid_b(int *grid)
+{
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shoot_batch<NP, SC>, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    *grid = nsm * (per_sm > 0 ? per_sm : 1);
+    return cudaSuccess;
+}
+
+cudaError_t batch_grid_size(int pairs_per_thread, int stage, int *grid)
+{
+    if (pairs_per_thread == 2) {
+        if (stage == 128) return grid_b<2, 128>(grid);
+        if (stage == 512) return grid_b<2, 512>(grid);
+        return grid_b<2, 256>(grid);
+    }
+    if (stage == 128) return grid_b<4, 128>(grid);
+    if (stage == 512) return grid_b<4, 512>(grid);
+    return grid_b<4, 256>(grid);
+}
+
+template <int NP, int SC>
+static cudaError_t launch_b(const BatchLaunch &b, cudaStream_t s)
+{
+    const int64_t want = b.grid > 0 ? b.grid : 1;
+    const unsigned grid = (unsigned)(b.total < want ? (b.total > 0 ? b.total : 1) : want);
+    k_shoot_batch<NP, SC><<<grid, kThreads, 0, s>>>(b.fields, b.order, b.begin, b.nfields, b.total, b.counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shoot_batch(const BatchLaunch &b, int pairs_per_thread, int stage, cudaStream_t s)
+{
+    if (pairs_per_thread == 2) {
+        if (stage == 128) return launch_b<2, 128>(b, s);
+        if (stage == 512) return launch_b<2, 512>(b, s);
+        return launch_b<2, 256>(b, s);
+    }
+    if (stage == 128) return launch_b<4, 128>(b, s);
+    if (stage == 512) return launch_b<4, 512>(b, s);
+    return launch_b<4, 256>(b, s);
 }
 
 }  // namespace mlens

@@ -72,10 +72,11 @@ __global__ void __launch_bounds__(kT64) k_fp64(ShootArgs a, const double2 *theta
     double sx = __dadd_rn(__dmul_rn(__dadd_rn(kc, g1), tx), __dmul_rn(g2, ty));
     double sy = __dadd_rn(__dmul_rn(g2, tx), __dmul_rn(__dsub_rn(kc, g1), ty));
     for (int64_t s0 = 0; s0 < a.nstars; s0 += kT64) {
+        const int cnt = (int)min((int64_t)kT64, a.nstars - s0);
         __syncthreads();
-        sq[tid] = a.stars[s0 + tid];  // nstars is a multiple of kStarPad >= kT64
+        if (tid < cnt) sq[tid] = a.stars[s0 + tid];
         __syncthreads();
-        alpha_fp64(tx, ty, sq, kT64, sx, sy);
+        alpha_fp64(tx, ty, sq, cnt, sx, sy);
     }
     const double bx = __dsub_rn(tx, sx), by = __dsub_rn(ty, sy);
     if (!GRID) {
@@ -101,7 +102,6 @@ __global__ void __launch_bounds__(kT64) k_fp64(ShootArgs a, const double2 *theta
 
 cudaError_t launch_shoot_fp64(const ShootArgs &a, cudaStream_t s)
 {
-    static_assert(kStarPad % kT64 == 0, "star padding must be whole FP64 stages");
     dim3 grid((unsigned)((a.rays.nx + 31) / 32), (unsigned)((a.rays.ny + 3) / 4));
     if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
     k_fp64<true><<<grid, kT64, 0, s>>>(a, nullptr, nullptr, 0);

@@ -65,13 +65,20 @@ _dp = C.POINTER(C.c_double)
 SIGNATURES = {
     "mlens_create": (C.c_int, [C.POINTER(_vp), _dp, _dp, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int32]),
     "mlens_set_precision": (C.c_int, [_vp, C.c_int32]),
-    "mlens_set_tuning": (C.c_int, [_vp, C.c_int32]),
+    "mlens_set_tuning": (C.c_int, [_vp, C.c_int32, C.c_int32]),
     "mlens_shoot": (C.c_int, [_vp, _gp, _gp, _vp, C.c_uint32, _sp, _vp]),
     "mlens_shoot_beta": (C.c_int, [_vp, _gp, _gp, _vp, _vp, C.c_uint32, _sp, _vp]),
     "mlens_trace": (C.c_int, [_vp, _dp, C.c_int64, _dp, _vp]),
     "mlens_bin": (C.c_int, [_vp, C.c_int64, _gp, _vp, C.c_uint32, _sp, _vp]),
     "mlens_shoot_noalloc": (C.c_int, [_vp, C.c_int64, C.c_double, C.c_double, C.c_double, _gp, _gp, _vp, C.c_uint32,
                                       _sp, _vp]),
+    "mlens_batch_create": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int32, _gp, _gp, C.POINTER(_vp),
+                                     C.c_uint32]),
+    "mlens_batch_set_tuning": (C.c_int, [_vp, C.c_int32, C.c_int32]),
+    "mlens_batch_tune": (C.c_int, [_vp, _vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
+    "mlens_batch_run": (C.c_int, [_vp, _sp, _vp]),
+    "mlens_batch_destroy": (None, [_vp]),
+    "mlens_shoot_batch": (C.c_int, [C.POINTER(_vp), C.c_int32, _gp, _gp, C.POINTER(_vp), C.c_uint32, _sp, _vp]),
     "mlens_destroy": (None, [_vp]),
     "mlens_last_error": (C.c_char_p, []),
     "mlens_version": (C.c_int, []),
@@ -179,8 +186,8 @@ def mlens_set_precision(ctx: Ctx, precision):
     _check(load().mlens_set_precision(ctx.handle, int(precision)))
 
 
-def mlens_set_tuning(ctx: Ctx, rays_per_thread: int):
-    _check(load().mlens_set_tuning(ctx.handle, int(rays_per_thread)))
+def mlens_set_tuning(ctx: Ctx, rays_per_thread: int, star_stage: int = 0):
+    _check(load().mlens_set_tuning(ctx.handle, int(rays_per_thread), int(star_stage)))
 
 
 def mlens_shoot(ctx: Ctx, rays, src, counts, flags: int = 0, stats: bool = False, stream=None):
@@ -224,6 +231,71 @@ def mlens_shoot_noalloc(stars, n: int, kappa_c: float, gamma1: float, gamma2: fl
                                       C.byref(g), C.byref(s), _dev_ptr(counts), int(flags),
                                       C.byref(st) if stats else None, _stream_ptr(stream)))
     return st.asdict() if stats else None
+
+
+class Batch:
+    """Owns one mlens_batch* (and keeps its contexts and maps referenced)."""
+
+    def __init__(self, handle: int, keep):
+        self.handle = C.c_void_p(handle)
+        self._keep = keep
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def close(self):
+        if self.handle and self.handle.value:
+            load().mlens_batch_destroy(self.handle)
+            self.handle = C.c_void_p(0)
+
+
+def _batch_arrays(ctxs, rays, srcs, counts):
+    nf = len(ctxs)
+    if not (len(rays) == len(srcs) == len(counts) == nf):
+        raise ValueError("ctxs, rays, srcs and counts must have one entry per field")
+    cx = (_vp * nf)(*[c.handle.value for c in ctxs])
+    ga = (mlens_grid * nf)(*[grid(g) for g in rays])
+    sa = (mlens_grid * nf)(*[grid(g) for g in srcs])
+    pa = (_vp * nf)(*[_dev_ptr(t).value for t in counts])
+    return nf, cx, ga, sa, pa
+
+
+def mlens_batch_create(ctxs, rays, srcs, counts, flags: int = 0) -> Batch:
+    nf, cx, ga, sa, pa = _batch_arrays(ctxs, rays, srcs, counts)
+    h = C.c_void_p(0)
+    _check(load().mlens_batch_create(C.byref(h), cx, nf, ga, sa, pa, int(flags)))
+    return Batch(h.value, (list(ctxs), list(counts)))
+
+
+def mlens_batch_set_tuning(b: Batch, rays_per_thread: int, star_stage: int = 0):
+    _check(load().mlens_batch_set_tuning(b.handle, int(rays_per_thread), int(star_stage)))
+
+
+def mlens_batch_tune(b: Batch, stream=None):
+    r, s, ms = C.c_int32(0), C.c_int32(0), C.c_double(0.0)
+    _check(load().mlens_batch_tune(b.handle, _stream_ptr(stream), C.byref(r), C.byref(s), C.byref(ms)))
+    return int(r.value), int(s.value), float(ms.value)
+
+
+def mlens_batch_run(b: Batch, stats: bool = False, stream=None):
+    nf = len(b._keep[0])
+    st = (mlens_stats * nf)()
+    _check(load().mlens_batch_run(b.handle, st if stats else None, _stream_ptr(stream)))
+    return [x.asdict() for x in st] if stats else None
+
+
+def mlens_batch_destroy(b: Batch):
+    b.close()
+
+
+def mlens_shoot_batch(ctxs, rays, srcs, counts, flags: int = 0, stats: bool = False, stream=None):
+    nf, cx, ga, sa, pa = _batch_arrays(ctxs, rays, srcs, counts)
+    st = (mlens_stats * nf)()
+    _check(load().mlens_shoot_batch(cx, nf, ga, sa, pa, int(flags), st if stats else None, _stream_ptr(stream)))
+    return [x.asdict() for x in st] if stats else None
 
 
 def mlens_destroy(ctx: Ctx):
