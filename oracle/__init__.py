@@ -26,6 +26,10 @@ _lock = threading.Lock()
 _lib = None
 
 
+class OrcCells(C.Structure):
+    _fields_ = [("x0", C.c_double), ("y0", C.c_double), ("w", C.c_double), ("n", C.c_int32)]
+
+
 class OrcGrid(C.Structure):
     _fields_ = [("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double),
                 ("nx", C.c_int32), ("ny", C.c_int32)]
@@ -58,6 +62,10 @@ def _load(path: str):
                                   C.c_int]
     L.orc_alpha_jacobian.argtypes = [dp, C.c_int64, dp, dp, C.c_int64, C.c_double, C.c_double, C.c_double, dp,
                                      C.c_int]
+    cp = C.POINTER(OrcCells)
+    L.orc_cell_index.argtypes = [dp, C.c_int64, cp, ip]
+    L.orc_split_alpha.argtypes = [dp, ip, C.c_int64, dp, dp, C.c_int64, cp, dp, dp, C.c_int]
+    L.orc_local_coeffs.argtypes = [ip, C.c_int64, C.c_int32, C.c_double, dp, dp, C.c_int64, cp, dp, C.c_int]
     L.orc_pixels.argtypes = [dp, C.c_int64, gp, ip]
     L.orc_ray_theta.argtypes = [gp, ip, C.c_int64, dp]
     L.orc_shoot.argtypes = [gp, gp, dp, dp, C.c_int64, C.c_double, C.c_double, C.c_double, up, u64p, C.c_int]
@@ -234,3 +242,38 @@ def pair_pixels(beta4: np.ndarray, src) -> np.ndarray:
     lib().orc_pair_pixels(b.ctypes.data_as(C.POINTER(C.c_float)), b.shape[0], C.byref(s),
                           out.ctypes.data_as(C.POINTER(C.c_int64)))
     return out
+
+
+# ----------------------------------------------------------------- cells
+def cells(x0: float, y0: float, w: float, n: int) -> OrcCells:
+    return OrcCells(float(x0), float(y0), float(w), int(n))
+
+
+def cell_index(xy: np.ndarray, c: OrcCells) -> np.ndarray:
+    a, pa = _d(np.asarray(xy).reshape(-1, 2))
+    out = np.empty(a.shape[0], dtype=np.int64)
+    lib().orc_cell_index(pa, a.shape[0], C.byref(c), out.ctypes.data_as(C.POINTER(C.c_int64)))
+    return out
+
+
+def split_alpha(theta: np.ndarray, ray_cell: np.ndarray, field, c: OrcCells, nthreads: int = 0):
+    """(near, far) star terms of Eq. (3) at theta for rays in the given cells."""
+    th, pth = _d(np.asarray(theta).reshape(-1, 2))
+    rc = np.ascontiguousarray(ray_cell, dtype=np.int64)
+    xy, pxy, m, pm = _stars(field)
+    near = np.empty_like(th)
+    far = np.empty_like(th)
+    lib().orc_split_alpha(pth, rc.ctypes.data_as(C.POINTER(C.c_int64)), th.shape[0], pxy, pm, field.n, C.byref(c),
+                          near.ctypes.data_as(C.POINTER(C.c_double)), far.ctypes.data_as(C.POINTER(C.c_double)),
+                          int(nthreads))
+    return near, far
+
+
+def local_coeffs(cell_ids: np.ndarray, P: int, scale: float, field, c: OrcCells, nthreads: int = 0) -> np.ndarray:
+    """Complex coefficients (ncell, P+1) of the far field's local expansion in (z - z_c)/scale."""
+    ids = np.ascontiguousarray(cell_ids, dtype=np.int64)
+    xy, pxy, m, pm = _stars(field)
+    out = np.empty((ids.shape[0], P + 1, 2))
+    lib().orc_local_coeffs(ids.ctypes.data_as(C.POINTER(C.c_int64)), ids.shape[0], int(P), float(scale), pxy, pm,
+                           field.n, C.byref(c), out.ctypes.data_as(C.POINTER(C.c_double)), int(nthreads))
+    return out[..., 0] + 1j * out[..., 1]

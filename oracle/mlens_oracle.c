@@ -131,6 +131,116 @@ void orc_alpha_jacobian(const double *theta, int64_t k, const double *xy, const 
     }
 }
 
+/* ------------------------------------------------ cells: near and far stars */
+/* The learned-far-field variant splits the lens plane into a grid of square
+ * cells; for a ray in cell c the "near" stars are those in the 3 x 3 block of
+ * cells around c (clipped to the grid) and every other star (including stars
+ * outside the grid) is "far".  Cell (ix, iy) covers
+ * [x0 + ix w, x0 + (ix+1) w) x [y0 + iy w, y0 + (iy+1) w), w = (x1 - x0)/n. */
+typedef struct {
+    double x0, y0, w;
+    int32_t n;
+} orc_cells;
+
+static int64_t cell_index(double x, double y, const orc_cells *c)
+{
+    double fx = floor((x - c->x0) / c->w), fy = floor((y - c->y0) / c->w);
+    if (!(fx >= 0.0 && fx < (double)c->n && fy >= 0.0 && fy < (double)c->n)) return -1;
+    return (int64_t)fy * c->n + (int64_t)fx;
+}
+
+void orc_cell_index(const double *xy, int64_t k, const orc_cells *c, int64_t *out)
+{
+    for (int64_t r = 0; r < k; ++r) out[r] = cell_index(xy[2 * r], xy[2 * r + 1], c);
+}
+
+static int is_near(int64_t star_cell, int64_t ray_cell, int32_t n)
+{
+    if (star_cell < 0 || ray_cell < 0) return 0;
+    int64_t sx = star_cell % n, sy = star_cell / n, rx = ray_cell % n, ry = ray_cell / n;
+    return (sx - rx <= 1 && rx - sx <= 1 && sy - ry <= 1 && ry - sy <= 1);
+}
+
+/* Star term of Eq. (3) at theta split by the cell rule: out_near and out_far
+ * (either may be NULL), both k x 2.  ray_cell[r] is the cell the ray belongs to. */
+void orc_split_alpha(const double *theta, const int64_t *ray_cell, int64_t k, const double *xy, const double *m,
+                     int64_t n, const orc_cells *c, double *out_near, double *out_far, int nthreads)
+{
+    int64_t *scell = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t s = 0; s < n; ++s) scell[s] = cell_index(xy[2 * s], xy[2 * s + 1], c);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t r = 0; r < k; ++r) {
+        double tx = theta[2 * r], ty = theta[2 * r + 1];
+        double nx = 0.0, ny = 0.0, fx = 0.0, fy = 0.0;
+        for (int64_t s = 0; s < n; ++s) {
+            double dx = tx - xy[2 * s];
+            double dy = ty - xy[2 * s + 1];
+            double r2 = dx * dx + dy * dy;
+            double ax = m[s] * dx / r2, ay = m[s] * dy / r2;
+            if (is_near(scell[s], ray_cell[r], c->n)) {
+                nx += ax;
+                ny += ay;
+            } else {
+                fx += ax;
+                fy += ay;
+            }
+        }
+        if (out_near) {
+            out_near[2 * r] = nx;
+            out_near[2 * r + 1] = ny;
+        }
+        if (out_far) {
+            out_far[2 * r] = fx;
+            out_far[2 * r + 1] = fy;
+        }
+    }
+    free(scell);
+}
+
+/* Local (Taylor) expansion of the far field of each listed cell about its
+ * centre z_c.  With z = x + i y, the star term of Eq. (3) is the complex
+ * conjugate of F(z) = sum_k m_k / (z - z_k), holomorphic away from the stars;
+ * for the far stars of cell c,
+ *     F(z) = sum_{p>=0} a_p (z - z_c)^p,   a_p = - sum_far m_k / (z_k - z_c)^(p+1).
+ * out[(cell i, p)] = (Re a_p, Im a_p) scaled by s^p (s = scale): the coefficients
+ * of the series in (z - z_c)/s.  FP64, stars in input order. */
+void orc_local_coeffs(const int64_t *cells, int64_t ncell, int32_t P, double scale, const double *xy,
+                      const double *m, int64_t n, const orc_cells *c, double *out, int nthreads)
+{
+    int64_t *scell = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t s = 0; s < n; ++s) scell[s] = cell_index(xy[2 * s], xy[2 * s + 1], c);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t i = 0; i < ncell; ++i) {
+        int64_t cc = cells[i];
+        double zx = c->x0 + ((double)(cc % c->n) + 0.5) * c->w;
+        double zy = c->y0 + ((double)(cc / c->n) + 0.5) * c->w;
+        double *o = out + (size_t)i * 2 * (size_t)(P + 1);
+        for (int32_t p = 0; p <= P; ++p) o[2 * p] = o[2 * p + 1] = 0.0;
+        for (int64_t s = 0; s < n; ++s) {
+            if (is_near(scell[s], cc, c->n)) continue;
+            /* w = scale / (z_k - z_c); term_p = -m w^(p+1) / scale */
+            double dx = xy[2 * s] - zx, dy = xy[2 * s + 1] - zy;
+            double d2 = dx * dx + dy * dy;
+            double wr = scale * dx / d2, wi = -scale * dy / d2;
+            double tr = -m[s] * wr / scale, ti = -m[s] * wi / scale;
+            for (int32_t p = 0; p <= P; ++p) {
+                o[2 * p] += tr;
+                o[2 * p + 1] += ti;
+                double nr = tr * wr - ti * wi, ni = tr * wi + ti * wr;
+                tr = nr;
+                ti = ni;
+            }
+        }
+    }
+    free(scell);
+}
+
 /* ------------------------------------------------------ grid and binning */
 
 static double ray_x(const orc_grid *g, int64_t i) { return g->x0 + ((double)i + 0.5) * ((g->x1 - g->x0) / g->nx); }
