@@ -27,7 +27,7 @@ _lib = None
 
 
 class OrcCells(C.Structure):
-    _fields_ = [("x0", C.c_double), ("y0", C.c_double), ("w", C.c_double), ("n", C.c_int32)]
+    _fields_ = [("x0", C.c_double), ("y0", C.c_double), ("w", C.c_double), ("nx", C.c_int32), ("ny", C.c_int32)]
 
 
 class OrcGrid(C.Structure):
@@ -245,8 +245,9 @@ def pair_pixels(beta4: np.ndarray, src) -> np.ndarray:
 
 
 # ----------------------------------------------------------------- cells
-def cells(x0: float, y0: float, w: float, n: int) -> OrcCells:
-    return OrcCells(float(x0), float(y0), float(w), int(n))
+def cells(x0: float, y0: float, w: float, nx: int, ny: int = None) -> OrcCells:
+    """Square cells of width w: nx x ny of them from (x0, y0); index iy*nx + ix."""
+    return OrcCells(float(x0), float(y0), float(w), int(nx), int(nx if ny is None else ny))
 
 
 def cell_index(xy: np.ndarray, c: OrcCells) -> np.ndarray:

@@ -135,18 +135,18 @@ void orc_alpha_jacobian(const double *theta, int64_t k, const double *xy, const 
 /* The learned-far-field variant splits the lens plane into a grid of square
  * cells; for a ray in cell c the "near" stars are those in the 3 x 3 block of
  * cells around c (clipped to the grid) and every other star (including stars
- * outside the grid) is "far".  Cell (ix, iy) covers
- * [x0 + ix w, x0 + (ix+1) w) x [y0 + iy w, y0 + (iy+1) w), w = (x1 - x0)/n. */
+ * outside the grid) is "far".  Cell (ix, iy), 0 <= ix < nx, 0 <= iy < ny, covers
+ * [x0 + ix w, x0 + (ix+1) w) x [y0 + iy w, y0 + (iy+1) w); index iy*nx + ix. */
 typedef struct {
     double x0, y0, w;
-    int32_t n;
+    int32_t nx, ny;
 } orc_cells;
 
 static int64_t cell_index(double x, double y, const orc_cells *c)
 {
     double fx = floor((x - c->x0) / c->w), fy = floor((y - c->y0) / c->w);
-    if (!(fx >= 0.0 && fx < (double)c->n && fy >= 0.0 && fy < (double)c->n)) return -1;
-    return (int64_t)fy * c->n + (int64_t)fx;
+    if (!(fx >= 0.0 && fx < (double)c->nx && fy >= 0.0 && fy < (double)c->ny)) return -1;
+    return (int64_t)fy * c->nx + (int64_t)fx;
 }
 
 void orc_cell_index(const double *xy, int64_t k, const orc_cells *c, int64_t *out)
@@ -157,7 +157,7 @@ void orc_cell_index(const double *xy, int64_t k, const orc_cells *c, int64_t *ou
 static int is_near(int64_t star_cell, int64_t ray_cell, int32_t n)
 {
     if (star_cell < 0 || ray_cell < 0) return 0;
-    int64_t sx = star_cell % n, sy = star_cell / n, rx = ray_cell % n, ry = ray_cell / n;
+    int64_t sx = star_cell % n, sy = star_cell / n, rx = ray_cell % n, ry = ray_cell / n;  /* n = cells per row */
     return (sx - rx <= 1 && rx - sx <= 1 && sy - ry <= 1 && ry - sy <= 1);
 }
 
@@ -180,7 +180,7 @@ void orc_split_alpha(const double *theta, const int64_t *ray_cell, int64_t k, co
             double dy = ty - xy[2 * s + 1];
             double r2 = dx * dx + dy * dy;
             double ax = m[s] * dx / r2, ay = m[s] * dy / r2;
-            if (is_near(scell[s], ray_cell[r], c->n)) {
+            if (is_near(scell[s], ray_cell[r], c->nx)) {
                 nx += ax;
                 ny += ay;
             } else {
@@ -218,12 +218,12 @@ void orc_local_coeffs(const int64_t *cells, int64_t ncell, int32_t P, double sca
 #endif
     for (int64_t i = 0; i < ncell; ++i) {
         int64_t cc = cells[i];
-        double zx = c->x0 + ((double)(cc % c->n) + 0.5) * c->w;
-        double zy = c->y0 + ((double)(cc / c->n) + 0.5) * c->w;
+        double zx = c->x0 + ((double)(cc % c->nx) + 0.5) * c->w;
+        double zy = c->y0 + ((double)(cc / c->nx) + 0.5) * c->w;
         double *o = out + (size_t)i * 2 * (size_t)(P + 1);
         for (int32_t p = 0; p <= P; ++p) o[2 * p] = o[2 * p + 1] = 0.0;
         for (int64_t s = 0; s < n; ++s) {
-            if (is_near(scell[s], cc, c->n)) continue;
+            if (is_near(scell[s], cc, c->nx)) continue;
             /* w = scale / (z_k - z_c); term_p = -m w^(p+1) / scale */
             double dx = xy[2 * s] - zx, dy = xy[2 * s + 1] - zy;
             double d2 = dx * dx + dy * dy;

@@ -12,13 +12,14 @@ The network is a per-cell latent code z_c (32 numbers) plus one shared MLP
 silu(v) = v * sigma(v) with sigma(v) = (1 + tanh(v/2)) / 2, and
 silu'(v) = sigma(v) (1 + v (1 - sigma(v))).
 
-The GPU runs the two wide layers on BF16 tensor cores with FP32 accumulation.
-With `bf16=True` this reference rounds exactly the operands the GPU rounds to
-BF16 (round to nearest even): x, W1, a1 and W2 in the forward pass; dh2, W2 and
-dh1 (and the latent block of W1) in the backward pass.  Everything else stays
-in FP64 here.  The loss is mean over samples of |y - t|^2 (sum over the two
-outputs); its gradients are returned for every parameter and for each sample's
-latent.
+The GPU runs the latent block of layer 1 and layer 2 on BF16 tensor cores with
+FP32 accumulation; the position block of layer 1 (W1[:, 32:34] u) and layer 3
+stay in FP32 so that the position keeps full precision.  With `bf16=True` this
+reference rounds exactly the operands the GPU rounds to BF16 (round to nearest
+even): z, W1[:, :32], a1 and W2 in the forward pass; dh2, W2, dh1 and
+W1[:, :32] in the backward pass.  Everything else stays in FP64 here.  The loss
+is mean over samples of |y - t|^2 (sum over the two outputs); its gradients are
+returned for every parameter and for each sample's latent.
 """
 from __future__ import annotations
 
@@ -72,15 +73,17 @@ def init_params(rng: np.random.Generator):
 def forward(p, z, u, bf16: bool = True):
     """z (B,32), u (B,2) -> y (B,2) and the cache for backward."""
     R = bf16_round if bf16 else (lambda a: np.asarray(a, dtype=np.float64))
-    x = R(np.concatenate([z, u], axis=1))
-    W1 = R(p["W1"])
-    h1 = x @ W1.T + p["b1"]
+    zr = R(z)
+    W1z = R(p["W1"][:, :LATENT])
+    W1u = p["W1"][:, LATENT:]
+    h1 = zr @ W1z.T + u @ W1u.T + p["b1"]
     a1 = R(silu(h1))
     W2 = R(p["W2"])
     h2 = a1 @ W2.T + p["b2"]
     a2 = silu(h2)
     y = a2 @ p["W3"].T + p["b3"]
-    return y, dict(x=x, h1=h1, a1=a1, h2=h2, a2=a2, W1=W1, W2=W2)
+    x = np.concatenate([zr, np.asarray(u, dtype=np.float64)], axis=1)
+    return y, dict(x=x, h1=h1, a1=a1, h2=h2, a2=a2, W1z=W1z, W2=W2)
 
 
 def loss_and_grads(p, z, u, t, bf16: bool = True):
@@ -100,9 +103,10 @@ def loss_and_grads(p, z, u, t, bf16: bool = True):
     da1 = dh2r @ c["W2"]
     dh1 = da1 * dsilu(c["h1"])
     dh1r = R(dh1)
-    g["W1"] = dh1r.T @ c["x"]
+    # latent block through the tensor cores (rounded dh1), position block in FP32
+    g["W1"] = np.concatenate([dh1r.T @ c["x"][:, :LATENT], dh1.T @ c["x"][:, LATENT:]], axis=1)
     g["b1"] = dh1.sum(0)
-    g["z"] = dh1r @ R(p["W1"][:, :LATENT])
+    g["z"] = dh1r @ c["W1z"]
     return loss, g, y
 
 

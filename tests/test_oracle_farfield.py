@@ -18,7 +18,7 @@ def small_field(seed=1, n=3000, radius=12.0):
     return W.Field(xy=xy, m=m, kappa_c=0.1, gamma1=0.2, gamma2=-0.05)
 
 
-CELLS = oracle.cells(-8.0, -8.0, 0.5, 32)
+CELLS = oracle.cells(-8.0, -8.0, 0.5, 32, 32)
 
 
 def test_near_plus_far_is_the_star_term():
@@ -148,3 +148,17 @@ def test_adam_first_step_is_a_signed_lr_step():
     v = {"a": np.zeros(3)}
     mlp.adam_step(p, m, v, g, 1, lr=0.01)
     assert np.allclose(p["a"], [1.0 - 0.01 * 0.5 / (0.5 + 1e-8), -2.0 + 0.01 * 1e-3 / (1e-3 + 1e-8), 3.0])
+
+
+def test_rectangular_cell_grid_rule():
+    """nx != ny: index iy*nx + ix, near = within one cell in both axes, outside = far."""
+    c = oracle.cells(0.0, 0.0, 1.0, 5, 3)
+    pts = np.array([[0.5, 0.5], [4.5, 2.5], [4.5, 3.5], [5.0, 0.0], [2.2, 1.7]])
+    assert list(oracle.cell_index(pts, c)) == [0, 14, -1, -1, 7]
+    f = W.Field(xy=np.array([[2.5, 1.5], [4.5, 1.5], [0.5, 0.5]]), m=np.ones(3), kappa_c=0, gamma1=0, gamma2=0)
+    th = np.array([[3.5, 1.5]])
+    near, far = oracle.split_alpha(th, oracle.cell_index(th, c), f, c)
+    # stars at (2.5,1.5) and (4.5,1.5) are in neighbouring cells, (0.5,0.5) is two cells away
+    assert np.allclose(near[0], [1.0 / 1.0 - 1.0 / 1.0, 0.0], atol=1e-15)
+    d = np.array([3.0, 1.0])
+    assert np.allclose(far[0], d / (d @ d))
