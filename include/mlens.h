@@ -255,6 +255,112 @@ void mlens_batch_destroy(mlens_batch *b);
 int mlens_shoot_batch(mlens_ctx *const *ctxs, int32_t nfields, const mlens_grid *rays, const mlens_grid *srcs,
                       uint32_t *const *counts_dev, uint32_t flags, mlens_stats *stats_host, void *stream);
 
+/* ------------------------------------------------- learned far field */
+/*
+ * The direct sum costs N_rays x N_* (Section 1: the summation over the stars is
+ * the CPU-intensive part); with 10^6 stars most of it is the smooth pull of
+ * distant stars.  The learned-far-field variant splits the lens plane into
+ * square cells aligned with the ray tiles.  For a ray in cell c the stars of
+ * the 3 x 3 block of cells around c are summed exactly (FP32, re-centred,
+ * Kahan); the other stars act through the cell's far field F(z) =
+ * sum_far m_k / (z - z_k) (alpha_far = conj F), holomorphic on the block and
+ * written as a series in v = (z - z_c)/s (s = half the cell diagonal) whose
+ * coefficients are FP64 direct sums over the far stars.  Orders 0..order are
+ * evaluated exactly; the remainder up to target_order, v^(order+1) q(v), is
+ * learned through q (which enters the series as its next coefficient) by a
+ * small neural field -- a 32-number latent code per cell and one shared MLP
+ * 34 -> 64 -> 64 -> 2 (SiLU) -- trained on the GPU with BF16 tensor-core
+ * kernels (FP32 accumulation) on samples of that remainder.  Every cell whose
+ * held-out validation error exceeds `tolerance` falls back to the exact
+ * direct sum over all stars, which reproduces mlens_shoot's result for its
+ * rays bit for bit.  With use_network = 0 the series alone is used (ablation).
+ */
+typedef struct {
+    int32_t cells_x;              /* cells across the ray box in x; rays.nx must be a multiple of 64*cells_x */
+    int32_t order;                /* series order evaluated exactly, 0..16 (default 8) */
+    int32_t target_order;         /* order of the far-field expansion the network learns up to, order < . <= 24 (24) */
+    int32_t use_network;          /* 1: learn the remainder (default); 0: series only */
+    int64_t train_samples;        /* distinct training samples (2^24) */
+    int32_t epochs;               /* passes over them (64) */
+    int32_t batch;                /* samples per optimiser step, >= 128 (65536) */
+    float lr_weights, lr_latents; /* Adam learning rates, cosine-decayed to 5 % (3e-3, 5e-2) */
+    int32_t val_samples_per_cell; /* held-out samples per cell for validation (64) */
+    double tolerance;             /* max validation error allowed per cell, theta_E (1e-6) */
+    uint64_t seed;                /* seed of the counter-based sample and weight generators */
+} mlens_fit_params;
+
+typedef struct {
+    int32_t cells, cells_fallback;     /* ray cells, and those falling back to the exact sum */
+    int64_t tiles, tiles_fallback;     /* 64 x 32-ray tiles, and those on fallback cells */
+    int64_t train_steps;
+    double final_loss;                 /* mean squared error of the last step (cell-normalised units) */
+    double val_max_err_net, val_mean_err_net;       /* |alpha_far error| with the network (theta_E; -1 if unused) */
+    double val_max_err_series, val_mean_err_series; /* the same without the network (series to `order` only) */
+    double seconds_coefficients, seconds_train, seconds_validate;
+} mlens_fit_report;
+
+typedef struct {
+    int32_t cells_x, cells_y;       /* ray cells */
+    double grid_x0, grid_y0, cell_width;  /* cell grid incl. a one-cell ring: cell (ix, iy) covers
+                                             [x0 + ix w, x0 + (ix+1) w) x [y0 + iy w, ...) */
+    int32_t grid_nx, grid_ny;       /* = cells_x + 2, cells_y + 2; ray cell (cx, cy) is grid cell (cx+1, cy+1) */
+    int32_t order, target_order, use_network;
+    int32_t n_params, latent_dim;   /* network parameter count (flat FP32 layout), latent size */
+    mlens_fit_report report;
+} mlens_far_field_info;
+
+/* Fill *p with the defaults listed above. */
+void mlens_fit_params_default(mlens_fit_params *p);
+
+/*
+ * mlens_fit_far_field -- build the learned far field of ctx's stars for the ray
+ * grid `rays` (params NULL = defaults): cell CSR of the stars, FP64 expansion
+ * coefficients, network training (if enabled), validation, fallback flags and
+ * the work list (fallback tiles first).  Synchronous on `stream`; allocates the
+ * far-field state in the context (replacing any previous one).
+ * Errors: MLENS_ERR_ARG (grid not divisible into square tile-aligned cells, bad
+ * settings), MLENS_ERR_STATE (wrong device), MLENS_ERR_NOMEM, MLENS_ERR_CUDA.
+ */
+int mlens_fit_far_field(mlens_ctx *ctx, const mlens_grid *rays, const mlens_fit_params *params,
+                        mlens_fit_report *report, void *stream);
+
+/*
+ * mlens_shoot_learned -- mlens_shoot with the fitted far field: one persistent
+ * launch over the tiles of `rays` (which must be the grid of the fit).  Near
+ * stars exact, far field from the series and the network, flagged cells exact.
+ * beta_dev as for mlens_shoot_beta (NULL to skip); other arguments as mlens_shoot.
+ */
+int mlens_shoot_learned(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid *src, uint32_t *counts_dev,
+                        void *beta_dev, uint32_t flags, mlens_stats *stats_host, void *stream);
+
+/* Layout and fit report of the context's far field. */
+int mlens_far_field_get_info(mlens_ctx *ctx, mlens_far_field_info *out);
+
+/*
+ * mlens_far_field_export -- copy far-field state to host arrays (each may be NULL):
+ * params (n_params FP32), latents (cells x 32), flags (cells), coef (cells x
+ * (target_order+1) x {re, im} FP64 series coefficients in v), cell_start
+ * (grid_nx*grid_ny + 1 CSR offsets), per-cell validation maxima with and without
+ * the network (FP32, theta_E).  Waits for the device.
+ */
+int mlens_far_field_export(mlens_ctx *ctx, float *params, float *latents, int32_t *flags, double *coef,
+                           int32_t *cell_start, float *val_max_net, float *val_max_series);
+
+/* Save the fitted network, latents and flags (not the stars) to a file; loading
+ * it into a context with the same stars rebuilds the geometry and skips training. */
+int mlens_save_far_field(mlens_ctx *ctx, const char *path);
+int mlens_load_far_field(mlens_ctx *ctx, const char *path, void *stream);
+
+/*
+ * mlens_ff_eval -- the network kernel on explicit inputs, for verification:
+ * params_dev (n_params FP32), z_dev (n x 32), u_dev (n x 2), t_dev (n x 2 targets,
+ * may be NULL without gradients); outputs y_dev (n x 2, nullable), grads_dev
+ * (n_params, gradient of mean |y - t|^2, nullable), dz_dev (n x 32 latent
+ * gradients, nullable), *loss_host.  Synchronous; allocates 17 KB of scratch.
+ */
+int mlens_ff_eval(const float *params_dev, const float *z_dev, const float *u_dev, const float *t_dev, int64_t n,
+                  float *y_dev, float *grads_dev, float *dz_dev, float *loss_host, void *stream);
+
 /* Free a context's device memory (waits for its device).  NULL is ignored. */
 void mlens_destroy(mlens_ctx *ctx);
 

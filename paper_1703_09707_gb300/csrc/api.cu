@@ -347,6 +347,7 @@ void mlens_destroy(mlens_ctx *ctx)
     cudaGetDevice(&prev);
     if (ctx->device >= 0 && prev != ctx->device) cudaSetDevice(ctx->device);
     if (ctx->d_stars || ctx->d_stats) cudaDeviceSynchronize();
+    mlens_free_far_field(ctx);
     if (ctx->d_stars) cudaFree(ctx->d_stars);
     if (ctx->d_stats) cudaFree(ctx->d_stats);
     if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);

@@ -1,0 +1,641 @@
+// farfield_api.cu -- host side of the learned-far-field variant: fitting
+// (cell CSR, FP64 far-field expansion, network training on the GPU,
+// validation, fallback flags, work list), shooting, export, save / load, and
+// the network verification entry point.  Every computation runs in the kernels
+// of farfield.cu; this file sizes buffers, sequences launches and schedules.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "farfield.h"
+#include "mlp.cuh"
+
+using namespace mlens;
+
+struct FarState {
+    bool ready = false;
+    mlens_grid rays{};
+    CellGrid cg{};
+    int pe = 8, pt = 24, use_net = 1;
+    double tol = 0.0;
+    int nrc = 0, next = 0;
+    int *scell = nullptr, *count = nullptr, *start = nullptr, *fill = nullptr, *perm = nullptr;
+    float4 *cstars = nullptr;
+    double *coef64 = nullptr;
+    float *coef = nullptr, *tail = nullptr, *sc = nullptr;
+    float *params = nullptr, *m = nullptr, *v = nullptr, *grads = nullptr, *loss = nullptr;  // params then Z
+    __nv_bfloat16 *w1zb = nullptr, *w2b = nullptr, *w2tb = nullptr, *w1ztb = nullptr;
+    float *ec = nullptr;
+    int *flags = nullptr;
+    unsigned *vmax_net = nullptr, *vmax_series = nullptr;
+    double *vsum = nullptr;
+    int *items = nullptr;
+    int64_t nitems = 0, nfallback_tiles = 0;
+    unsigned long long *counter = nullptr;
+    int grid = 0;
+    mlens_fit_report report{};
+};
+
+namespace {
+
+int ffail(int code, const std::string &m)
+{
+    set_last_error(m);
+    return code;
+}
+
+int fcuda(cudaError_t e, const char *what)
+{
+    set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? MLENS_ERR_NOMEM : MLENS_ERR_CUDA;
+}
+
+#define FCUDA(call, what)                              \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return fcuda(e_, what); \
+    } while (0)
+
+template <class T>
+void ffree(T *&p)
+{
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+void free_state(FarState *f)
+{
+    ffree(f->scell), ffree(f->count), ffree(f->start), ffree(f->fill), ffree(f->perm), ffree(f->cstars);
+    ffree(f->coef64), ffree(f->coef), ffree(f->tail), ffree(f->sc);
+    ffree(f->params), ffree(f->m), ffree(f->v), ffree(f->grads), ffree(f->loss);
+    ffree(f->w1zb), ffree(f->w2b), ffree(f->w2tb), ffree(f->w1ztb), ffree(f->ec), ffree(f->flags);
+    ffree(f->vmax_net), ffree(f->vmax_series), ffree(f->vsum), ffree(f->items), ffree(f->counter);
+    f->ready = false;
+}
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+bool same_grid(const mlens_grid &a, const mlens_grid &b)
+{
+    return a.x0 == b.x0 && a.x1 == b.x1 && a.y0 == b.y0 && a.y1 == b.y1 && a.nx == b.nx && a.ny == b.ny;
+}
+
+// Cells aligned with the 64 x 32-ray tiles: cells_x cells across the ray box.
+int make_layout(const mlens_grid &r, int cells_x, CellGrid &cg)
+{
+    if (cells_x < 1) return ffail(MLENS_ERR_ARG, "cells_x must be >= 1");
+    if (r.nx % (64 * cells_x) != 0)
+        return ffail(MLENS_ERR_ARG, "rays.nx must be a multiple of 64 * cells_x (cells hold whole 64-ray tiles)");
+    const double dx = (r.x1 - r.x0) / r.nx, dy = (r.y1 - r.y0) / r.ny;
+    cg.ktx = r.nx / (64 * cells_x);
+    cg.w = 64.0 * cg.ktx * dx;
+    const double ky = cg.w / (32.0 * dy);
+    cg.kty = (int)std::lround(ky);
+    if (cg.kty < 1 || std::fabs(ky - cg.kty) > 1e-9 * ky)
+        return ffail(MLENS_ERR_ARG, "square cells need the cell width to be a whole number of 32-ray tiles in y");
+    cg.ncx = cells_x;
+    cg.ncy = (r.ny + 32 * cg.kty - 1) / (32 * cg.kty);
+    cg.nx = cg.ncx + 2;
+    cg.ny = cg.ncy + 2;
+    cg.x0 = r.x0 - cg.w;
+    cg.y0 = r.y0 - cg.w;
+    cg.rays_nx = r.nx;
+    cg.rays_ny = r.ny;
+    if ((int64_t)cg.nx * cg.ny > (int64_t(1) << 26)) return ffail(MLENS_ERR_ARG, "too many cells");
+    return MLENS_OK;
+}
+
+int alloc_state(FarState *f, int64_t nstars)
+{
+    const int nrc = f->nrc, nc = f->next;
+    const int64_t np = mlp::kParams + (int64_t)nrc * mlp::kLat;
+    FCUDA(cudaMalloc(&f->scell, sizeof(int) * std::max<int64_t>(nstars, 1)), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->perm, sizeof(int) * std::max<int64_t>(nstars, 1)), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->cstars, sizeof(float4) * std::max<int64_t>(nstars, 1)), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->count, sizeof(int) * nc), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->fill, sizeof(int) * nc), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->start, sizeof(int) * (nc + 1)), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->coef64, sizeof(double) * 2 * (size_t)nrc * (kPtMax + 1)), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->coef, sizeof(float) * (size_t)nrc * kCoefStride), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->tail, sizeof(float) * 2 * (size_t)nrc * kPtMax), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->sc, sizeof(float) * nrc), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->params, sizeof(float) * np), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->m, sizeof(float) * np), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->v, sizeof(float) * np), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->grads, sizeof(float) * np), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->loss, sizeof(float) * 2), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->w1zb, sizeof(__nv_bfloat16) * mlp::kHid * mlp::kLat), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->w1ztb, sizeof(__nv_bfloat16) * mlp::kHid * mlp::kLat), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->w2b, sizeof(__nv_bfloat16) * mlp::kHid * mlp::kHid), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->w2tb, sizeof(__nv_bfloat16) * mlp::kHid * mlp::kHid), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->ec, sizeof(float) * (size_t)nrc * mlp::kHid), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->flags, sizeof(int) * nrc), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->vmax_net, sizeof(unsigned) * nrc), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->vmax_series, sizeof(unsigned) * nrc), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->vsum, sizeof(double) * 2), "cudaMalloc");
+    FCUDA(cudaMalloc(&f->counter, sizeof(unsigned long long)), "cudaMalloc");
+    return MLENS_OK;
+}
+
+TrainArgs train_args(FarState *f)
+{
+    TrainArgs t{};
+    t.params = f->params;
+    t.w1zb = f->w1zb;
+    t.w2b = f->w2b;
+    t.w2tb = f->w2tb;
+    t.w1ztb = f->w1ztb;
+    t.grads = f->grads;
+    t.loss = f->loss;
+    t.z = f->params + mlp::kParams;
+    t.dz = f->grads + mlp::kParams;
+    t.tail = f->tail;
+    t.sc = f->sc;
+    t.cg = f->cg;
+    t.pe = f->pe;
+    t.pt = f->pt;
+    t.spec.nrc = f->nrc;
+    t.backward = 1;
+    return t;
+}
+
+// Validation on held-out samples: per-cell max error with and without the network.
+int validate(FarState *f, int64_t per_cell, uint64_t seed, cudaStream_t s, double *mean_net, double *mean_series)
+{
+    FCUDA(cudaMemsetAsync(f->vmax_net, 0, sizeof(unsigned) * f->nrc, s), "memset");
+    FCUDA(cudaMemsetAsync(f->vmax_series, 0, sizeof(unsigned) * f->nrc, s), "memset");
+    FCUDA(cudaMemsetAsync(f->vsum, 0, sizeof(double) * 2, s), "memset");
+    FCUDA(ff_prep_bf16(f->params, f->w1zb, f->w2b, f->w2tb, f->w1ztb, s), "prep");
+    TrainArgs t = train_args(f);
+    t.backward = 0;
+    t.loss = nullptr;
+    t.val_max_net = f->vmax_net;
+    t.val_max_series = f->vmax_series;
+    t.val_sum = f->vsum;
+    t.spec.seed = seed;
+    t.spec.offset = 0;
+    t.spec.count = per_cell * f->nrc;
+    t.inv_batch = 1.0f;
+    FCUDA(ff_train_step(t, t.spec.count, s), "validation");
+    double h[2];
+    FCUDA(cudaMemcpyAsync(h, f->vsum, sizeof(h), cudaMemcpyDeviceToHost, s), "memcpy");
+    FCUDA(cudaStreamSynchronize(s), "sync");
+    *mean_net = h[0] / (double)t.spec.count;
+    *mean_series = h[1] / (double)t.spec.count;
+    return MLENS_OK;
+}
+
+// Flags from the per-cell validation maxima, then the work list: tiles of flagged
+// cells (exact direct sum, heavy) first, then the rest.
+int schedule(FarState *f, cudaStream_t s)
+{
+    const unsigned *src = f->use_net ? f->vmax_net : f->vmax_series;
+    FCUDA(ff_flags(src, f->nrc, (float)f->tol, f->flags, s), "flags");
+    std::vector<int> fl(f->nrc);
+    std::vector<unsigned> vn(f->nrc), vs(f->nrc);
+    FCUDA(cudaMemcpyAsync(fl.data(), f->flags, sizeof(int) * f->nrc, cudaMemcpyDeviceToHost, s), "memcpy");
+    FCUDA(cudaMemcpyAsync(vn.data(), f->vmax_net, sizeof(unsigned) * f->nrc, cudaMemcpyDeviceToHost, s), "memcpy");
+    FCUDA(cudaMemcpyAsync(vs.data(), f->vmax_series, sizeof(unsigned) * f->nrc, cudaMemcpyDeviceToHost, s), "memcpy");
+    FCUDA(cudaStreamSynchronize(s), "sync");
+    const CellGrid &cg = f->cg;
+    const int ntx = (f->rays.nx + 63) / 64, nty = (f->rays.ny + 31) / 32;
+    std::vector<int> heavy, light;
+    for (int by = 0; by < nty; ++by)
+        for (int bx = 0; bx < ntx; ++bx) {
+            const int rc = (by / cg.kty) * cg.ncx + bx / cg.ktx;
+            (fl[rc] ? heavy : light).push_back(by * ntx + bx);
+        }
+    f->nfallback_tiles = (int64_t)heavy.size();
+    heavy.insert(heavy.end(), light.begin(), light.end());
+    f->nitems = (int64_t)heavy.size();
+    ffree(f->items);
+    FCUDA(cudaMalloc(&f->items, sizeof(int) * std::max<int64_t>(f->nitems, 1)), "cudaMalloc(items)");
+    FCUDA(cudaMemcpy(f->items, heavy.data(), sizeof(int) * f->nitems, cudaMemcpyHostToDevice), "memcpy(items)");
+    int nflag = 0;
+    double mx_n = 0.0, mx_s = 0.0;
+    for (int i = 0; i < f->nrc; ++i) {
+        nflag += fl[i];
+        float a, b;
+        memcpy(&a, &vn[i], 4);
+        memcpy(&b, &vs[i], 4);
+        mx_n = std::max(mx_n, (double)a);
+        mx_s = std::max(mx_s, (double)b);
+    }
+    f->report.cells = f->nrc;
+    f->report.cells_fallback = nflag;
+    f->report.tiles = f->nitems;
+    f->report.tiles_fallback = f->nfallback_tiles;
+    f->report.val_max_err_net = f->use_net ? mx_n : -1.0;
+    f->report.val_max_err_series = mx_s;
+    FCUDA(ff_learned_grid(&f->grid), "occupancy");
+    return MLENS_OK;
+}
+
+int finish_inference_tables(FarState *f, cudaStream_t s)
+{
+    FCUDA(ff_prep_bf16(f->params, f->w1zb, f->w2b, f->w2tb, f->w1ztb, s), "prep");
+    FCUDA(ff_embed(f->params, f->params + mlp::kParams, f->nrc, f->ec, s), "embed");
+    return MLENS_OK;
+}
+
+void default_params(mlens_fit_params *p)
+{
+    memset(p, 0, sizeof(*p));
+    p->cells_x = 256;
+    p->order = 8;
+    p->target_order = 24;
+    p->use_network = 1;
+    p->train_samples = int64_t(1) << 24;
+    p->epochs = 64;
+    p->batch = 65536;
+    p->lr_weights = 3e-3f;
+    p->lr_latents = 5e-2f;
+    p->val_samples_per_cell = 64;
+    p->tolerance = 1e-6;
+    p->seed = 1703;
+}
+
+int build_geometry(mlens_ctx *ctx, FarState *f, cudaStream_t s)
+{
+    FCUDA(ff_build_csr(ctx->d_stars, ctx->n_pad, f->cg, f->scell, f->count, f->start, f->fill, f->perm, f->cstars, s),
+          "cell CSR");
+    FCUDA(ff_coefficients(ctx->d_stars, f->scell, ctx->n_pad, f->cg, f->pt, f->coef64, s), "far-field coefficients");
+    FCUDA(ff_convert(f->coef64, f->cg, f->pe, f->pt, f->coef, f->tail, f->sc, s), "coefficient conversion");
+    return MLENS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mlens_fit_params_default(mlens_fit_params *p)
+{
+    if (p) default_params(p);
+}
+
+int mlens_fit_far_field(mlens_ctx *ctx, const mlens_grid *rays, const mlens_fit_params *pin, mlens_fit_report *rep,
+                        void *stream)
+{
+    if (!ctx || !rays) return ffail(MLENS_ERR_ARG, "ctx and rays must be non-NULL");
+    mlens_fit_params p;
+    if (pin) p = *pin;
+    else default_params(&p);
+    if (p.order < 0 || p.order > kPeMax) return ffail(MLENS_ERR_ARG, "order must be in [0, 16]");
+    if (p.target_order <= p.order || p.target_order > kPtMax)
+        return ffail(MLENS_ERR_ARG, "target_order must be in (order, 24]");
+    if (p.use_network && (p.train_samples < 1 || p.epochs < 1 || p.batch < 128))
+        return ffail(MLENS_ERR_ARG, "training needs train_samples >= 1, epochs >= 1, batch >= 128");
+    if (p.val_samples_per_cell < 1 || !(p.tolerance >= 0.0)) return ffail(MLENS_ERR_ARG, "bad validation settings");
+    if (!(rays->x1 > rays->x0 && rays->y1 > rays->y0) || rays->nx < 64 || rays->ny < 32)
+        return ffail(MLENS_ERR_ARG, "bad rays grid");
+    int dev = -1;
+    FCUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != ctx->device) return ffail(MLENS_ERR_STATE, "the context belongs to another device");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ctx->ff) {
+        free_state(ctx->ff);
+        delete ctx->ff;
+        ctx->ff = nullptr;
+    }
+    FarState *f = new FarState();
+    ctx->ff = f;
+    f->rays = *rays;
+    f->pe = p.order;
+    f->pt = p.target_order;
+    f->use_net = p.use_network ? 1 : 0;
+    f->tol = p.tolerance;
+    int rc = make_layout(*rays, p.cells_x, f->cg);
+    if (rc) return rc;
+    f->nrc = f->cg.ncx * f->cg.ncy;
+    f->next = f->cg.nx * f->cg.ny;
+    if ((rc = alloc_state(f, ctx->n_pad))) return rc;
+
+    double t0 = now_s();
+    if ((rc = build_geometry(ctx, f, s))) return rc;
+    FCUDA(cudaStreamSynchronize(s), "sync");
+    double t1 = now_s();
+    f->report.seconds_coefficients = t1 - t0;
+
+    const int64_t np = mlp::kParams + (int64_t)f->nrc * mlp::kLat;
+    FCUDA(ff_init_params(f->params, f->params + mlp::kParams, f->nrc, p.seed, s), "init");
+    FCUDA(cudaMemsetAsync(f->m, 0, sizeof(float) * np, s), "memset");
+    FCUDA(cudaMemsetAsync(f->v, 0, sizeof(float) * np, s), "memset");
+    int64_t steps = 0;
+    float last_loss = 0.0f;
+    if (f->use_net) {
+        const int64_t per_epoch = (p.train_samples + p.batch - 1) / p.batch;
+        const int64_t total = per_epoch * p.epochs;
+        TrainArgs t = train_args(f);
+        t.spec.seed = p.seed * 0x9E3779B97F4A7C15ull + 17;
+        for (int64_t k = 0; k < total; ++k) {
+            const int64_t j = k % per_epoch;
+            const int64_t cnt = std::min<int64_t>(p.batch, p.train_samples - j * p.batch);
+            t.spec.offset = j * p.batch;
+            t.spec.count = cnt;
+            t.inv_batch = 1.0f / (float)cnt;
+            FCUDA(cudaMemsetAsync(f->grads, 0, sizeof(float) * np, s), "memset(grads)");
+            FCUDA(cudaMemsetAsync(f->loss, 0, sizeof(float), s), "memset(loss)");
+            FCUDA(ff_prep_bf16(f->params, f->w1zb, f->w2b, f->w2tb, f->w1ztb, s), "prep");
+            FCUDA(ff_train_step(t, cnt, s), "train step");
+            // cosine decay to 5% of the initial rates
+            const double fr = (double)k / (double)std::max<int64_t>(total - 1, 1);
+            const double sc = 0.05 + 0.95 * 0.5 * (1.0 + std::cos(3.14159265358979323846 * fr));
+            const double st = (double)(k + 1);
+            const float bc1 = (float)(1.0 - std::pow(0.9, st)), bc2 = (float)(1.0 - std::pow(0.999, st));
+            FCUDA(ff_adam(f->params, f->m, f->v, f->grads, mlp::kParams, (float)(p.lr_weights * sc), 0.9f, 0.999f,
+                          1e-8f, bc1, bc2, s),
+                  "adam");
+            FCUDA(ff_adam(f->params + mlp::kParams, f->m + mlp::kParams, f->v + mlp::kParams,
+                          f->grads + mlp::kParams, (int64_t)f->nrc * mlp::kLat, (float)(p.lr_latents * sc), 0.9f,
+                          0.999f, 1e-8f, bc1, bc2, s),
+                  "adam(latents)");
+            if (k + 1 == total) FCUDA(cudaMemcpyAsync(&last_loss, f->loss, sizeof(float), cudaMemcpyDeviceToHost, s),
+                                      "memcpy(loss)");
+            ++steps;
+        }
+    }
+    FCUDA(cudaStreamSynchronize(s), "sync");
+    double t2 = now_s();
+    f->report.seconds_train = t2 - t1;
+    f->report.train_steps = steps;
+    f->report.final_loss = last_loss;
+
+    double mn = 0.0, ms = 0.0;
+    if ((rc = validate(f, p.val_samples_per_cell, p.seed * 0xD1B54A32D192ED03ull + 99, s, &mn, &ms))) return rc;
+    f->report.val_mean_err_net = f->use_net ? mn : -1.0;
+    f->report.val_mean_err_series = ms;
+    if ((rc = schedule(f, s))) return rc;
+    if ((rc = finish_inference_tables(f, s))) return rc;
+    FCUDA(cudaStreamSynchronize(s), "sync");
+    f->report.seconds_validate = now_s() - t2;
+    f->ready = true;
+    if (rep) *rep = f->report;
+    return MLENS_OK;
+}
+
+int mlens_shoot_learned(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid *src, uint32_t *counts_dev,
+                        void *beta_dev, uint32_t flags, mlens_stats *stats_host, void *stream)
+{
+    if (!ctx || !rays || !src || !counts_dev) return ffail(MLENS_ERR_ARG, "NULL argument");
+    if (!ctx->ff || !ctx->ff->ready) return ffail(MLENS_ERR_STATE, "no far field fitted on this context");
+    FarState *f = ctx->ff;
+    if (!same_grid(*rays, f->rays)) return ffail(MLENS_ERR_STATE, "the far field was fitted for another ray grid");
+    if (!(src->x1 > src->x0 && src->y1 > src->y0) || src->nx < 1 || src->ny < 1 ||
+        (int64_t)src->nx * src->ny > (int64_t(1) << 30))
+        return ffail(MLENS_ERR_ARG, "bad source grid");
+    if (((uintptr_t)counts_dev & 3u) || (beta_dev && ((uintptr_t)beta_dev & 15u)))
+        return ffail(MLENS_ERR_ARG, "misaligned buffer");
+    if (flags & ~MLENS_ACCUMULATE) return ffail(MLENS_ERR_ARG, "unknown flag bits");
+    int dev = -1;
+    FCUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != ctx->device) return ffail(MLENS_ERR_STATE, "the context belongs to another device");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!(flags & MLENS_ACCUMULATE))
+        FCUDA(cudaMemsetAsync(counts_dev, 0, (size_t)src->nx * src->ny * sizeof(uint32_t), s), "memset(counts)");
+    FCUDA(cudaMemsetAsync(ctx->d_stats, 0, 3 * sizeof(unsigned long long), s), "memset(stats)");
+    FCUDA(cudaMemsetAsync(f->counter, 0, sizeof(unsigned long long), s), "memset(counter)");
+    LearnedArgs L{};
+    L.plain.stars = ctx->d_stars;
+    L.plain.nstars = ctx->n_pad;
+    L.plain.rays = make_ray_grid(*rays);
+    L.plain.bin = make_bin_grid(*src);
+    L.plain.lens = ctx->lens;
+    L.plain.counts = counts_dev;
+    L.plain.stats = ctx->d_stats;
+    L.plain.beta_out = beta_dev;
+    L.cg = f->cg;
+    L.cstart = f->start;
+    L.cstars = f->cstars;
+    L.coef = f->coef;
+    L.sc = f->sc;
+    L.flags = f->flags;
+    L.ec = f->ec;
+    L.params = f->params;
+    L.w2b = f->w2b;
+    L.pe = f->pe;
+    L.use_net = f->use_net;
+    L.items = f->items;
+    L.nitems = f->nitems;
+    L.counter = f->counter;
+    FCUDA(ff_shoot_learned(L, f->grid, s), "learned shoot launch");
+    if (stats_host) {
+        unsigned long long h[3];
+        FCUDA(cudaMemcpyAsync(h, ctx->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s), "memcpy(stats)");
+        FCUDA(cudaStreamSynchronize(s), "sync");
+        stats_host->rays_total = (uint64_t)rays->nx * (uint64_t)rays->ny;
+        stats_host->rays_binned = h[0];
+        stats_host->rays_out = h[1];
+        stats_host->rays_nan = h[2];
+    }
+    return MLENS_OK;
+}
+
+int mlens_far_field_get_info(mlens_ctx *ctx, mlens_far_field_info *out)
+{
+    if (!ctx || !out) return ffail(MLENS_ERR_ARG, "NULL argument");
+    if (!ctx->ff || !ctx->ff->ready) return ffail(MLENS_ERR_STATE, "no far field fitted on this context");
+    const FarState *f = ctx->ff;
+    out->cells_x = f->cg.ncx;
+    out->cells_y = f->cg.ncy;
+    out->grid_x0 = f->cg.x0;
+    out->grid_y0 = f->cg.y0;
+    out->cell_width = f->cg.w;
+    out->grid_nx = f->cg.nx;
+    out->grid_ny = f->cg.ny;
+    out->order = f->pe;
+    out->target_order = f->pt;
+    out->use_network = f->use_net;
+    out->n_params = mlp::kParams;
+    out->latent_dim = mlp::kLat;
+    out->report = f->report;
+    return MLENS_OK;
+}
+
+int mlens_far_field_export(mlens_ctx *ctx, float *params, float *latents, int32_t *flags, double *coef,
+                           int32_t *cell_start, float *val_max_net, float *val_max_series)
+{
+    if (!ctx) return ffail(MLENS_ERR_ARG, "NULL context");
+    if (!ctx->ff || !ctx->ff->ready) return ffail(MLENS_ERR_STATE, "no far field fitted on this context");
+    FarState *f = ctx->ff;
+    FCUDA(cudaDeviceSynchronize(), "sync");
+    if (params) FCUDA(cudaMemcpy(params, f->params, sizeof(float) * mlp::kParams, cudaMemcpyDeviceToHost), "memcpy");
+    if (latents)
+        FCUDA(cudaMemcpy(latents, f->params + mlp::kParams, sizeof(float) * f->nrc * mlp::kLat, cudaMemcpyDeviceToHost),
+              "memcpy");
+    if (flags) FCUDA(cudaMemcpy(flags, f->flags, sizeof(int) * f->nrc, cudaMemcpyDeviceToHost), "memcpy");
+    if (coef)
+        FCUDA(cudaMemcpy(coef, f->coef64, sizeof(double) * 2 * (size_t)f->nrc * (f->pt + 1), cudaMemcpyDeviceToHost),
+              "memcpy");
+    if (cell_start) FCUDA(cudaMemcpy(cell_start, f->start, sizeof(int) * (f->next + 1), cudaMemcpyDeviceToHost), "memcpy");
+    if (val_max_net) FCUDA(cudaMemcpy(val_max_net, f->vmax_net, sizeof(float) * f->nrc, cudaMemcpyDeviceToHost), "memcpy");
+    if (val_max_series)
+        FCUDA(cudaMemcpy(val_max_series, f->vmax_series, sizeof(float) * f->nrc, cudaMemcpyDeviceToHost), "memcpy");
+    return MLENS_OK;
+}
+
+// ---------------------------------------------------------- save / load
+static const char kMagic[8] = {'M', 'L', 'E', 'N', 'S', 'F', 'F', '1'};
+
+int mlens_save_far_field(mlens_ctx *ctx, const char *path)
+{
+    if (!ctx || !path) return ffail(MLENS_ERR_ARG, "NULL argument");
+    if (!ctx->ff || !ctx->ff->ready) return ffail(MLENS_ERR_STATE, "no far field fitted on this context");
+    FarState *f = ctx->ff;
+    std::vector<float> prm(mlp::kParams + (size_t)f->nrc * mlp::kLat);
+    std::vector<int> fl(f->nrc);
+    std::vector<unsigned> vn(f->nrc), vs(f->nrc);
+    FCUDA(cudaDeviceSynchronize(), "sync");
+    FCUDA(cudaMemcpy(prm.data(), f->params, sizeof(float) * prm.size(), cudaMemcpyDeviceToHost), "memcpy");
+    FCUDA(cudaMemcpy(fl.data(), f->flags, sizeof(int) * f->nrc, cudaMemcpyDeviceToHost), "memcpy");
+    FCUDA(cudaMemcpy(vn.data(), f->vmax_net, sizeof(unsigned) * f->nrc, cudaMemcpyDeviceToHost), "memcpy");
+    FCUDA(cudaMemcpy(vs.data(), f->vmax_series, sizeof(unsigned) * f->nrc, cudaMemcpyDeviceToHost), "memcpy");
+    FILE *fh = fopen(path, "wb");
+    if (!fh) return ffail(MLENS_ERR_ARG, std::string("cannot open ") + path + " for writing");
+    const int64_t n = ctx->n;
+    bool ok = fwrite(kMagic, 1, 8, fh) == 8 && fwrite(&f->rays, sizeof(f->rays), 1, fh) == 1 &&
+              fwrite(&f->cg, sizeof(f->cg), 1, fh) == 1 && fwrite(&f->pe, sizeof(int), 1, fh) == 1 &&
+              fwrite(&f->pt, sizeof(int), 1, fh) == 1 && fwrite(&f->use_net, sizeof(int), 1, fh) == 1 &&
+              fwrite(&f->tol, sizeof(double), 1, fh) == 1 && fwrite(&n, sizeof(n), 1, fh) == 1 &&
+              fwrite(&f->report, sizeof(f->report), 1, fh) == 1 &&
+              fwrite(prm.data(), sizeof(float), prm.size(), fh) == prm.size() &&
+              fwrite(fl.data(), sizeof(int), fl.size(), fh) == fl.size() &&
+              fwrite(vn.data(), sizeof(unsigned), vn.size(), fh) == vn.size() &&
+              fwrite(vs.data(), sizeof(unsigned), vs.size(), fh) == vs.size();
+    fclose(fh);
+    if (!ok) return ffail(MLENS_ERR_ARG, std::string("short write to ") + path);
+    return MLENS_OK;
+}
+
+int mlens_load_far_field(mlens_ctx *ctx, const char *path, void *stream)
+{
+    if (!ctx || !path) return ffail(MLENS_ERR_ARG, "NULL argument");
+    FILE *fh = fopen(path, "rb");
+    if (!fh) return ffail(MLENS_ERR_ARG, std::string("cannot open ") + path);
+    char mg[8];
+    mlens_grid rays;
+    CellGrid cg;
+    int pe, pt, un;
+    double tol;
+    int64_t n;
+    mlens_fit_report rep;
+    bool ok = fread(mg, 1, 8, fh) == 8 && memcmp(mg, kMagic, 8) == 0 && fread(&rays, sizeof(rays), 1, fh) == 1 &&
+              fread(&cg, sizeof(cg), 1, fh) == 1 && fread(&pe, sizeof(int), 1, fh) == 1 &&
+              fread(&pt, sizeof(int), 1, fh) == 1 && fread(&un, sizeof(int), 1, fh) == 1 &&
+              fread(&tol, sizeof(double), 1, fh) == 1 && fread(&n, sizeof(n), 1, fh) == 1 &&
+              fread(&rep, sizeof(rep), 1, fh) == 1;
+    if (!ok) {
+        fclose(fh);
+        return ffail(MLENS_ERR_ARG, std::string(path) + " is not a far-field file");
+    }
+    if (n != ctx->n || pe < 0 || pe > kPeMax || pt <= pe || pt > kPtMax) {
+        fclose(fh);
+        return ffail(MLENS_ERR_ARG, std::string(path) + " belongs to another star field or is damaged");
+    }
+    const int nrc = cg.ncx * cg.ncy;
+    std::vector<float> prm(mlp::kParams + (size_t)nrc * mlp::kLat);
+    std::vector<int> fl(nrc);
+    std::vector<unsigned> vn(nrc), vs(nrc);
+    ok = fread(prm.data(), sizeof(float), prm.size(), fh) == prm.size() &&
+         fread(fl.data(), sizeof(int), fl.size(), fh) == fl.size() &&
+         fread(vn.data(), sizeof(unsigned), vn.size(), fh) == vn.size() &&
+         fread(vs.data(), sizeof(unsigned), vs.size(), fh) == vs.size();
+    fclose(fh);
+    if (!ok) return ffail(MLENS_ERR_ARG, std::string("short read from ") + path);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ctx->ff) {
+        free_state(ctx->ff);
+        delete ctx->ff;
+        ctx->ff = nullptr;
+    }
+    FarState *f = new FarState();
+    ctx->ff = f;
+    f->rays = rays;
+    f->cg = cg;
+    f->pe = pe;
+    f->pt = pt;
+    f->use_net = un;
+    f->tol = tol;
+    f->nrc = nrc;
+    f->next = cg.nx * cg.ny;
+    f->report = rep;
+    int rc;
+    if ((rc = alloc_state(f, ctx->n_pad))) return rc;
+    // the geometry (CSR, coefficients) is recomputed from the context's stars
+    if ((rc = build_geometry(ctx, f, s))) return rc;
+    FCUDA(cudaMemcpy(f->params, prm.data(), sizeof(float) * prm.size(), cudaMemcpyHostToDevice), "memcpy");
+    FCUDA(cudaMemcpy(f->flags, fl.data(), sizeof(int) * nrc, cudaMemcpyHostToDevice), "memcpy");
+    FCUDA(cudaMemcpy(f->vmax_net, vn.data(), sizeof(unsigned) * nrc, cudaMemcpyHostToDevice), "memcpy");
+    FCUDA(cudaMemcpy(f->vmax_series, vs.data(), sizeof(unsigned) * nrc, cudaMemcpyHostToDevice), "memcpy");
+    if ((rc = schedule(f, s))) return rc;
+    if ((rc = finish_inference_tables(f, s))) return rc;
+    FCUDA(cudaStreamSynchronize(s), "sync");
+    f->ready = true;
+    return MLENS_OK;
+}
+
+// ------------------------------------------- network verification entry
+int mlens_ff_eval(const float *params_dev, const float *z_dev, const float *u_dev, const float *t_dev, int64_t nsamples,
+                  float *y_dev, float *grads_dev, float *dz_dev, float *loss_host, void *stream)
+{
+    if (!params_dev || !z_dev || !u_dev || nsamples < 1) return ffail(MLENS_ERR_ARG, "bad arguments");
+    if (grads_dev && !t_dev) return ffail(MLENS_ERR_ARG, "gradients need targets");
+    cudaStream_t s = (cudaStream_t)stream;
+    __nv_bfloat16 *w = nullptr;
+    float *dl = nullptr;
+    FCUDA(cudaMalloc(&w, sizeof(__nv_bfloat16) * (2 * mlp::kHid * mlp::kLat + 2 * mlp::kHid * mlp::kHid)), "cudaMalloc");
+    cudaError_t e = cudaMalloc(&dl, sizeof(float));
+    __nv_bfloat16 *w1zb = w, *w1ztb = w + mlp::kHid * mlp::kLat, *w2b = w1ztb + mlp::kHid * mlp::kLat,
+                  *w2tb = w2b + mlp::kHid * mlp::kHid;
+    if (e == cudaSuccess) e = cudaMemsetAsync(dl, 0, sizeof(float), s);
+    if (e == cudaSuccess && grads_dev) e = cudaMemsetAsync(grads_dev, 0, sizeof(float) * mlp::kParams, s);
+    if (e == cudaSuccess) e = ff_prep_bf16(params_dev, w1zb, w2b, w2tb, w1ztb, s);
+    if (e == cudaSuccess) {
+        TrainArgs t{};
+        t.params = const_cast<float *>(params_dev);
+        t.w1zb = w1zb;
+        t.w2b = w2b;
+        t.w2tb = w2tb;
+        t.w1ztb = w1ztb;
+        t.grads = grads_dev;
+        t.loss = dl;
+        t.spec.count = nsamples;
+        t.spec.nrc = 1;
+        t.inv_batch = 1.0f / (float)nsamples;
+        t.zin = z_dev;
+        t.uin = u_dev;
+        t.tin = t_dev;
+        t.yout = y_dev;
+        t.dzout = dz_dev;
+        t.backward = grads_dev ? 1 : 0;
+        e = ff_train_step(t, nsamples, s);
+    }
+    float h = 0.0f;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, dl, sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(w);
+    cudaFree(dl);
+    if (e != cudaSuccess) return fcuda(e, "mlens_ff_eval");
+    if (loss_host) *loss_host = h;
+    return MLENS_OK;
+}
+
+}  // extern "C"
+
+void mlens_free_far_field(mlens_ctx *ctx)
+{
+    if (ctx && ctx->ff) {
+        free_state(ctx->ff);
+        delete ctx->ff;
+        ctx->ff = nullptr;
+    }
+}

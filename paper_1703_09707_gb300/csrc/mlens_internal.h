@@ -97,6 +97,9 @@ LensTerms make_lens_terms(double kc, double g1, double g2);
 
 }  // namespace mlens
 
+struct FarState;                       // learned far field (farfield_api.cu)
+void mlens_free_far_field(mlens_ctx *ctx);
+
 // A star field on one device (definition shared by the API translation units).
 struct mlens_ctx {
     int device = -1;
@@ -108,4 +111,5 @@ struct mlens_ctx {
     int precision = MLENS_PREC_FP32;
     int pairs_per_thread = 4;
     int star_stage = 256;
+    FarState *ff = nullptr;
 };

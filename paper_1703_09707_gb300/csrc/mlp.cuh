@@ -1,0 +1,79 @@
+// mlp.cuh -- the far-field network of the learned-far-field variant on BF16
+// tensor cores (mma.sync m16n8k16, FP32 accumulation).
+//
+// Network: a per-cell latent z (32) and one shared MLP 34 -> 64 -> 64 -> 2,
+//   h1 = W1z z + W1u u + b1, a1 = silu(h1); h2 = W2 a1 + b2, a2 = silu(h2);
+//   y = W3 a2 + b3,  silu(v) = v (1 + tanh(v/2)) / 2.
+// The latent block of layer 1 and layer 2 run on the tensor cores with BF16
+// operands (z, W1z, a1, W2; dh2, dh1 in the backward pass); the position block
+// of layer 1 (W1u u, 2 inputs) and layer 3 stay in FP32.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mlens {
+namespace mlp {
+
+constexpr int kLat = 32;
+constexpr int kHid = 64;
+constexpr int kOut = 2;
+// flat FP32 parameter layout
+constexpr int oW1z = 0;                      // [64][32]
+constexpr int oW1u = oW1z + kHid * kLat;     // [64][2]
+constexpr int ob1 = oW1u + kHid * 2;         // [64]
+constexpr int oW2 = ob1 + kHid;              // [64][64]
+constexpr int ob2 = oW2 + kHid * kHid;       // [64]
+constexpr int oW3 = ob2 + kHid;              // [2][64]
+constexpr int ob3 = oW3 + kOut * kHid;       // [2]
+constexpr int kParams = ob3 + kOut;          // 6530
+
+__device__ __forceinline__ float sigm(float v) { return 0.5f * (1.0f + tanhf(0.5f * v)); }
+__device__ __forceinline__ float silu(float v) { return v * sigm(v); }
+__device__ __forceinline__ float dsilu(float v)
+{
+    const float s = sigm(v);
+    return s * (1.0f + v * (1.0f - s));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&p);
+}
+
+__device__ __forceinline__ __nv_bfloat16 to_bf16(float v) { return __float2bfloat16_rn(v); }
+
+// D = A (16x16, row) * B (16x8, col) + D
+__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const uint32_t b[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Fragment loads from shared memory.  A: row-major [row][k] with leading dim ld;
+// B: stored [n][k] with leading dim ld (k contiguous).  g = lane/4, t = lane%4.
+__device__ __forceinline__ void load_a(uint32_t a[4], const __nv_bfloat16 *A, int ld, int row0, int k0)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const __nv_bfloat16 *p = A + (row0 + g) * ld + k0 + 2 * t;
+    a[0] = *reinterpret_cast<const uint32_t *>(p);
+    a[1] = *reinterpret_cast<const uint32_t *>(p + 8 * ld);
+    a[2] = *reinterpret_cast<const uint32_t *>(p + 8);
+    a[3] = *reinterpret_cast<const uint32_t *>(p + 8 * ld + 8);
+}
+
+__device__ __forceinline__ void load_b(uint32_t b[2], const __nv_bfloat16 *B, int ld, int n0, int k0)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const __nv_bfloat16 *p = B + (n0 + g) * ld + k0 + 2 * t;
+    b[0] = *reinterpret_cast<const uint32_t *>(p);
+    b[1] = *reinterpret_cast<const uint32_t *>(p + 8);
+}
+
+}  // namespace mlp
+}  // namespace mlens

@@ -27,264 +27,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "mlens_dev.cuh"
+#include "tile.cuh"
 
 namespace mlens {
-
-constexpr int kThreads = 256;
-constexpr int kTileX = 64;                 // rays per tile row = threads per row group
-constexpr int kGroups = kThreads / kTileX; // row groups
-constexpr int kKahan = 32;                 // stars per compensated partial
-
-static_assert(kStarPad % kKahan == 0, "star padding must be whole Kahan chunks");
-
-template <int SC>
-struct StarStage {
-    float4 q[2][SC];   // (-dx, -dx, -dy, -dy) relative to the tile centre
-    float2 mm[2][SC];  // (m, m)
-};
-
-template <int SC>
-union ShootSmem {
-    StarStage<SC> st;
-    uint32_t hist[kWin * kWin];
-};
-
-struct TileShared {
-    float tc[8];       // cx, cy, ex, ey, B0h.x, B0h.y, B0l.x, B0l.y
-    int win[2];
-    unsigned sred[3];
-};
-
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-
-// v - c for packed pairs, with one rounding (fma with -1 is exact in the product)
-__device__ __forceinline__ float2 sub2(float2 v, float2 c) { return __ffma2_rn(c, f2(-1.0f, -1.0f), v); }
-
-// Kahan step on packed pairs: S + v with compensation C (true sum ~ S - C).
-__device__ __forceinline__ void kahan2(float2 &S, float2 &C, float2 v)
-{
-    float2 y = sub2(v, C);
-    float2 t = __fadd2_rn(S, y);
-    C = sub2(sub2(t, S), y);
-    S = t;
-}
-
-constexpr int tile_rows(int np) { return kGroups * 2 * np; }
-
-// One tile (bx, by) of the ray grid of `a`, start to finish: prologue, star
-// stages, beta, binning, counters.  Every thread of the CTA must call it.
-template <int NP, int SC, bool NAIVE>
-__device__ __forceinline__ void shoot_tile(const ShootArgs &a, int bx, int by, ShootSmem<SC> &sm, TileShared &ts)
-{
-    constexpr int kTileY = tile_rows(NP);
-    constexpr int kLoads = (SC + kThreads - 1) / kThreads;
-    const int tid = threadIdx.x;
-    const int tx = tid % kTileX;
-    const int tg = tid / kTileX;
-    const int i0 = bx * kTileX;
-    const int j0 = by * kTileY;
-    const RayGrid &R = a.rays;
-
-    if (tid == 0) {
-        if (!NAIVE) {
-            // tile centre (any float near the middle), offsets of the first ray and
-            // A c in FP64, split into float pairs
-            double cxd = R.x0 + ((double)i0 + 0.5 * kTileX) * R.dx;
-            double cyd = R.y0 + ((double)j0 + 0.5 * kTileY) * R.dy;
-            float cx = (float)cxd, cy = (float)cyd;
-            double ex = (R.x0 + ((double)i0 + 0.5) * R.dx) - (double)cx;
-            double ey = (R.y0 + ((double)j0 + 0.5) * R.dy) - (double)cy;
-            double bxd = a.lens.a11 * (double)cx + a.lens.a12 * (double)cy;
-            double byd = a.lens.a12 * (double)cx + a.lens.a22 * (double)cy;
-            float bxh = (float)bxd, byh = (float)byd;
-            ts.tc[0] = cx;
-            ts.tc[1] = cy;
-            ts.tc[2] = (float)ex;
-            ts.tc[3] = (float)ey;
-            ts.tc[4] = bxh;
-            ts.tc[5] = byh;
-            ts.tc[6] = (float)(bxd - (double)bxh);
-            ts.tc[7] = (float)(byd - (double)byh);
-        }
-        ts.sred[0] = ts.sred[1] = ts.sred[2] = 0u;
-    }
-    __syncthreads();
-
-    // ------------------------------------------------------- this thread's rays
-    float2 rx;       // packed (x, x): both rays of a pair share the column
-    float2 ry[NP];   // packed (y_2p, y_2p+1)
-    float2 px[NP], py[NP];             // partial sums (NAIVE: the whole running sum)
-    float2 Sx[NP], Sy[NP], Cx[NP], Cy[NP];
-    const float kx = (float)tx;
-    float cx = 0.f, cy = 0.f;
-    if (!NAIVE) {
-        cx = ts.tc[0];
-        cy = ts.tc[1];
-        float dxr = __fmaf_rn(kx, R.dxh, __fmaf_rn(kx, R.dxl, ts.tc[2]));
-        rx = f2(dxr, dxr);
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            float k0 = (float)(tg * 2 * NP + 2 * p), k1 = k0 + 1.0f;
-            ry[p] = f2(__fmaf_rn(k0, R.dyh, __fmaf_rn(k0, R.dyl, ts.tc[3])),
-                       __fmaf_rn(k1, R.dyh, __fmaf_rn(k1, R.dyl, ts.tc[3])));
-            px[p] = py[p] = Sx[p] = Sy[p] = Cx[p] = Cy[p] = f2(0.f, 0.f);
-        }
-    } else {
-        const float x0f = (float)R.x0, y0f = (float)R.y0;
-        const float dxf = (float)R.dx, dyf = (float)R.dy;
-        float thx = x0f + ((float)(i0 + tx) + 0.5f) * dxf;
-        rx = f2(thx, thx);
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            float y0 = y0f + ((float)(j0 + tg * 2 * NP + 2 * p) + 0.5f) * dyf;
-            float y1 = y0f + ((float)(j0 + tg * 2 * NP + 2 * p + 1) + 0.5f) * dyf;
-            ry[p] = f2(y0, y1);
-            // alpha_0 first (Algorithm 1), then every star is added to it
-            px[p] = f2(a.lens.fm11 * thx + a.lens.fm12 * y0, a.lens.fm11 * thx + a.lens.fm12 * y1);
-            py[p] = f2(a.lens.fm12 * thx + a.lens.fm22 * y0, a.lens.fm12 * thx + a.lens.fm22 * y1);
-            Sx[p] = Sy[p] = Cx[p] = Cy[p] = f2(0.f, 0.f);
-        }
-    }
-
-    // ---------------------------------------------------------- star stages
-    const int64_t nst = a.nstars;  // multiple of kKahan
-    const int nstage = (int)((nst + SC - 1) / SC);
-    float4 nxt[kLoads];
-    auto stage_load = [&](int s) {
-        const int64_t base = (int64_t)s * SC;
-#pragma unroll
-        for (int l = 0; l < kLoads; ++l) {
-            const int k = tid + l * kThreads;
-            nxt[l] = (k < SC && base + k < nst) ? __ldg(&a.stars[base + k]) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    };
-    auto stage_store = [&](int buf) {
-#pragma unroll
-        for (int l = 0; l < kLoads; ++l) {
-            const int k = tid + l * kThreads;
-            if (k < SC) {
-                const float4 q = nxt[l];
-                float nx = NAIVE ? -q.x : __fsub_rn(cx, q.x);
-                float ny = NAIVE ? -q.y : __fsub_rn(cy, q.y);
-                sm.st.q[buf][k] = make_float4(nx, nx, ny, ny);
-                sm.st.mm[buf][k] = f2(q.z, q.z);
-            }
-        }
-    };
-    if (nstage > 0) {
-        stage_load(0);
-        stage_store(0);
-    }
-    __syncthreads();
-
-    for (int s = 0; s < nstage; ++s) {
-        const int buf = s & 1;
-        const int cnt = (int)min((int64_t)SC, nst - (int64_t)s * SC);
-        if (s + 1 < nstage) stage_load(s + 1);
-        const float4 *Q = sm.st.q[buf];
-        const float2 *M = sm.st.mm[buf];
-#pragma unroll 1
-        for (int k0 = 0; k0 < cnt; k0 += kKahan) {
-#pragma unroll
-            for (int k = k0; k < k0 + kKahan; ++k) {
-                const float4 q = Q[k];
-                const float2 m2 = M[k];
-                const float2 dx = __fadd2_rn(rx, f2(q.x, q.y));
-                const float2 dx2 = __fmul2_rn(dx, dx);
-                const float2 nyv = f2(q.z, q.w);
-#pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    const float2 dy = __fadd2_rn(ry[p], nyv);
-                    const float2 r2 = __ffma2_rn(dy, dy, dx2);
-                    const float2 inv = f2(rcp_approx(r2.x), rcp_approx(r2.y));
-                    const float2 f = __fmul2_rn(m2, inv);
-                    px[p] = __ffma2_rn(f, dx, px[p]);
-                    py[p] = __ffma2_rn(f, dy, py[p]);
-                }
-            }
-            if (!NAIVE) {
-#pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    kahan2(Sx[p], Cx[p], px[p]);
-                    kahan2(Sy[p], Cy[p], py[p]);
-                    px[p] = py[p] = f2(0.f, 0.f);
-                }
-            }
-        }
-        if (s + 1 < nstage) stage_store(buf ^ 1);
-        __syncthreads();
-    }
-
-    // ------------------------------------------------ beta as float pairs
-    float bxh[2 * NP], byh[2 * NP], bxl[2 * NP], byl[2 * NP];
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int r = 2 * p + h;
-            if (!NAIVE) {
-                const float sx = h ? Sx[p].y : Sx[p].x, sy = h ? Sy[p].y : Sy[p].x;
-                const float ccx = h ? Cx[p].y : Cx[p].x, ccy = h ? Cy[p].y : Cy[p].x;
-                const float dxr = rx.x, dyr = h ? ry[p].y : ry[p].x;
-                // A delta for this ray (small)
-                const float lx = __fmaf_rn(a.lens.fa11, dxr, __fmul_rn(a.lens.fa12, dyr));
-                const float ly = __fmaf_rn(a.lens.fa12, dxr, __fmul_rn(a.lens.fa22, dyr));
-                float th, tl;
-                two_sum(ts.tc[4], -sx, th, tl);
-                tl = __fadd_rn(tl, __fadd_rn(__fadd_rn(ts.tc[6], ccx), lx));
-                two_sum(th, tl, bxh[r], bxl[r]);
-                two_sum(ts.tc[5], -sy, th, tl);
-                tl = __fadd_rn(tl, __fadd_rn(__fadd_rn(ts.tc[7], ccy), ly));
-                two_sum(th, tl, byh[r], byl[r]);
-            } else {
-                const float thy = h ? ry[p].y : ry[p].x;
-                bxh[r] = __fsub_rn(rx.x, h ? px[p].y : px[p].x);
-                byh[r] = __fsub_rn(thy, h ? py[p].y : py[p].x);
-                bxl[r] = 0.0f;
-                byl[r] = 0.0f;
-            }
-        }
-    }
-
-    // ----------------------------------------------------------- binning
-    const int ix = i0 + tx;
-    const bool col_ok = ix < R.nx;
-    __syncthreads();  // star stages are dead: reuse the memory as the window
-    for (int b = tid; b < kWin * kWin; b += kThreads) sm.hist[b] = 0u;
-    if (tid == 0) {
-        ts.win[0] = pair_axis_rough(bxh[0], a.bin.ax) - kWin / 2;
-        ts.win[1] = pair_axis_rough(byh[0], a.bin.ay) - kWin / 2;
-    }
-    __syncthreads();
-    WinHist W{sm.hist, ts.win[0], ts.win[1]};
-    unsigned nb = 0, no = 0, nn = 0;
-#pragma unroll
-    for (int r = 0; r < 2 * NP; ++r) {
-        const int jy = j0 + tg * 2 * NP + r;
-        uint32_t key = kNoKey;
-        if (col_ok && jy < R.ny) {
-            int gpx = 0, gpy = 0;
-            const int pix = pair_pixel(bxh[r], byh[r], bxl[r], byl[r], a.bin, gpx, gpy);
-            if (pix >= 0) {
-                ++nb;
-                key = hist_key(pix, gpx, gpy, W, a.bin);
-            } else if (pix == -1) {
-                ++no;
-            } else {
-                ++nn;
-            }
-            if (a.beta_out) {
-                float4 *bo = reinterpret_cast<float4 *>(a.beta_out);
-                bo[(int64_t)jy * R.nx + ix] = make_float4(bxh[r], byh[r], bxl[r], byl[r]);
-            }
-        }
-        hist_add_warp(key, W, a.counts);
-    }
-    __syncthreads();
-    hist_flush(W, a.bin, a.counts);
-    stats_add_block(nb, no, nn, ts.sred, a.stats);
-}
 
 template <int NP, int SC, bool NAIVE>
 __global__ void __launch_bounds__(kThreads, 2) k_shoot_fp32(ShootArgs a)

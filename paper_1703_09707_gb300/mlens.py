@@ -54,6 +54,32 @@ class mlens_stats(C.Structure):
                     rays_out=int(self.rays_out), rays_nan=int(self.rays_nan))
 
 
+class mlens_fit_params(C.Structure):
+    _fields_ = [("cells_x", C.c_int32), ("order", C.c_int32), ("target_order", C.c_int32),
+                ("use_network", C.c_int32), ("train_samples", C.c_int64), ("epochs", C.c_int32),
+                ("batch", C.c_int32), ("lr_weights", C.c_float), ("lr_latents", C.c_float),
+                ("val_samples_per_cell", C.c_int32), ("tolerance", C.c_double), ("seed", C.c_uint64)]
+
+
+class mlens_fit_report(C.Structure):
+    _fields_ = [("cells", C.c_int32), ("cells_fallback", C.c_int32), ("tiles", C.c_int64),
+                ("tiles_fallback", C.c_int64), ("train_steps", C.c_int64), ("final_loss", C.c_double),
+                ("val_max_err_net", C.c_double), ("val_mean_err_net", C.c_double),
+                ("val_max_err_series", C.c_double), ("val_mean_err_series", C.c_double),
+                ("seconds_coefficients", C.c_double), ("seconds_train", C.c_double),
+                ("seconds_validate", C.c_double)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class mlens_far_field_info(C.Structure):
+    _fields_ = [("cells_x", C.c_int32), ("cells_y", C.c_int32), ("grid_x0", C.c_double), ("grid_y0", C.c_double),
+                ("cell_width", C.c_double), ("grid_nx", C.c_int32), ("grid_ny", C.c_int32), ("order", C.c_int32),
+                ("target_order", C.c_int32), ("use_network", C.c_int32), ("n_params", C.c_int32),
+                ("latent_dim", C.c_int32), ("report", mlens_fit_report)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -79,6 +105,14 @@ SIGNATURES = {
     "mlens_batch_run": (C.c_int, [_vp, _sp, _vp]),
     "mlens_batch_destroy": (None, [_vp]),
     "mlens_shoot_batch": (C.c_int, [C.POINTER(_vp), C.c_int32, _gp, _gp, C.POINTER(_vp), C.c_uint32, _sp, _vp]),
+    "mlens_fit_params_default": (None, [C.POINTER(mlens_fit_params)]),
+    "mlens_fit_far_field": (C.c_int, [_vp, _gp, C.POINTER(mlens_fit_params), C.POINTER(mlens_fit_report), _vp]),
+    "mlens_shoot_learned": (C.c_int, [_vp, _gp, _gp, _vp, _vp, C.c_uint32, _sp, _vp]),
+    "mlens_far_field_get_info": (C.c_int, [_vp, C.POINTER(mlens_far_field_info)]),
+    "mlens_far_field_export": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "mlens_save_far_field": (C.c_int, [_vp, C.c_char_p]),
+    "mlens_load_far_field": (C.c_int, [_vp, C.c_char_p, _vp]),
+    "mlens_ff_eval": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, _vp, _vp, _vp, C.POINTER(C.c_float), _vp]),
     "mlens_destroy": (None, [_vp]),
     "mlens_last_error": (C.c_char_p, []),
     "mlens_version": (C.c_int, []),
@@ -296,6 +330,71 @@ def mlens_shoot_batch(ctxs, rays, srcs, counts, flags: int = 0, stats: bool = Fa
     st = (mlens_stats * nf)()
     _check(load().mlens_shoot_batch(cx, nf, ga, sa, pa, int(flags), st if stats else None, _stream_ptr(stream)))
     return [x.asdict() for x in st] if stats else None
+
+
+def fit_params(**kw) -> mlens_fit_params:
+    """Defaults of mlens_fit_params_default, with keyword overrides."""
+    p = mlens_fit_params()
+    load().mlens_fit_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def mlens_fit_far_field(ctx: Ctx, rays, params: mlens_fit_params = None, stream=None) -> dict:
+    g = grid(rays)
+    rep = mlens_fit_report()
+    _check(load().mlens_fit_far_field(ctx.handle, C.byref(g), C.byref(params) if params is not None else None,
+                                      C.byref(rep), _stream_ptr(stream)))
+    return rep.asdict()
+
+
+def mlens_shoot_learned(ctx: Ctx, rays, src, counts, beta=None, flags: int = 0, stats: bool = False, stream=None):
+    st = mlens_stats()
+    g, s = grid(rays), grid(src)
+    _check(load().mlens_shoot_learned(ctx.handle, C.byref(g), C.byref(s), _dev_ptr(counts), _dev_ptr(beta),
+                                      int(flags), C.byref(st) if stats else None, _stream_ptr(stream)))
+    return st.asdict() if stats else None
+
+
+def mlens_far_field_get_info(ctx: Ctx) -> mlens_far_field_info:
+    info = mlens_far_field_info()
+    _check(load().mlens_far_field_get_info(ctx.handle, C.byref(info)))
+    return info
+
+
+def mlens_far_field_export(ctx: Ctx) -> dict:
+    """All exportable far-field state as numpy arrays."""
+    info = mlens_far_field_get_info(ctx)
+    nrc = info.cells_x * info.cells_y
+    out = dict(params=np.empty(info.n_params, np.float32), latents=np.empty((nrc, info.latent_dim), np.float32),
+               flags=np.empty(nrc, np.int32), coef=np.empty((nrc, info.target_order + 1, 2), np.float64),
+               cell_start=np.empty(info.grid_nx * info.grid_ny + 1, np.int32),
+               val_max_net=np.empty(nrc, np.float32), val_max_series=np.empty(nrc, np.float32))
+    ptr = {k: v.ctypes.data_as(_vp) for k, v in out.items()}
+    _check(load().mlens_far_field_export(ctx.handle, ptr["params"], ptr["latents"], ptr["flags"], ptr["coef"],
+                                         ptr["cell_start"], ptr["val_max_net"], ptr["val_max_series"]))
+    out["info"] = info
+    return out
+
+
+def mlens_save_far_field(ctx: Ctx, path: str):
+    _check(load().mlens_save_far_field(ctx.handle, path.encode()))
+
+
+def mlens_load_far_field(ctx: Ctx, path: str, stream=None):
+    _check(load().mlens_load_far_field(ctx.handle, path.encode(), _stream_ptr(stream)))
+
+
+def mlens_ff_eval(params, z, u, t=None, y=None, grads=None, dz=None, stream=None) -> float:
+    """Network kernel on explicit CUDA tensors (float32); returns the loss."""
+    loss = C.c_float(0.0)
+    n = int(z.shape[0])
+    _check(load().mlens_ff_eval(_dev_ptr(params), _dev_ptr(z), _dev_ptr(u), _dev_ptr(t), n, _dev_ptr(y),
+                                _dev_ptr(grads), _dev_ptr(dz), C.byref(loss), _stream_ptr(stream)))
+    return float(loss.value)
 
 
 def mlens_destroy(ctx: Ctx):

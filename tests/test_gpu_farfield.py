@@ -1,0 +1,198 @@
+"""The learned-far-field variant on the GPU against the FP64 oracle and against the
+plain direct-sum path: cell CSR, FP64 expansion coefficients, the network's forward
+and backward kernels, the shooting kernel (series only, fallback, trained network),
+and save/load."""
+import math
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import workloads as W  # noqa: E402
+from gpu_util import compare_to_oracle, make_ctx, shoot_gpu  # noqa: E402
+from oracle import mlp  # noqa: E402
+from paper_1703_09707_gb300 import mlens as M  # noqa: E402
+
+# A reduced version of the 10^6-star workload: the same star density (kappa_* = 0.45,
+# 0.64 stars per theta_E^2), the same cell width (0.46875 theta_E) and 2048^2 rays.
+N_STARS = 20000
+RAYS = W.Grid(-7.5, 7.5, -2.5, 2.5, 2048, 2048)
+SRC = W.Grid(-2.0, 2.0, -2.0, 2.0, 512, 512)
+CELLS_X = 32
+
+
+@pytest.fixture(scope="module")
+def field():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return W.random_field(W.SEED_BASE + 40, N_STARS, 0.45, 0.05, 0.25, 0.0)
+
+
+def ext_cells(info):
+    return oracle.cells(info.grid_x0, info.grid_y0, info.cell_width, info.grid_nx, info.grid_ny)
+
+
+def host(c, src):
+    return c.cpu().numpy().view(np.uint32).reshape(src.ny, src.nx)
+
+
+def plain_map(f):
+    c, st, b4 = shoot_gpu(f, RAYS, SRC)
+    return c, st, b4
+
+
+def learned_map(ctx, want_beta=False):
+    counts = torch.empty(SRC.n, dtype=torch.int32, device="cuda")
+    beta = torch.empty(RAYS.n * 4, dtype=torch.float32, device="cuda") if want_beta else None
+    st = M.mlens_shoot_learned(ctx, RAYS, SRC, counts, beta=beta, stats=True)
+    torch.cuda.synchronize()
+    b = beta.cpu().numpy().reshape(-1, 4) if want_beta else None
+    return host(counts, SRC), st, b
+
+
+def test_cell_csr_and_coefficients_match_the_oracle(field):
+    ctx = make_ctx(field)
+    rep = M.mlens_fit_far_field(ctx, RAYS, M.fit_params(cells_x=CELLS_X, use_network=0, order=8))
+    ex = M.mlens_far_field_export(ctx)
+    info = ex["info"]
+    assert (info.cells_x, info.cells_y) == (32, 11) and abs(info.cell_width - 0.46875) < 1e-15
+    c = ext_cells(info)
+    # CSR offsets = counting sort of the oracle's cell index of every star
+    idx = oracle.cell_index(field.xy, c)
+    cnt = np.bincount(idx[idx >= 0], minlength=info.grid_nx * info.grid_ny)
+    assert np.array_equal(ex["cell_start"], np.concatenate([[0], np.cumsum(cnt)]).astype(np.int32))
+    # FP64 coefficients of a sample of ray cells
+    rng = np.random.default_rng(1)
+    rcs = rng.choice(info.cells_x * info.cells_y, 12, replace=False)
+    ext = (rcs // info.cells_x + 1) * info.grid_nx + rcs % info.cells_x + 1
+    ref = oracle.local_coeffs(ext, info.target_order, info.cell_width / math.sqrt(2), field, c)
+    got = ex["coef"][rcs, :, 0] + 1j * ex["coef"][rcs, :, 1]
+    scale = np.abs(ref).max(axis=1, keepdims=True)
+    assert np.max(np.abs(got - ref) / scale) < 1e-11
+    assert rep["cells"] == 352 and rep["train_steps"] == 0
+    ctx.close()
+
+
+def _flat(p):
+    return np.concatenate([p["W1"][:, :32].ravel(), p["W1"][:, 32:].ravel(), p["b1"], p["W2"].ravel(), p["b2"],
+                           p["W3"].ravel(), p["b3"]]).astype(np.float32)
+
+
+def _unflat_grad(g):
+    o = 0
+    W1z = g[o:o + 2048].reshape(64, 32); o += 2048
+    W1u = g[o:o + 128].reshape(64, 2); o += 128
+    b1 = g[o:o + 64]; o += 64
+    W2 = g[o:o + 4096].reshape(64, 64); o += 4096
+    b2 = g[o:o + 64]; o += 64
+    W3 = g[o:o + 128].reshape(2, 64); o += 128
+    b3 = g[o:o + 2]
+    return {"W1": np.concatenate([W1z, W1u], 1), "b1": b1, "W2": W2, "b2": b2, "W3": W3, "b3": b3}
+
+
+@pytest.mark.parametrize("B", [128, 1000])
+def test_network_forward_and_backward_match_the_oracle(B):
+    """The GPU training kernel (BF16 tensor cores, FP32 accumulation) on explicit
+    inputs against the FP64 reference with the same BF16 rounding points.  Bound:
+    2e-3 relative (Frobenius) per gradient block, from one BF16 half-ulp (2^-9)
+    of a rounded operand flipping where FP32 and FP64 pre-rounding values differ."""
+    rng = np.random.default_rng(10 + B)
+    p = mlp.init_params(rng)
+    for k in p:
+        if k.startswith("b"):
+            p[k] = rng.normal(0, 0.1, p[k].shape)
+    flat = _flat(p)
+    p32 = _unflat_grad(flat.astype(np.float64))  # the float32 values the GPU sees
+    z = rng.normal(0, 0.5, (B, 32)).astype(np.float32)
+    u = rng.uniform(-1, 1, (B, 2)).astype(np.float32)
+    t = rng.normal(0, 1, (B, 2)).astype(np.float32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    y = torch.empty((B, 2), dtype=torch.float32, device="cuda")
+    g = torch.empty(flat.shape[0], dtype=torch.float32, device="cuda")
+    dz = torch.empty((B, 32), dtype=torch.float32, device="cuda")
+    loss = M.mlens_ff_eval(dev(flat), dev(z), dev(u), dev(t), y=y, grads=g, dz=dz)
+    lref, gref, yref = mlp.loss_and_grads(p32, z.astype(np.float64), u.astype(np.float64), t.astype(np.float64),
+                                          bf16=True)
+    assert np.allclose(y.cpu().numpy(), yref, rtol=1e-4, atol=1e-5)
+    assert abs(loss - lref) <= 1e-4 * abs(lref)
+    gg = _unflat_grad(g.cpu().numpy().astype(np.float64))
+    for k in gref:
+        if k == "z":
+            continue
+        err = np.linalg.norm(gg[k] - gref[k]) / max(np.linalg.norm(gref[k]), 1e-30)
+        assert err < 2e-3, (k, err)
+    err = np.linalg.norm(dz.cpu().numpy() - gref["z"]) / np.linalg.norm(gref["z"])
+    assert err < 2e-3, ("z", err)
+
+
+def test_series_only_far_field_matches_the_plain_path(field):
+    """Order-16 exact series (truncation ~1e-9 theta_E): the learned path without a
+    network must meet the same oracle bar as the plain path, and nearly equal its map."""
+    ctx = make_ctx(field)
+    rep = M.mlens_fit_far_field(ctx, RAYS, M.fit_params(cells_x=CELLS_X, use_network=0, order=16, tolerance=1e-6))
+    assert rep["cells_fallback"] == 0, rep
+    cl, st, b4 = learned_map(ctx, want_beta=True)
+    c_re, st_re = oracle.rebin_pair(b4, SRC)
+    assert np.array_equal(cl, c_re) and st == st_re
+    cp, stp, _ = plain_map(field)
+    e = compare_to_oracle(field, RAYS, SRC, b4, W.ray_sample(RAYS, 20000, 3))
+    assert e["misbinned_frac"] <= 1e-4 and e["bound_ratio"] <= 1.0, e
+    l1 = np.abs(cl.astype(np.int64) - cp).sum() / cp.sum()
+    assert l1 < 1e-4, l1
+    ctx.close()
+
+
+def test_fallback_cells_reproduce_the_plain_map_bit_for_bit(field):
+    ctx = make_ctx(field)
+    rep = M.mlens_fit_far_field(ctx, RAYS, M.fit_params(cells_x=CELLS_X, use_network=0, order=4, tolerance=0.0))
+    assert rep["cells_fallback"] == rep["cells"]
+    cl, st, b4 = learned_map(ctx, want_beta=True)
+    cp, stp, bp = plain_map(field)
+    assert np.array_equal(cl, cp) and st == stp
+    assert np.array_equal(b4.view(np.uint32), bp.view(np.uint32))
+    ctx.close()
+
+
+def test_trained_network_reduces_the_far_field_error(field):
+    """Order-6 series + network (trained on the GPU) against order-6 series alone, on
+    held-out samples; then the map of the learned path against the plain map."""
+    ctx = make_ctx(field)
+    prm = M.fit_params(cells_x=CELLS_X, use_network=1, order=6, train_samples=1 << 20, epochs=128, tolerance=1e-6)
+    rep = M.mlens_fit_far_field(ctx, RAYS, prm)
+    print("fit", rep)
+    assert rep["train_steps"] == 128 * 16
+    assert rep["val_mean_err_net"] < 0.2 * rep["val_mean_err_series"], rep
+    assert rep["val_max_err_net"] < rep["val_max_err_series"], rep
+    cl, st, _ = learned_map(ctx)
+    cp, _, _ = plain_map(field)
+    l1 = np.abs(cl.astype(np.int64) - cp).sum() / cp.sum()
+    print("map L1 vs plain", l1, "fallback cells", rep["cells_fallback"], "/", rep["cells"])
+    assert l1 <= 1e-3
+    # save / load into a fresh context of the same stars: same map without retraining
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ff.bin")
+        M.mlens_save_far_field(ctx, path)
+        ctx2 = make_ctx(field)
+        M.mlens_load_far_field(ctx2, path)
+        c2, st2, _ = learned_map(ctx2)
+        assert np.array_equal(c2, cl) and st2 == st
+        ctx2.close()
+    ctx.close()
+
+
+def test_learned_shoot_rejects_wrong_state(field):
+    ctx = make_ctx(field)
+    counts = torch.empty(SRC.n, dtype=torch.int32, device="cuda")
+    with pytest.raises(M.MlensError) as ei:
+        M.mlens_shoot_learned(ctx, RAYS, SRC, counts)
+    assert ei.value.code == M.MLENS_ERR_STATE
+    with pytest.raises(M.MlensError) as ei:
+        M.mlens_fit_far_field(ctx, W.Grid(-7.5, 7.5, -2.5, 2.5, 2000, 2048), M.fit_params(cells_x=32))
+    assert ei.value.code == M.MLENS_ERR_ARG
+    ctx.close()
