@@ -61,7 +61,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batched-fields measurement that rides along the main line")
+                    help="skip the batched-fields and learned-far-field measurements that ride along the main line")
+    ap.add_argument("--extras", default="batched,learned", help="comma list of extra sections: batched, learned")
+    ap.add_argument("--learned-tol", type=float, default=5e-6, help="per-cell validation bound of the learned field")
+    ap.add_argument("--learned-order", type=int, default=8)
     return ap.parse_args()
 
 
@@ -222,6 +225,87 @@ def bench_batched(M, torch, steps: int, warmup: int, flush):
         "tuned": {"rays_per_thread": rpt, "star_stage": stage, "tune_s": tune_s},
         "gpu_launches_per_batch": 1,
     }
+
+
+# --------------------------------------------------------------- learned
+def bench_learned(M, torch, steps: int, flush, tol: float, order: int):
+    """10^6 stars, 32768^2 rays, 4096^2 map: the learned far field (fit on the GPU,
+    then one persistent launch per map) against the plain direct sum.  The plain
+    map of the whole grid takes minutes, so both paths are compared on a strip of
+    768 ray rows (two cell rows, 2.5e13 interactions for the plain path): the strip
+    gives the plain path's throughput and the map error of the learned path
+    (relative L1 of the strip maps).  Done with and without the network."""
+    wl = W.config("learned")
+    f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
+    stream = torch.cuda.current_stream()
+    ctx = M.mlens_create(f.xy, f.m, f.kappa_c, f.gamma1, f.gamma2, M.MLENS_PREC_FP32)
+    dy = (rays.y1 - rays.y0) / rays.ny
+    j0 = (rays.ny // 2 // 384) * 384
+    j1 = j0 + 768
+    strip = W.Grid(rays.x0, rays.x1, rays.y0 + j0 * dy, rays.y0 + j1 * dy, rays.nx, j1 - j0)
+    cp = torch.empty(src.n, dtype=torch.int32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    M.mlens_shoot(ctx, strip, src, cp)
+    e1.record(stream)
+    e1.synchronize()
+    plain_strip_ms = e0.elapsed_time(e1)
+    plain_rate = strip.n * f.n / (plain_strip_ms / 1e3)
+    plain_full_s = rays.n * f.n / plain_rate
+    cp_h = cp.cpu().numpy().view(np.uint32).astype(np.int64)
+    out = {"workload": f"learned: {f.n} stars, {rays.nx}^2 rays, {src.nx}^2 map, 256 x 86 cells of 0.46875 theta_E",
+           "plain": {"interactions_per_s": plain_rate, "map_s_estimated": plain_full_s,
+                     "measured_on": f"rows [{j0},{j1}) of the grid ({strip.n} rays)"}}
+    for use_net in (1, 0):
+        t0 = time.perf_counter()
+        rep = M.mlens_fit_far_field(ctx, rays, M.fit_params(cells_x=256, order=order, use_network=use_net,
+                                                            tolerance=tol))
+        fit_s = time.perf_counter() - t0
+        cl = torch.empty(src.n, dtype=torch.int32, device="cuda")
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        M.mlens_shoot_learned(ctx, rays, src, cl, rows=(j0, j1))
+        b.record(stream)
+        b.synchronize()
+        strip_s = a.elapsed_time(b) / 1e3
+        cl_h = cl.cpu().numpy().view(np.uint32).astype(np.int64)
+        if use_net:
+            # the whole map, timed (a few seconds); the series-only ablation spends most of
+            # its time in fallback tiles (minutes per map), so it is timed on the strip only
+            counts = torch.empty(src.n, dtype=torch.int32, device="cuda")
+            M.mlens_shoot_learned(ctx, rays, src, counts)  # warm-up
+            ms = []
+            for i in range(steps):
+                flush.fill_(float(i))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                M.mlens_shoot_learned(ctx, rays, src, counts)
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            learned_s = statistics.mean(ms) / 1e3
+            timing = f"whole map, mean of {steps} CUDA-event-timed launches"
+        else:
+            learned_s = strip_s * rays.n / strip.n
+            timing = f"estimated from the strip ({strip_s:.3f} s for rows [{j0},{j1}))"
+        l1 = float(np.abs(cl_h - cp_h).sum() / max(cp_h.sum(), 1))
+        key = "with_network" if use_net else "series_only"
+        out[key] = {
+            "map_s": learned_s, "map_s_timing": timing, "maps_per_s": 1.0 / learned_s,
+            "effective_interactions_per_s": rays.n * f.n / learned_s,
+            "speedup_vs_plain": plain_full_s / learned_s,
+            "map_rel_l1_vs_plain": l1, "equal_error": l1 <= 1e-3,
+            "fallback_cells": rep["cells_fallback"], "cells": rep["cells"],
+            "fallback_tiles": rep["tiles_fallback"], "tiles": rep["tiles"],
+            "val_mean_err": rep["val_mean_err_net"] if use_net else rep["val_mean_err_series"],
+            "val_max_err": rep["val_max_err_net"] if use_net else rep["val_max_err_series"],
+            "fit_s": fit_s, "fit_seconds": {"coefficients": rep["seconds_coefficients"],
+                                            "train": rep["seconds_train"], "validate": rep["seconds_validate"]},
+            "train_steps": rep["train_steps"], "order": order, "tolerance": tol,
+        }
+    ctx.close()
+    return out
 
 
 # ------------------------------------------------------------------- main
@@ -391,11 +475,16 @@ def run_mine(args):
         "device": props.name,
     }
     line["config"]["rays_per_thread"] = args.rays_per_thread
+    extras = set(x for x in args.extras.split(",") if x)
     if not args.no_extras and world == 1 and args.workload == "paper" and args.rays_scale == 1.0:
-        bt = bench_batched(M, torch, max(2, min(args.steps, 5)), 2, flush)
-        peak_b = n_sm * MUFU_RCP_PER_SM_CLK * SM_MAX_MHZ * 1e6
-        bt["roofline_frac"] = bt["interactions_per_s"] / peak_b
-        line["batched"] = bt
+        if "batched" in extras:
+            bt = bench_batched(M, torch, max(2, min(args.steps, 5)), 2, flush)
+            peak_b = n_sm * MUFU_RCP_PER_SM_CLK * SM_MAX_MHZ * 1e6
+            bt["roofline_frac"] = bt["interactions_per_s"] / peak_b
+            line["batched"] = bt
+        if "learned" in extras:
+            line["learned"] = bench_learned(M, torch, max(2, min(args.steps, 3)), flush, args.learned_tol,
+                                            args.learned_order)
     if not args.no_cpu_baseline and world == 1:
         v, cores, sample = cpu_oracle_rate(f, rays, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "interactions/s", "cores": cores, "kind": "oracle",

@@ -329,9 +329,13 @@ int mlens_fit_far_field(mlens_ctx *ctx, const mlens_grid *rays, const mlens_fit_
  * launch over the tiles of `rays` (which must be the grid of the fit).  Near
  * stars exact, far field from the series and the network, flagged cells exact.
  * beta_dev as for mlens_shoot_beta (NULL to skip); other arguments as mlens_shoot.
+ * row_begin/row_end restrict the call to ray rows [row_begin, row_end) (both
+ * multiples of 32; 0, 0 = all rows); a restricted call copies a filtered work
+ * list into a device buffer the context allocates on first use.
  */
 int mlens_shoot_learned(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid *src, uint32_t *counts_dev,
-                        void *beta_dev, uint32_t flags, mlens_stats *stats_host, void *stream);
+                        void *beta_dev, int32_t row_begin, int32_t row_end, uint32_t flags, mlens_stats *stats_host,
+                        void *stream);
 
 /* Layout and fit report of the context's far field. */
 int mlens_far_field_get_info(mlens_ctx *ctx, mlens_far_field_info *out);

@@ -38,6 +38,8 @@ struct FarState {
     double *vsum = nullptr;
     int *items = nullptr;
     int64_t nitems = 0, nfallback_tiles = 0;
+    std::vector<int> h_items;      // host copy of the work list
+    int *sub_items = nullptr;      // filtered work list for row-restricted calls
     unsigned long long *counter = nullptr;
     int grid = 0;
     mlens_fit_report report{};
@@ -77,6 +79,7 @@ void free_state(FarState *f)
     ffree(f->params), ffree(f->m), ffree(f->v), ffree(f->grads), ffree(f->loss);
     ffree(f->w1zb), ffree(f->w2b), ffree(f->w2tb), ffree(f->w1ztb), ffree(f->ec), ffree(f->flags);
     ffree(f->vmax_net), ffree(f->vmax_series), ffree(f->vsum), ffree(f->items), ffree(f->counter);
+    ffree(f->sub_items);
     f->ready = false;
 }
 
@@ -221,6 +224,8 @@ int schedule(FarState *f, cudaStream_t s)
     ffree(f->items);
     FCUDA(cudaMalloc(&f->items, sizeof(int) * std::max<int64_t>(f->nitems, 1)), "cudaMalloc(items)");
     FCUDA(cudaMemcpy(f->items, heavy.data(), sizeof(int) * f->nitems, cudaMemcpyHostToDevice), "memcpy(items)");
+    f->h_items = heavy;
+    ffree(f->sub_items);
     int nflag = 0;
     double mx_n = 0.0, mx_s = 0.0;
     for (int i = 0; i < f->nrc; ++i) {
@@ -384,7 +389,8 @@ int mlens_fit_far_field(mlens_ctx *ctx, const mlens_grid *rays, const mlens_fit_
 }
 
 int mlens_shoot_learned(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid *src, uint32_t *counts_dev,
-                        void *beta_dev, uint32_t flags, mlens_stats *stats_host, void *stream)
+                        void *beta_dev, int32_t row_begin, int32_t row_end, uint32_t flags, mlens_stats *stats_host,
+                        void *stream)
 {
     if (!ctx || !rays || !src || !counts_dev) return ffail(MLENS_ERR_ARG, "NULL argument");
     if (!ctx->ff || !ctx->ff->ready) return ffail(MLENS_ERR_STATE, "no far field fitted on this context");
@@ -396,10 +402,30 @@ int mlens_shoot_learned(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid
     if (((uintptr_t)counts_dev & 3u) || (beta_dev && ((uintptr_t)beta_dev & 15u)))
         return ffail(MLENS_ERR_ARG, "misaligned buffer");
     if (flags & ~MLENS_ACCUMULATE) return ffail(MLENS_ERR_ARG, "unknown flag bits");
+    const bool all_rows = row_begin == 0 && row_end == 0;
+    if (!all_rows && (row_begin < 0 || row_end > rays->ny || row_begin >= row_end || row_begin % 32 || row_end % 32))
+        return ffail(MLENS_ERR_ARG, "row range must be 0 <= row_begin < row_end <= rays.ny, multiples of 32");
     int dev = -1;
     FCUDA(cudaGetDevice(&dev), "cudaGetDevice");
     if (dev != ctx->device) return ffail(MLENS_ERR_STATE, "the context belongs to another device");
     cudaStream_t s = (cudaStream_t)stream;
+    const int *items = f->items;
+    int64_t nitems = f->nitems, nrows_total = (int64_t)rays->nx * rays->ny;
+    if (!all_rows) {
+        const int ntx = (rays->nx + 63) / 64;
+        std::vector<int> sub;
+        for (int t : f->h_items) {
+            const int by = t / ntx;
+            if (by * 32 >= row_begin && by * 32 < row_end) sub.push_back(t);
+        }
+        if (!f->sub_items) FCUDA(cudaMalloc(&f->sub_items, sizeof(int) * std::max<int64_t>(f->nitems, 1)), "cudaMalloc");
+        FCUDA(cudaMemcpyAsync(f->sub_items, sub.data(), sizeof(int) * sub.size(), cudaMemcpyHostToDevice, s),
+              "memcpy(sub items)");
+        FCUDA(cudaStreamSynchronize(s), "sync");
+        items = f->sub_items;
+        nitems = (int64_t)sub.size();
+        nrows_total = (int64_t)rays->nx * (row_end - row_begin);
+    }
     if (!(flags & MLENS_ACCUMULATE))
         FCUDA(cudaMemsetAsync(counts_dev, 0, (size_t)src->nx * src->ny * sizeof(uint32_t), s), "memset(counts)");
     FCUDA(cudaMemsetAsync(ctx->d_stats, 0, 3 * sizeof(unsigned long long), s), "memset(stats)");
@@ -424,15 +450,15 @@ int mlens_shoot_learned(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid
     L.w2b = f->w2b;
     L.pe = f->pe;
     L.use_net = f->use_net;
-    L.items = f->items;
-    L.nitems = f->nitems;
+    L.items = items;
+    L.nitems = nitems;
     L.counter = f->counter;
     FCUDA(ff_shoot_learned(L, f->grid, s), "learned shoot launch");
     if (stats_host) {
         unsigned long long h[3];
         FCUDA(cudaMemcpyAsync(h, ctx->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s), "memcpy(stats)");
         FCUDA(cudaStreamSynchronize(s), "sync");
-        stats_host->rays_total = (uint64_t)rays->nx * (uint64_t)rays->ny;
+        stats_host->rays_total = (uint64_t)nrows_total;
         stats_host->rays_binned = h[0];
         stats_host->rays_out = h[1];
         stats_host->rays_nan = h[2];

@@ -107,7 +107,7 @@ SIGNATURES = {
     "mlens_shoot_batch": (C.c_int, [C.POINTER(_vp), C.c_int32, _gp, _gp, C.POINTER(_vp), C.c_uint32, _sp, _vp]),
     "mlens_fit_params_default": (None, [C.POINTER(mlens_fit_params)]),
     "mlens_fit_far_field": (C.c_int, [_vp, _gp, C.POINTER(mlens_fit_params), C.POINTER(mlens_fit_report), _vp]),
-    "mlens_shoot_learned": (C.c_int, [_vp, _gp, _gp, _vp, _vp, C.c_uint32, _sp, _vp]),
+    "mlens_shoot_learned": (C.c_int, [_vp, _gp, _gp, _vp, _vp, C.c_int32, C.c_int32, C.c_uint32, _sp, _vp]),
     "mlens_far_field_get_info": (C.c_int, [_vp, C.POINTER(mlens_far_field_info)]),
     "mlens_far_field_export": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "mlens_save_far_field": (C.c_int, [_vp, C.c_char_p]),
@@ -351,11 +351,13 @@ def mlens_fit_far_field(ctx: Ctx, rays, params: mlens_fit_params = None, stream=
     return rep.asdict()
 
 
-def mlens_shoot_learned(ctx: Ctx, rays, src, counts, beta=None, flags: int = 0, stats: bool = False, stream=None):
+def mlens_shoot_learned(ctx: Ctx, rays, src, counts, beta=None, rows=(0, 0), flags: int = 0, stats: bool = False,
+                        stream=None):
     st = mlens_stats()
     g, s = grid(rays), grid(src)
     _check(load().mlens_shoot_learned(ctx.handle, C.byref(g), C.byref(s), _dev_ptr(counts), _dev_ptr(beta),
-                                      int(flags), C.byref(st) if stats else None, _stream_ptr(stream)))
+                                      int(rows[0]), int(rows[1]), int(flags), C.byref(st) if stats else None,
+                                      _stream_ptr(stream)))
     return st.asdict() if stats else None
 
 

@@ -196,3 +196,18 @@ def test_learned_shoot_rejects_wrong_state(field):
         M.mlens_fit_far_field(ctx, W.Grid(-7.5, 7.5, -2.5, 2.5, 2000, 2048), M.fit_params(cells_x=32))
     assert ei.value.code == M.MLENS_ERR_ARG
     ctx.close()
+
+
+def test_row_restricted_calls_add_up_to_the_full_map(field):
+    ctx = make_ctx(field)
+    M.mlens_fit_far_field(ctx, RAYS, M.fit_params(cells_x=CELLS_X, use_network=0, order=8, tolerance=2e-6))
+    full, st, _ = learned_map(ctx)
+    acc = torch.zeros(SRC.n, dtype=torch.int32, device="cuda")
+    bounds = [0, 192, 1024, 1056, 2048]
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        M.mlens_shoot_learned(ctx, RAYS, SRC, acc, rows=(a, b), flags=M.MLENS_ACCUMULATE)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(acc, SRC), full)
+    with pytest.raises(M.MlensError):
+        M.mlens_shoot_learned(ctx, RAYS, SRC, acc, rows=(0, 100))
+    ctx.close()
