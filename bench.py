@@ -73,6 +73,26 @@ def dist_env():
         os.environ.get("LOCAL_RANK", "0"))
 
 
+def rank_field(wl, rank: int):
+    """Weak scaling: rank 0 shoots the workload's own field, rank r > 0 an independent
+    field of the same size and lens terms (seed offset by r); no data is exchanged."""
+    f = wl.fields[0]
+    if rank == 0:
+        return f
+    return W.random_field(W.SEED_BASE + 100 + rank, f.n, f.kappa_star, f.kappa_c, f.gamma1, f.gamma2)
+
+
+def max_over_ranks(seconds: float, device=None) -> float:
+    """The job's time is the slowest rank's (torch.distributed all-reduce MAX)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return seconds
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload_config(name, wl, precision, note_l2):
     f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
     return {
@@ -369,8 +389,7 @@ def run_mine(args):
 
     wl = W.config(args.workload, rays_scale=args.rays_scale)
     f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
-    if world > 1 and rank > 0:  # an independent field of the same size per rank
-        f = W.random_field(W.SEED_BASE + 100 + rank, f.n, f.kappa_star, f.kappa_c, f.gamma1, f.gamma2)
+    f = rank_field(wl, rank)
     n_inter = rays.n * f.n
 
     ctx = M.mlens_create(f.xy, f.m, f.kappa_c, f.gamma1, f.gamma2, prec)
@@ -405,10 +424,7 @@ def run_mine(args):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     dev_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([dev_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_s = float(t.item())
+    dev_s = max_over_ranks(dev_s, device="cuda")
     value = n_inter * args.steps * world / dev_s
     kernel_ms = statistics.mean(step_ms)
 

@@ -51,7 +51,7 @@ def position_rounding(rays, rays_per_thread=8):
     return 2.0 ** -22 * ext
 
 
-def compare_to_oracle(f, rays, src, b4, idx=None, nthreads=0, rays_per_thread=8):
+def compare_to_oracle(f, rays, src, b4, idx=None, nthreads=0, rays_per_thread=8, presampled=False):
     """Per-ray comparison of GPU float-pair beta (rows idx of the grid, or all rays)
     with the FP64 oracle.  Returns a dict of error statistics.
 
@@ -62,6 +62,8 @@ def compare_to_oracle(f, rays, src, b4, idx=None, nthreads=0, rays_per_thread=8)
     if idx is None:
         idx = np.arange(rays.n, dtype=np.int64)
         bsel = b4
+    elif presampled:
+        bsel = b4  # already the rows of idx
     else:
         bsel = b4[idx]
     b64 = oracle.beta_rays(rays, idx, f, nthreads)
