@@ -56,10 +56,13 @@ def parse():
     ap.add_argument("--workload", default="paper", choices=["paper", "tiny", "precision"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_naive", "fp64"])
     ap.add_argument("--rays-per-thread", type=int, default=8, choices=[4, 8])
+    ap.add_argument("--fma-pairs", type=int, default=0, choices=[0, 1],
+                    help="ray pairs per thread whose reciprocal runs on the FMA pipe (Newton-Raphson)")
     ap.add_argument("--rays-scale", type=float, default=1.0,
                     help="shrink the ray grid per axis (same field, boxes and map) for profiling runs")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--print-kernel-hash", action="store_true", help="print the FP32 kernel source hash and exit")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-fields and learned-far-field measurements that ride along the main line")
     ap.add_argument("--extras", default="batched,learned", help="comma list of extra sections: batched, learned")
@@ -160,15 +163,27 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- profiles
-def profile_traffic(kernel_key: str, src_file: str):
+KERNEL_SOURCES = ("shoot_fp32.cu", "tile.cuh", "mlens_dev.cuh", "mlens_internal.h")
+
+
+def kernel_source_hash() -> str:
+    """Hash of the sources the FP32 shooting kernel is compiled from."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1703_09707_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kernel_key: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel source (else None)."""
+    current kernel sources (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as fh:
             d = json.load(fh)
         ent = d[kernel_key]
-        h = hashlib.sha256(open(src_file, "rb").read()).hexdigest()[:16]
+        h = kernel_source_hash()
         if ent.get("source_sha256_16") != h:
             return None, ent
         return float(ent["dram_bytes_per_launch"]), ent
@@ -208,7 +223,7 @@ def bench_batched(M, torch, steps: int, warmup: int, flush):
     stream = torch.cuda.current_stream()
     b = M.mlens_batch_create(ctxs, wl.rays, wl.srcs, counts)
     t0 = time.perf_counter()
-    rpt, stage, tune_ms = M.mlens_batch_tune(b)
+    rpt, stage, fma, tune_ms = M.mlens_batch_tune(b)
     tune_s = time.perf_counter() - t0
 
     def timed(fn):
@@ -228,7 +243,7 @@ def bench_batched(M, torch, steps: int, warmup: int, flush):
 
     persistent_ms = timed(lambda: M.mlens_batch_run(b))
     for c in ctxs:
-        M.mlens_set_tuning(c, rpt, stage)
+        M.mlens_set_tuning(c, rpt, stage, fma)
     per_field_ms = timed(lambda: [M.mlens_shoot(c, r, s, k) for c, r, s, k in zip(ctxs, wl.rays, wl.srcs, counts)])
     b.close()
     for c in ctxs:
@@ -242,7 +257,7 @@ def bench_batched(M, torch, steps: int, warmup: int, flush):
         "speedup_vs_per_field_launches": per_field_ms / persistent_ms,
         "interactions_per_s": inter / (persistent_ms / 1e3),
         "ms_per_batch": persistent_ms, "ms_per_batch_per_field_launches": per_field_ms,
-        "tuned": {"rays_per_thread": rpt, "star_stage": stage, "tune_s": tune_s},
+        "tuned": {"rays_per_thread": rpt, "star_stage": stage, "fma_pairs": fma, "tune_s": tune_s},
         "gpu_launches_per_batch": 1,
     }
 
@@ -393,7 +408,7 @@ def run_mine(args):
     n_inter = rays.n * f.n
 
     ctx = M.mlens_create(f.xy, f.m, f.kappa_c, f.gamma1, f.gamma2, prec)
-    M.mlens_set_tuning(ctx, args.rays_per_thread)
+    M.mlens_set_tuning(ctx, args.rays_per_thread, 0, args.fma_pairs)
     counts = torch.empty(src.n, dtype=torch.int32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -439,7 +454,7 @@ def run_mine(args):
     e0.record(stream)
     for _ in range(e2e_steps):
         c2 = M.mlens_create(f.xy, f.m, f.kappa_c, f.gamma1, f.gamma2, prec)
-        M.mlens_set_tuning(c2, args.rays_per_thread)
+        M.mlens_set_tuning(c2, args.rays_per_thread, 0, args.fma_pairs)
         M.mlens_shoot(c2, rays, src, counts)
         host_counts.copy_(counts, non_blocking=True)
         torch.cuda.current_stream().synchronize()
@@ -464,9 +479,8 @@ def run_mine(args):
     n_sm = props.multi_processor_count
     peak = n_sm * MUFU_RCP_PER_SM_CLK * SM_MAX_MHZ * 1e6
     achieved = n_inter / (kernel_ms / 1e3)
-    kern_src = os.path.join(ROOT, "paper_1703_09707_gb300", "csrc", "shoot_fp32.cu")
-    key = f"shoot_fp32_{args.workload}_rpt{args.rays_per_thread}"
-    traffic, _ = profile_traffic(key, kern_src) if args.precision != "fp64" else (None, None)
+    key = f"shoot_fp32_{args.workload}_rpt{args.rays_per_thread}_fma{args.fma_pairs}"
+    traffic, _ = profile_traffic(key) if args.precision != "fp64" else (None, None)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "interactions/s", "frac": achieved / peak,
             "traffic": traffic,
             "peak_basis": f"MUFU.RCP {MUFU_RCP_PER_SM_CLK}/SM/clk x {n_sm} SMs x {SM_MAX_MHZ:.0f} MHz (max SM clock)",
@@ -491,6 +505,7 @@ def run_mine(args):
         "device": props.name,
     }
     line["config"]["rays_per_thread"] = args.rays_per_thread
+    line["config"]["fma_pairs"] = args.fma_pairs
     extras = set(x for x in args.extras.split(",") if x)
     if not args.no_extras and world == 1 and args.workload == "paper" and args.rays_scale == 1.0:
         if "batched" in extras:
@@ -515,6 +530,9 @@ def run_mine(args):
 
 def main():
     args = parse()
+    if args.print_kernel_hash:
+        print(kernel_source_hash())
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_mine(args)

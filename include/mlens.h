@@ -104,13 +104,15 @@ int mlens_set_precision(mlens_ctx *ctx, int32_t precision);
 /*
  * mlens_set_tuning -- launch shape of the FP32 kernels for later calls on this
  * context: rays_per_thread in {4, 8} (tile 64 x 16 or 64 x 32 rays per CTA of
- * 256 threads) and star_stage in {128, 256, 512} stars staged through shared
- * memory at a time (0 = 256).  The stage size never changes the arithmetic.
- * Different tile shapes put tile centres in different places, so beta can
- * differ in its last bits between shapes (never by more than the error bar); a
- * given shape is deterministic.  Defaults: 8 rays per thread, 256 stars.
+ * 256 threads), star_stage in {128, 256, 512} stars staged through shared
+ * memory at a time (0 = 256), and fma_pairs in {0, 1}: how many of a thread's
+ * ray pairs take their reciprocals from Newton-Raphson iterations on the FMA
+ * pipe instead of the MUFU unit (which is the bound).  The stage size never
+ * changes the arithmetic; the tile shape (it moves the tile centres) and the
+ * reciprocal source change beta in its last bits (never by more than the error
+ * bar).  A given setting is deterministic.  Defaults: 8, 256, 0.
  */
-int mlens_set_tuning(mlens_ctx *ctx, int32_t rays_per_thread, int32_t star_stage);
+int mlens_set_tuning(mlens_ctx *ctx, int32_t rays_per_thread, int32_t star_stage, int32_t fma_pairs);
 
 /*
  * mlens_shoot -- Algorithm 1 over a whole ray grid: deflect every ray by Eq. (3),
@@ -226,20 +228,22 @@ typedef struct mlens_batch mlens_batch;
 int mlens_batch_create(mlens_batch **out, mlens_ctx *const *ctxs, int32_t nfields, const mlens_grid *rays,
                        const mlens_grid *srcs, uint32_t *const *counts_dev, uint32_t flags);
 
-/* Set the launch shape (rays_per_thread 4 or 8; star_stage 0=256, 128, 256, 512).
- * Waits for the device; the graph is captured again at the next run. */
-int mlens_batch_set_tuning(mlens_batch *b, int32_t rays_per_thread, int32_t star_stage);
+/* Set the launch shape (as mlens_set_tuning).  Waits for the device; the graph is
+ * captured again at the next run. */
+int mlens_batch_set_tuning(mlens_batch *b, int32_t rays_per_thread, int32_t star_stage, int32_t fma_pairs);
 
 /*
- * mlens_batch_tune -- the autotuner: time every launch shape on this batch (a
- * warm-up and two timed replays each, CUDA events on `stream`), keep the fastest
- * and report it (any output pointer may be NULL; *best_ms = -1 when the shape came
- * from the cache).  Results are cached per process by device and workload
+ * mlens_batch_tune -- the autotuner: time the launch shapes (rays per thread 8
+ * or 4, star stage 256 or 512, fma_pairs 0 or 1) on this batch (a warm-up and
+ * two timed replays each, CUDA events on `stream`), keep the fastest and report
+ * it (any output pointer may be NULL; *best_ms = -1 when the shape came from the
+ * cache).  Results are cached per process by device and workload
  * signature (field count, ray grid, star counts bucketed by powers of two), and
  * appended to / read from the text file named by the environment variable
  * MLENS_TUNE_CACHE when it is set.  The maps are overwritten by the trial runs.
  */
-int mlens_batch_tune(mlens_batch *b, void *stream, int32_t *rays_per_thread, int32_t *star_stage, double *best_ms);
+int mlens_batch_tune(mlens_batch *b, void *stream, int32_t *rays_per_thread, int32_t *star_stage, int32_t *fma_pairs,
+                     double *best_ms);
 
 /*
  * mlens_batch_run -- shoot every field (graph launch on `stream`; the first run of a

@@ -139,7 +139,8 @@ int shoot_impl(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid *src, ui
     if (ctx->precision == MLENS_PREC_FP64)
         e = launch_shoot_fp64(a, s);
     else
-        e = launch_shoot_fp32(a, ctx->pairs_per_thread, ctx->precision == MLENS_PREC_FP32_NAIVE, s, ctx->star_stage);
+        e = launch_shoot_fp32(a, ctx->pairs_per_thread, ctx->precision == MLENS_PREC_FP32_NAIVE, s, ctx->star_stage,
+                              ctx->fma_pairs);
     if (e != cudaSuccess) return cuda_fail(e, "shoot kernel launch");
     if (stats) return read_stats(ctx->d_stats, (uint64_t)rays->nx * (uint64_t)rays->ny, stats, s);
     return MLENS_OK;
@@ -266,14 +267,16 @@ int mlens_set_precision(mlens_ctx *ctx, int32_t precision)
     return MLENS_OK;
 }
 
-int mlens_set_tuning(mlens_ctx *ctx, int32_t rays_per_thread, int32_t star_stage)
+int mlens_set_tuning(mlens_ctx *ctx, int32_t rays_per_thread, int32_t star_stage, int32_t fma_pairs)
 {
     if (!ctx) return fail(MLENS_ERR_ARG, "context is NULL");
     if (rays_per_thread != 4 && rays_per_thread != 8) return fail(MLENS_ERR_ARG, "rays_per_thread must be 4 or 8");
     if (star_stage != 0 && star_stage != 128 && star_stage != 256 && star_stage != 512)
         return fail(MLENS_ERR_ARG, "star_stage must be 0 (default), 128, 256 or 512");
+    if (fma_pairs != 0 && fma_pairs != 1) return fail(MLENS_ERR_ARG, "fma_pairs must be 0 or 1");
     ctx->pairs_per_thread = rays_per_thread / 2;
     ctx->star_stage = star_stage ? star_stage : 256;
+    ctx->fma_pairs = fma_pairs;
     return MLENS_OK;
 }
 

@@ -40,6 +40,7 @@ struct mlens_batch {
     unsigned long long *d_stats = nullptr;  // 3 per field
     int pairs_per_thread = 4;
     int star_stage = 256;
+    int fma_pairs = 0;
     int64_t total = 0;
     int grid = 0;
     cudaStream_t cap = nullptr;
@@ -101,7 +102,7 @@ int build_tables(mlens_batch *b)
     BCUDA(cudaMemcpy(b->d_order, order.data(), sizeof(int) * nf, cudaMemcpyHostToDevice), "cudaMemcpy(order)");
     BCUDA(cudaMemcpy(b->d_begin, begin.data(), sizeof(int64_t) * (nf + 1), cudaMemcpyHostToDevice),
           "cudaMemcpy(begin)");
-    BCUDA(batch_grid_size(b->pairs_per_thread, b->star_stage, &b->grid), "occupancy query");
+    BCUDA(batch_grid_size(b->pairs_per_thread, b->star_stage, &b->grid, b->fma_pairs), "occupancy query");
     return MLENS_OK;
 }
 
@@ -123,7 +124,7 @@ int capture(mlens_batch *b)
             e = cudaMemsetAsync(b->counts[f], 0, (size_t)b->srcs[f].nx * b->srcs[f].ny * sizeof(uint32_t), b->cap);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_stats, 0, sizeof(unsigned long long) * 3 * b->nfields, b->cap);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), b->cap);
-    if (e == cudaSuccess) e = launch_shoot_batch(L, b->pairs_per_thread, b->star_stage, b->cap);
+    if (e == cudaSuccess) e = launch_shoot_batch(L, b->pairs_per_thread, b->star_stage, b->cap, b->fma_pairs);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
     if (e != cudaSuccess) {
@@ -136,15 +137,17 @@ int capture(mlens_batch *b)
     return MLENS_OK;
 }
 
-int set_shape(mlens_batch *b, int rpt, int stage)
+int set_shape(mlens_batch *b, int rpt, int stage, int fma)
 {
     if (rpt != 4 && rpt != 8) return bfail(MLENS_ERR_ARG, "rays_per_thread must be 4 or 8");
     if (stage != 128 && stage != 256 && stage != 512) return bfail(MLENS_ERR_ARG, "star_stage must be 128, 256 or 512");
-    if (b->pairs_per_thread == rpt / 2 && b->star_stage == stage && b->exec) return MLENS_OK;
+    if (fma != 0 && fma != 1) return bfail(MLENS_ERR_ARG, "fma_pairs must be 0 or 1");
+    if (b->pairs_per_thread == rpt / 2 && b->star_stage == stage && b->fma_pairs == fma && b->exec) return MLENS_OK;
     // the tables are rewritten below: no launch of the old shape may still read them
     BCUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
     b->pairs_per_thread = rpt / 2;
     b->star_stage = stage;
+    b->fma_pairs = fma;
     drop_graph(b);
     return build_tables(b);
 }
@@ -152,7 +155,10 @@ int set_shape(mlens_batch *b, int rpt, int stage)
 // process-wide cache of tuned shapes, keyed by device and workload signature;
 // also read from / appended to the file named by MLENS_TUNE_CACHE, if set
 std::mutex g_tune_mu;
-std::map<std::string, std::pair<int, int>> g_tune;
+struct Shape {
+    int rpt, stage, fma;
+};
+std::map<std::string, Shape> g_tune;
 bool g_tune_file_read = false;
 
 std::string signature(const mlens_batch *b)
@@ -179,19 +185,19 @@ void read_tune_file()
     FILE *fh = fopen(path, "r");
     if (!fh) return;
     char key[1024];
-    int rpt, st;
+    int rpt, st, fm;
     double ms;
-    while (fscanf(fh, "%1023s %d %d %lf", key, &rpt, &st, &ms) == 4) g_tune[key] = {rpt, st};
+    while (fscanf(fh, "%1023s %d %d %d %lf", key, &rpt, &st, &fm, &ms) == 5) g_tune[key] = {rpt, st, fm};
     fclose(fh);
 }
 
-void append_tune_file(const std::string &key, int rpt, int st, double ms)
+void append_tune_file(const std::string &key, int rpt, int st, int fm, double ms)
 {
     const char *path = getenv("MLENS_TUNE_CACHE");
     if (!path) return;
     FILE *fh = fopen(path, "a");
     if (!fh) return;
-    fprintf(fh, "%s %d %d %.6f\n", key.c_str(), rpt, st, ms);
+    fprintf(fh, "%s %d %d %d %.6f\n", key.c_str(), rpt, st, fm, ms);
     fclose(fh);
 }
 
@@ -269,10 +275,10 @@ int mlens_batch_create(mlens_batch **out, mlens_ctx *const *ctxs, int32_t nfield
     return MLENS_OK;
 }
 
-int mlens_batch_set_tuning(mlens_batch *b, int32_t rays_per_thread, int32_t star_stage)
+int mlens_batch_set_tuning(mlens_batch *b, int32_t rays_per_thread, int32_t star_stage, int32_t fma_pairs)
 {
     if (!b) return bfail(MLENS_ERR_ARG, "batch is NULL");
-    return set_shape(b, rays_per_thread, star_stage ? star_stage : 256);
+    return set_shape(b, rays_per_thread, star_stage ? star_stage : 256, fma_pairs);
 }
 
 int mlens_batch_run(mlens_batch *b, mlens_stats *stats_host, void *stream)
@@ -302,7 +308,8 @@ int mlens_batch_run(mlens_batch *b, mlens_stats *stats_host, void *stream)
     return MLENS_OK;
 }
 
-int mlens_batch_tune(mlens_batch *b, void *stream, int32_t *rays_per_thread, int32_t *star_stage, double *best_ms)
+int mlens_batch_tune(mlens_batch *b, void *stream, int32_t *rays_per_thread, int32_t *star_stage, int32_t *fma_pairs,
+                     double *best_ms)
 {
     if (!b) return bfail(MLENS_ERR_ARG, "batch is NULL");
     cudaStream_t s = (cudaStream_t)stream;
@@ -312,25 +319,27 @@ int mlens_batch_tune(mlens_batch *b, void *stream, int32_t *rays_per_thread, int
         read_tune_file();
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
-            int rc = set_shape(b, it->second.first, it->second.second);
+            int rc = set_shape(b, it->second.rpt, it->second.stage, it->second.fma);
             if (rc != MLENS_OK) return rc;
-            if (rays_per_thread) *rays_per_thread = it->second.first;
-            if (star_stage) *star_stage = it->second.second;
+            if (rays_per_thread) *rays_per_thread = it->second.rpt;
+            if (star_stage) *star_stage = it->second.stage;
+            if (fma_pairs) *fma_pairs = it->second.fma;
             if (best_ms) *best_ms = -1.0;  // taken from the cache, not timed now
             return MLENS_OK;
         }
     }
     const int cand_rpt[2] = {8, 4};
-    const int cand_st[3] = {256, 128, 512};
+    const int cand_st[2] = {256, 512};
     cudaEvent_t e0, e1;
     BCUDA(cudaEventCreate(&e0), "cudaEventCreate");
     BCUDA(cudaEventCreate(&e1), "cudaEventCreate");
     double best = 1e300;
-    int brpt = 8, bst = 256;
+    int brpt = 8, bst = 256, bfm = 0;
     int rc = MLENS_OK;
-    for (int i = 0; i < 2 && rc == MLENS_OK; ++i) {
-        for (int j = 0; j < 3 && rc == MLENS_OK; ++j) {
-            if ((rc = set_shape(b, cand_rpt[i], cand_st[j])) != MLENS_OK) break;
+    for (int c = 0; c < 8 && rc == MLENS_OK; ++c) {
+        const int i = (c / 2) % 2, j = c % 2, fm = c / 4;
+        {
+            if ((rc = set_shape(b, cand_rpt[i], cand_st[j], fm)) != MLENS_OK) break;
             if ((rc = mlens_batch_run(b, nullptr, stream)) != MLENS_OK) break;  // warm-up + capture
             double tmin = 1e300;
             for (int r = 0; r < 2; ++r) {
@@ -350,20 +359,22 @@ int mlens_batch_tune(mlens_batch *b, void *stream, int32_t *rays_per_thread, int
                 best = tmin;
                 brpt = cand_rpt[i];
                 bst = cand_st[j];
+                bfm = fm;
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != MLENS_OK) return rc;
-    if ((rc = set_shape(b, brpt, bst)) != MLENS_OK) return rc;
+    if ((rc = set_shape(b, brpt, bst, bfm)) != MLENS_OK) return rc;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune[key] = {brpt, bst};
-        append_tune_file(key, brpt, bst, best);
+        g_tune[key] = {brpt, bst, bfm};
+        append_tune_file(key, brpt, bst, bfm, best);
     }
     if (rays_per_thread) *rays_per_thread = brpt;
     if (star_stage) *star_stage = bst;
+    if (fma_pairs) *fma_pairs = bfm;
     if (best_ms) *best_ms = best;
     return MLENS_OK;
 }

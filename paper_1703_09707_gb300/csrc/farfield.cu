@@ -1020,6 +1020,7 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
     stats_add_block(nb, no, nn, ts.sred, a.stats);
 }
 
+template <int NRP>
 __global__ void __launch_bounds__(kThreads, 2) k_shoot_learned(LearnedArgs L)
 {
     __shared__ __align__(16) ShootSmem<256> sm;
@@ -1047,7 +1048,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_shoot_learned(LearnedArgs L)
         const int bx = tile % ntx, by = tile / ntx;
         const int rc = (by / L.cg.kty) * L.cg.ncx + bx / L.cg.ktx;
         if (L.flags[rc])
-            shoot_tile<4, 256, false>(L.plain, bx, by, sm, ts);
+            shoot_tile<4, 256, false, NRP>(L.plain, bx, by, sm, ts);
         else
             learned_tile(L, bx, by, sm, ts, ls);
     }
@@ -1055,8 +1056,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_shoot_learned(LearnedArgs L)
 
 cudaError_t ff_learned_grid(int *grid)
 {
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shoot_learned, kThreads, 0);
+    int per_sm = 0, per_sm1 = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shoot_learned<0>, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, k_shoot_learned<1>, kThreads, 0);
+    per_sm = per_sm < per_sm1 ? per_sm : per_sm1;
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -1065,10 +1069,13 @@ cudaError_t ff_learned_grid(int *grid)
     return cudaSuccess;
 }
 
-cudaError_t ff_shoot_learned(const LearnedArgs &L, int grid, cudaStream_t s)
+cudaError_t ff_shoot_learned(const LearnedArgs &L, int grid, int fma_pairs, cudaStream_t s)
 {
     const int64_t g = L.nitems < grid ? (L.nitems > 0 ? L.nitems : 1) : grid;
-    k_shoot_learned<<<(unsigned)g, kThreads, 0, s>>>(L);
+    if (fma_pairs)
+        k_shoot_learned<1><<<(unsigned)g, kThreads, 0, s>>>(L);
+    else
+        k_shoot_learned<0><<<(unsigned)g, kThreads, 0, s>>>(L);
     return cudaGetLastError();
 }
 

@@ -107,7 +107,8 @@ cudaError_t ff_adam(float *p, float *m, float *v, const float *g, int64_t n, flo
                     float bc1, float bc2, cudaStream_t s);
 cudaError_t ff_embed(const float *params, const float *z, int nrc, float *ec, cudaStream_t s);
 cudaError_t ff_flags(const unsigned *maxerr, int nrc, float tol, int *flags, cudaStream_t s);
-cudaError_t ff_shoot_learned(const LearnedArgs &L, int grid, cudaStream_t s);
+// fallback tiles use the plain tile function with the context's fma_pairs setting
+cudaError_t ff_shoot_learned(const LearnedArgs &L, int grid, int fma_pairs, cudaStream_t s);
 cudaError_t ff_learned_grid(int *grid);
 
 }  // namespace mlens

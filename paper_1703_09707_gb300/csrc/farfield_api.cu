@@ -453,7 +453,7 @@ int mlens_shoot_learned(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid
     L.items = items;
     L.nitems = nitems;
     L.counter = f->counter;
-    FCUDA(ff_shoot_learned(L, f->grid, s), "learned shoot launch");
+    FCUDA(ff_shoot_learned(L, f->grid, ctx->fma_pairs, s), "learned shoot launch");
     if (stats_host) {
         unsigned long long h[3];
         FCUDA(cudaMemcpyAsync(h, ctx->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s), "memcpy(stats)");

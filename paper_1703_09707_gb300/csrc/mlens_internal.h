@@ -79,10 +79,12 @@ struct BatchLaunch {
 
 // launchers (defined in the .cu files)
 // pairs_per_thread in {2, 4} (4 or 8 rays per thread); stage in {128, 256, 512} stars
+// fma_pairs in {0, 1}: ray pairs per thread whose reciprocal runs on the FMA pipe
 cudaError_t launch_shoot_fp32(const ShootArgs &a, int pairs_per_thread, bool naive, cudaStream_t s,
-                              int stage = 256);
-cudaError_t launch_shoot_batch(const BatchLaunch &b, int pairs_per_thread, int stage, cudaStream_t s);
-cudaError_t batch_grid_size(int pairs_per_thread, int stage, int *grid);
+                              int stage = 256, int fma_pairs = 0);
+cudaError_t launch_shoot_batch(const BatchLaunch &b, int pairs_per_thread, int stage, cudaStream_t s,
+                               int fma_pairs = 0);
+cudaError_t batch_grid_size(int pairs_per_thread, int stage, int *grid, int fma_pairs = 0);
 int64_t tiles_of(const RayGrid &r, int pairs_per_thread);
 cudaError_t launch_shoot_fp64(const ShootArgs &a, cudaStream_t s);
 cudaError_t launch_trace_fp64(const float4 *stars, int64_t nstars, const LensTerms &lens, const double2 *theta,
@@ -111,5 +113,6 @@ struct mlens_ctx {
     int precision = MLENS_PREC_FP32;
     int pairs_per_thread = 4;
     int star_stage = 256;
+    int fma_pairs = 0;
     FarState *ff = nullptr;
 };

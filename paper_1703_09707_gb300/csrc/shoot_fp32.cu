@@ -31,19 +31,19 @@
 
 namespace mlens {
 
-template <int NP, int SC, bool NAIVE>
+template <int NP, int SC, bool NAIVE, int NRP>
 __global__ void __launch_bounds__(kThreads, 2) k_shoot_fp32(ShootArgs a)
 {
     __shared__ __align__(16) ShootSmem<SC> sm;
     __shared__ TileShared ts;
-    shoot_tile<NP, SC, NAIVE>(a, blockIdx.x, blockIdx.y, sm, ts);
+    shoot_tile<NP, SC, NAIVE, NRP>(a, blockIdx.x, blockIdx.y, sm, ts);
 }
 
 // Persistent kernel over many fields: CTAs pull (field, tile) items from one
 // atomic counter until the queue is empty.  Items are numbered field by field in
 // the order `order` (heaviest field first, so the tail is made of light items);
 // begin[k] is the first item of the k-th field in that order (begin[nf] = total).
-template <int NP, int SC>
+template <int NP, int SC, int NRP>
 __global__ void __launch_bounds__(kThreads, 2)
     k_shoot_batch(const ShootArgs *fields, const int *order, const int64_t *begin, int nf, int64_t total,
                   unsigned long long *counter)
@@ -66,35 +66,38 @@ __global__ void __launch_bounds__(kThreads, 2)
         const ShootArgs &A = fields[order[lo]];
         const int64_t t = item - begin[lo];
         const int tiles_x = (A.rays.nx + kTileX - 1) / kTileX;
-        shoot_tile<NP, SC, false>(A, (int)(t % tiles_x), (int)(t / tiles_x), sm, ts);
+        shoot_tile<NP, SC, false, NRP>(A, (int)(t % tiles_x), (int)(t / tiles_x), sm, ts);
     }
 }
 
-template <int NP, int SC, bool NAIVE>
+template <int NP, int SC, bool NAIVE, int NRP>
 static cudaError_t launch_t(const ShootArgs &a, cudaStream_t s)
 {
     dim3 grid((unsigned)((a.rays.nx + kTileX - 1) / kTileX), (unsigned)((a.rays.ny + tile_rows(NP) - 1) / tile_rows(NP)));
     if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
-    k_shoot_fp32<NP, SC, NAIVE><<<grid, kThreads, 0, s>>>(a);
+    k_shoot_fp32<NP, SC, NAIVE, NRP><<<grid, kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-template <bool NAIVE>
+template <bool NAIVE, int NRP>
 static cudaError_t launch_sel(const ShootArgs &a, int np, int sc, cudaStream_t s)
 {
     if (np == 2) {
-        if (sc == 128) return launch_t<2, 128, NAIVE>(a, s);
-        if (sc == 512) return launch_t<2, 512, NAIVE>(a, s);
-        return launch_t<2, 256, NAIVE>(a, s);
+        if (sc == 128) return launch_t<2, 128, NAIVE, NRP>(a, s);
+        if (sc == 512) return launch_t<2, 512, NAIVE, NRP>(a, s);
+        return launch_t<2, 256, NAIVE, NRP>(a, s);
     }
-    if (sc == 128) return launch_t<4, 128, NAIVE>(a, s);
-    if (sc == 512) return launch_t<4, 512, NAIVE>(a, s);
-    return launch_t<4, 256, NAIVE>(a, s);
+    if (sc == 128) return launch_t<4, 128, NAIVE, NRP>(a, s);
+    if (sc == 512) return launch_t<4, 512, NAIVE, NRP>(a, s);
+    return launch_t<4, 256, NAIVE, NRP>(a, s);
 }
 
-cudaError_t launch_shoot_fp32(const ShootArgs &a, int pairs_per_thread, bool naive, cudaStream_t s, int stage)
+cudaError_t launch_shoot_fp32(const ShootArgs &a, int pairs_per_thread, bool naive, cudaStream_t s, int stage,
+                              int fma_pairs)
 {
-    return naive ? launch_sel<true>(a, pairs_per_thread, stage, s) : launch_sel<false>(a, pairs_per_thread, stage, s);
+    if (naive) return launch_sel<true, 0>(a, pairs_per_thread, stage, s);
+    return fma_pairs ? launch_sel<false, 1>(a, pairs_per_thread, stage, s)
+                     : launch_sel<false, 0>(a, pairs_per_thread, stage, s);
 }
 
 int64_t tiles_of(const RayGrid &r, int pairs_per_thread)
@@ -103,11 +106,11 @@ int64_t tiles_of(const RayGrid &r, int pairs_per_thread)
     return (int64_t)((r.nx + kTileX - 1) / kTileX) * (int64_t)((r.ny + ty - 1) / ty);
 }
 
-template <int NP, int SC>
+template <int NP, int SC, int NRP>
 static cudaError_t grid_b(int *grid)
 {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shoot_batch<NP, SC>, kThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shoot_batch<NP, SC, NRP>, kThreads, 0);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -116,37 +119,49 @@ static cudaError_t grid_b(int *grid)
     return cudaSuccess;
 }
 
-cudaError_t batch_grid_size(int pairs_per_thread, int stage, int *grid)
+template <int NRP>
+static cudaError_t grid_sel(int np, int sc, int *grid)
 {
-    if (pairs_per_thread == 2) {
-        if (stage == 128) return grid_b<2, 128>(grid);
-        if (stage == 512) return grid_b<2, 512>(grid);
-        return grid_b<2, 256>(grid);
+    if (np == 2) {
+        if (sc == 128) return grid_b<2, 128, NRP>(grid);
+        if (sc == 512) return grid_b<2, 512, NRP>(grid);
+        return grid_b<2, 256, NRP>(grid);
     }
-    if (stage == 128) return grid_b<4, 128>(grid);
-    if (stage == 512) return grid_b<4, 512>(grid);
-    return grid_b<4, 256>(grid);
+    if (sc == 128) return grid_b<4, 128, NRP>(grid);
+    if (sc == 512) return grid_b<4, 512, NRP>(grid);
+    return grid_b<4, 256, NRP>(grid);
 }
 
-template <int NP, int SC>
+cudaError_t batch_grid_size(int pairs_per_thread, int stage, int *grid, int fma_pairs)
+{
+    return fma_pairs ? grid_sel<1>(pairs_per_thread, stage, grid) : grid_sel<0>(pairs_per_thread, stage, grid);
+}
+
+template <int NP, int SC, int NRP>
 static cudaError_t launch_b(const BatchLaunch &b, cudaStream_t s)
 {
     const int64_t want = b.grid > 0 ? b.grid : 1;
     const unsigned grid = (unsigned)(b.total < want ? (b.total > 0 ? b.total : 1) : want);
-    k_shoot_batch<NP, SC><<<grid, kThreads, 0, s>>>(b.fields, b.order, b.begin, b.nfields, b.total, b.counter);
+    k_shoot_batch<NP, SC, NRP><<<grid, kThreads, 0, s>>>(b.fields, b.order, b.begin, b.nfields, b.total, b.counter);
     return cudaGetLastError();
 }
 
-cudaError_t launch_shoot_batch(const BatchLaunch &b, int pairs_per_thread, int stage, cudaStream_t s)
+template <int NRP>
+static cudaError_t launch_bsel(const BatchLaunch &b, int np, int sc, cudaStream_t s)
 {
-    if (pairs_per_thread == 2) {
-        if (stage == 128) return launch_b<2, 128>(b, s);
-        if (stage == 512) return launch_b<2, 512>(b, s);
-        return launch_b<2, 256>(b, s);
+    if (np == 2) {
+        if (sc == 128) return launch_b<2, 128, NRP>(b, s);
+        if (sc == 512) return launch_b<2, 512, NRP>(b, s);
+        return launch_b<2, 256, NRP>(b, s);
     }
-    if (stage == 128) return launch_b<4, 128>(b, s);
-    if (stage == 512) return launch_b<4, 512>(b, s);
-    return launch_b<4, 256>(b, s);
+    if (sc == 128) return launch_b<4, 128, NRP>(b, s);
+    if (sc == 512) return launch_b<4, 512, NRP>(b, s);
+    return launch_b<4, 256, NRP>(b, s);
+}
+
+cudaError_t launch_shoot_batch(const BatchLaunch &b, int pairs_per_thread, int stage, cudaStream_t s, int fma_pairs)
+{
+    return fma_pairs ? launch_bsel<1>(b, pairs_per_thread, stage, s) : launch_bsel<0>(b, pairs_per_thread, stage, s);
 }
 
 }  // namespace mlens

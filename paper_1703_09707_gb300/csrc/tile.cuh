@@ -52,9 +52,33 @@ __device__ __forceinline__ void kahan2(float2 &S, float2 &C, float2 v)
 
 constexpr int tile_rows(int np) { return kGroups * 2 * np; }
 
+// Reciprocal on the FMA pipe for a packed pair: an initial guess read off the
+// float bits (seed - bits(x), seed chosen by a minimax search over one binade:
+// relative error <= 5.1%) refined by three Newton-Raphson steps
+// y <- y + y (1 - x y), each squaring the relative error (5.1e-2 -> 2.6e-3 ->
+// 6.5e-6 -> 4e-11, below float32 resolution).  x = 0 gives a non-finite result,
+// as the hardware reciprocal does.  Used for some ray pairs so that the FMA pipe
+// takes part of the reciprocal load off the MUFU unit.
+constexpr int kRcpSeed = 0x7EF311C2;
+
+__device__ __forceinline__ float2 rcp_nr2(float2 x)
+{
+    float2 y = f2(__int_as_float(kRcpSeed - __float_as_int(x.x)), __int_as_float(kRcpSeed - __float_as_int(x.y)));
+    const float2 nx = f2(-x.x, -x.y);
+    const float2 one = f2(1.0f, 1.0f);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float2 e = __ffma2_rn(nx, y, one);
+        y = __ffma2_rn(y, e, y);
+    }
+    return y;
+}
+
 // One tile (bx, by) of the ray grid of `a`, start to finish: prologue, star
 // stages, beta, binning, counters.  Every thread of the CTA must call it.
-template <int NP, int SC, bool NAIVE>
+// NRP of the NP ray pairs take their reciprocals from rcp_nr2 (FMA pipe), the
+// others from the MUFU unit.
+template <int NP, int SC, bool NAIVE, int NRP = 0>
 __device__ __forceinline__ void shoot_tile(const ShootArgs &a, int bx, int by, ShootSmem<SC> &sm, TileShared &ts)
 {
     constexpr int kTileY = tile_rows(NP);
@@ -177,7 +201,7 @@ __device__ __forceinline__ void shoot_tile(const ShootArgs &a, int bx, int by, S
                 for (int p = 0; p < NP; ++p) {
                     const float2 dy = __fadd2_rn(ry[p], nyv);
                     const float2 r2 = __ffma2_rn(dy, dy, dx2);
-                    const float2 inv = f2(rcp_approx(r2.x), rcp_approx(r2.y));
+                    const float2 inv = p < NRP ? rcp_nr2(r2) : f2(rcp_approx(r2.x), rcp_approx(r2.y));
                     const float2 f = __fmul2_rn(m2, inv);
                     px[p] = __ffma2_rn(f, dx, px[p]);
                     py[p] = __ffma2_rn(f, dy, py[p]);

@@ -91,7 +91,7 @@ _dp = C.POINTER(C.c_double)
 SIGNATURES = {
     "mlens_create": (C.c_int, [C.POINTER(_vp), _dp, _dp, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int32]),
     "mlens_set_precision": (C.c_int, [_vp, C.c_int32]),
-    "mlens_set_tuning": (C.c_int, [_vp, C.c_int32, C.c_int32]),
+    "mlens_set_tuning": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32]),
     "mlens_shoot": (C.c_int, [_vp, _gp, _gp, _vp, C.c_uint32, _sp, _vp]),
     "mlens_shoot_beta": (C.c_int, [_vp, _gp, _gp, _vp, _vp, C.c_uint32, _sp, _vp]),
     "mlens_trace": (C.c_int, [_vp, _dp, C.c_int64, _dp, _vp]),
@@ -100,8 +100,9 @@ SIGNATURES = {
                                       _sp, _vp]),
     "mlens_batch_create": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int32, _gp, _gp, C.POINTER(_vp),
                                      C.c_uint32]),
-    "mlens_batch_set_tuning": (C.c_int, [_vp, C.c_int32, C.c_int32]),
-    "mlens_batch_tune": (C.c_int, [_vp, _vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
+    "mlens_batch_set_tuning": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32]),
+    "mlens_batch_tune": (C.c_int, [_vp, _vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_double)]),
     "mlens_batch_run": (C.c_int, [_vp, _sp, _vp]),
     "mlens_batch_destroy": (None, [_vp]),
     "mlens_shoot_batch": (C.c_int, [C.POINTER(_vp), C.c_int32, _gp, _gp, C.POINTER(_vp), C.c_uint32, _sp, _vp]),
@@ -220,8 +221,8 @@ def mlens_set_precision(ctx: Ctx, precision):
     _check(load().mlens_set_precision(ctx.handle, int(precision)))
 
 
-def mlens_set_tuning(ctx: Ctx, rays_per_thread: int, star_stage: int = 0):
-    _check(load().mlens_set_tuning(ctx.handle, int(rays_per_thread), int(star_stage)))
+def mlens_set_tuning(ctx: Ctx, rays_per_thread: int, star_stage: int = 0, fma_pairs: int = 0):
+    _check(load().mlens_set_tuning(ctx.handle, int(rays_per_thread), int(star_stage), int(fma_pairs)))
 
 
 def mlens_shoot(ctx: Ctx, rays, src, counts, flags: int = 0, stats: bool = False, stream=None):
@@ -304,14 +305,15 @@ def mlens_batch_create(ctxs, rays, srcs, counts, flags: int = 0) -> Batch:
     return Batch(h.value, (list(ctxs), list(counts)))
 
 
-def mlens_batch_set_tuning(b: Batch, rays_per_thread: int, star_stage: int = 0):
-    _check(load().mlens_batch_set_tuning(b.handle, int(rays_per_thread), int(star_stage)))
+def mlens_batch_set_tuning(b: Batch, rays_per_thread: int, star_stage: int = 0, fma_pairs: int = 0):
+    _check(load().mlens_batch_set_tuning(b.handle, int(rays_per_thread), int(star_stage), int(fma_pairs)))
 
 
 def mlens_batch_tune(b: Batch, stream=None):
-    r, s, ms = C.c_int32(0), C.c_int32(0), C.c_double(0.0)
-    _check(load().mlens_batch_tune(b.handle, _stream_ptr(stream), C.byref(r), C.byref(s), C.byref(ms)))
-    return int(r.value), int(s.value), float(ms.value)
+    """Returns (rays_per_thread, star_stage, fma_pairs, best_ms)."""
+    r, s, f, ms = C.c_int32(0), C.c_int32(0), C.c_int32(0), C.c_double(0.0)
+    _check(load().mlens_batch_tune(b.handle, _stream_ptr(stream), C.byref(r), C.byref(s), C.byref(f), C.byref(ms)))
+    return int(r.value), int(s.value), int(f.value), float(ms.value)
 
 
 def mlens_batch_run(b: Batch, stats: bool = False, stream=None):

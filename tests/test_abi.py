@@ -65,7 +65,7 @@ def test_bad_arguments_are_rejected_before_any_device_call(lib):
     g = M.mlens_grid(-1.0, 1.0, -1.0, 1.0, 4, 4)
     assert lib.mlens_shoot(None, C.byref(g), C.byref(g), C.c_void_p(16), 0, None, None) == M.MLENS_ERR_ARG
     assert "context" in M.mlens_last_error()
-    assert lib.mlens_set_tuning(None, 8, 0) == M.MLENS_ERR_ARG
+    assert lib.mlens_set_tuning(None, 8, 0, 0) == M.MLENS_ERR_ARG
     assert lib.mlens_set_precision(None, 0) == M.MLENS_ERR_ARG
     badg = M.mlens_grid(1.0, -1.0, -1.0, 1.0, 4, 4)
     assert lib.mlens_bin(C.c_void_p(16), 4, C.byref(badg), C.c_void_p(16), 0, None, None) == M.MLENS_ERR_ARG
@@ -85,7 +85,7 @@ def test_batch_arguments_rejected_without_a_device(lib):
     assert "field 0" in M.mlens_last_error()
     assert lib.mlens_batch_create(C.byref(h), ctxs, 0, g, g, cnt, 0) == M.MLENS_ERR_ARG
     assert lib.mlens_batch_run(None, None, None) == M.MLENS_ERR_ARG
-    assert lib.mlens_batch_set_tuning(None, 8, 0) == M.MLENS_ERR_ARG
+    assert lib.mlens_batch_set_tuning(None, 8, 0, 0) == M.MLENS_ERR_ARG
     lib.mlens_batch_destroy(None)
 
 

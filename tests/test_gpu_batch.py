@@ -29,15 +29,15 @@ def host(c, s):
     return c.cpu().numpy().view(np.uint32).reshape(s.ny, s.nx)
 
 
-@pytest.mark.parametrize("rpt,stage", [(8, 256), (4, 128), (8, 512)])
-def test_batch_equals_single_field_shots(small_batch, rpt, stage):
+@pytest.mark.parametrize("rpt,stage,fma", [(8, 256, 0), (4, 128, 0), (8, 512, 1), (4, 256, 1)])
+def test_batch_equals_single_field_shots(small_batch, rpt, stage, fma):
     wl, ctxs, counts = small_batch
     b = M.mlens_batch_create(ctxs, wl.rays, wl.srcs, counts)
-    M.mlens_batch_set_tuning(b, rpt, stage)
+    M.mlens_batch_set_tuning(b, rpt, stage, fma)
     st = M.mlens_batch_run(b, stats=True)
     torch.cuda.synchronize()
     for f, ctx in enumerate(ctxs):
-        M.mlens_set_tuning(ctx, rpt, stage)
+        M.mlens_set_tuning(ctx, rpt, stage, fma)
         ref = torch.empty_like(counts[f])
         st1 = M.mlens_shoot(ctx, wl.rays[f], wl.srcs[f], ref, stats=True)
         assert torch.equal(ref, counts[f]), f"field {f}"
@@ -82,14 +82,14 @@ def test_batch_accumulate_and_one_shot(small_batch):
 def test_autotuner_picks_a_valid_shape_and_caches_it(small_batch, tmp_path, monkeypatch):
     wl, ctxs, counts = small_batch
     b = M.mlens_batch_create(ctxs, wl.rays, wl.srcs, counts)
-    rpt, stage, ms = M.mlens_batch_tune(b)
-    assert rpt in (4, 8) and stage in (128, 256, 512)
+    rpt, stage, fma, ms = M.mlens_batch_tune(b)
+    assert rpt in (4, 8) and stage in (128, 256, 512) and fma in (0, 1)
     assert ms > 0 or ms == -1.0
-    rpt2, stage2, ms2 = M.mlens_batch_tune(b)  # same signature: served from the cache
-    assert (rpt2, stage2) == (rpt, stage) and ms2 == -1.0
+    rpt2, stage2, fma2, ms2 = M.mlens_batch_tune(b)  # same signature: served from the cache
+    assert (rpt2, stage2, fma2) == (rpt, stage, fma) and ms2 == -1.0
     st = M.mlens_batch_run(b, stats=True)
     for f, ctx in enumerate(ctxs):
-        M.mlens_set_tuning(ctx, rpt, stage)
+        M.mlens_set_tuning(ctx, rpt, stage, fma)
         ref = torch.empty_like(counts[f])
         assert M.mlens_shoot(ctx, wl.rays[f], wl.srcs[f], ref, stats=True) == st[f]
         assert torch.equal(ref, counts[f])

@@ -208,15 +208,17 @@ def test_standalone_bin_matches_fused_map():
     ctx.close()
 
 
-def test_launch_shapes_both_meet_the_bar():
-    """rays_per_thread 4 and 8 use different tiles (different centres), so beta may
-    differ in its last bits; both must meet the bar and nearly agree."""
+@pytest.mark.parametrize("fma", [0, 1])
+def test_launch_shapes_both_meet_the_bar(fma):
+    """rays_per_thread 4 and 8 use different tiles (different centres), and fma = 1
+    takes some reciprocals from Newton-Raphson on the FMA pipe, so beta may differ in
+    its last bits; every shape must meet the bar and they must nearly agree."""
     wl = W.config("paper", rays_scale=1 / 8)
     f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
     maps = []
     for rpt in (4, 8):
         ctx = make_ctx(f)
-        M.mlens_set_tuning(ctx, rpt)
+        M.mlens_set_tuning(ctx, rpt, 0, fma)
         c, st, b4 = shoot_gpu(f, rays, src, ctx=ctx)
         ctx.close()
         assert_rebin_exact(c, st, b4, src)
