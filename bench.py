@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--workload", default="paper", choices=["paper", "tiny", "precision"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_naive", "fp64"])
     ap.add_argument("--rays-per-thread", type=int, default=8, choices=[4, 8])
+    ap.add_argument("--star-stage", type=int, default=256, choices=[128, 256, 512])
     ap.add_argument("--fma-pairs", type=int, default=0, choices=[0, 1],
                     help="ray pairs per thread whose reciprocal runs on the FMA pipe (Newton-Raphson)")
     ap.add_argument("--rays-scale", type=float, default=1.0,
@@ -408,7 +409,7 @@ def run_mine(args):
     n_inter = rays.n * f.n
 
     ctx = M.mlens_create(f.xy, f.m, f.kappa_c, f.gamma1, f.gamma2, prec)
-    M.mlens_set_tuning(ctx, args.rays_per_thread, 0, args.fma_pairs)
+    M.mlens_set_tuning(ctx, args.rays_per_thread, args.star_stage, args.fma_pairs)
     counts = torch.empty(src.n, dtype=torch.int32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -454,7 +455,7 @@ def run_mine(args):
     e0.record(stream)
     for _ in range(e2e_steps):
         c2 = M.mlens_create(f.xy, f.m, f.kappa_c, f.gamma1, f.gamma2, prec)
-        M.mlens_set_tuning(c2, args.rays_per_thread, 0, args.fma_pairs)
+        M.mlens_set_tuning(c2, args.rays_per_thread, args.star_stage, args.fma_pairs)
         M.mlens_shoot(c2, rays, src, counts)
         host_counts.copy_(counts, non_blocking=True)
         torch.cuda.current_stream().synchronize()
@@ -506,6 +507,7 @@ def run_mine(args):
     }
     line["config"]["rays_per_thread"] = args.rays_per_thread
     line["config"]["fma_pairs"] = args.fma_pairs
+    line["config"]["star_stage"] = args.star_stage
     extras = set(x for x in args.extras.split(",") if x)
     if not args.no_extras and world == 1 and args.workload == "paper" and args.rays_scale == 1.0:
         if "batched" in extras:

@@ -108,6 +108,11 @@ cudaError_t ff_build_csr(const float4 *stars, int64_t n, const CellGrid &cg, int
 
 // ===================================================== FP64 coefficients
 // One warp per ray cell, eight cells per CTA sharing each staged chunk of stars.
+// b_0 (the far field's value at the centre, ~30 theta_E, needed to ~1e-9) is
+// formed entirely in FP64.  For p >= 1 the terms -(m/s) w^(p+1) are formed in
+// FP32 from the FP64 w (relative error ~p 6e-8 per term, far below what the
+// series needs) and accumulated in FP64, so the sums keep FP64 accuracy while
+// the per-term work moves to the FP32 pipe.
 __global__ void __launch_bounds__(256) k_coeffs(const float4 *stars, const int *scell, int64_t n, CellGrid g, int pt,
                                                 double scale, double *out)
 {
@@ -122,6 +127,7 @@ __global__ void __launch_bounds__(256) k_coeffs(const float4 *stars, const int *
     double ar[kPtMax + 1], ai[kPtMax + 1];
 #pragma unroll
     for (int p = 0; p <= kPtMax; ++p) ar[p] = ai[p] = 0.0;
+    const float fscale = (float)scale;
     for (int64_t s0 = 0; s0 < n; s0 += 256) {
         const int cnt = (int)min((int64_t)256, n - s0);
         __syncthreads();
@@ -141,16 +147,20 @@ __global__ void __launch_bounds__(256) k_coeffs(const float4 *stars, const int *
             const double dx = (double)q.x - zx, dy = (double)q.y - zy;
             const double inv = scale / (dx * dx + dy * dy);
             const double wr = dx * inv, wi = -dy * inv;  // s / (z_k - z_c)
-            double tr = -(double)q.z * wr / scale, ti = -(double)q.z * wi / scale;
+            const double tr = -(double)q.z * wr / scale, ti = -(double)q.z * wi / scale;
+            ar[0] += tr;
+            ai[0] += ti;
+            const float fwr = (float)wr, fwi = (float)wi;
+            float fr = (float)tr, fi = (float)ti;
 #pragma unroll
-            for (int p = 0; p <= kPtMax; ++p) {
+            for (int p = 1; p <= kPtMax; ++p) {
+                const float nr = fr * fwr - fi * fwi, ni = fr * fwi + fi * fwr;
+                fr = nr;
+                fi = ni;
                 if (p <= pt) {
-                    ar[p] += tr;
-                    ai[p] += ti;
+                    ar[p] += (double)fr;
+                    ai[p] += (double)fi;
                 }
-                const double nr = tr * wr - ti * wi, ni = tr * wi + ti * wr;
-                tr = nr;
-                ti = ni;
             }
         }
     }
