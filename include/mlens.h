@@ -372,6 +372,17 @@ int mlens_ff_eval(const float *params_dev, const float *z_dev, const float *u_de
 /* Free a context's device memory (waits for its device).  NULL is ignored. */
 void mlens_destroy(mlens_ctx *ctx);
 
+/*
+ * mlens_set_device_memory_limit -- a budget (bytes; 0 = none, the default) for the
+ * device memory the library itself allocates (star copies, counters, batch and
+ * far-field tables; never the caller's maps).  An allocation that would exceed it
+ * fails with MLENS_ERR_NOMEM as if the device were full, leaving every existing
+ * context usable.  The environment variable MLENS_DEVICE_MEMORY_LIMIT sets the
+ * initial budget.  mlens_device_memory_in_use reports the bytes currently held.
+ */
+int mlens_set_device_memory_limit(uint64_t bytes);
+uint64_t mlens_device_memory_in_use(void);
+
 /* Message describing the calling thread's most recent failure ("" if none). */
 const char *mlens_last_error(void);
 

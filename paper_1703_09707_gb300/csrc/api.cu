@@ -8,8 +8,11 @@
 #include <stdio.h>
 
 #include <cmath>
+#include <atomic>
+#include <cstdlib>
 #include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "mlens_internal.h"
@@ -81,7 +84,7 @@ int device_scratch(unsigned long long **out)
     MLENS_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     std::lock_guard<std::mutex> lk(g_scratch_mu);
     if ((int)g_scratch.size() <= dev) g_scratch.resize(dev + 1, nullptr);
-    if (!g_scratch[dev]) MLENS_CUDA(cudaMalloc(&g_scratch[dev], 4 * sizeof(unsigned long long)), "cudaMalloc(scratch)");
+    if (!g_scratch[dev]) MLENS_CUDA(dmalloc(&g_scratch[dev], 4 * sizeof(unsigned long long)), "cudaMalloc(scratch)");
     *out = g_scratch[dev];
     return MLENS_OK;
 }
@@ -152,6 +155,63 @@ namespace mlens {
 
 void set_last_error(const std::string &msg) { g_err = msg; }
 
+namespace {
+std::mutex g_mem_mu;
+std::unordered_map<const void *, size_t> g_mem_sizes;
+uint64_t g_mem_in_use = 0;
+uint64_t g_mem_limit = 0;  // 0 = no budget
+std::once_flag g_mem_env_once;
+
+// The budget may also come from the environment (MLENS_DEVICE_MEMORY_LIMIT, bytes).
+void read_env_limit()
+{
+    std::call_once(g_mem_env_once, [] {
+        const char *v = getenv("MLENS_DEVICE_MEMORY_LIMIT");
+        if (v) g_mem_limit = strtoull(v, nullptr, 10);
+    });
+}
+}  // namespace
+
+uint64_t mem_in_use()
+{
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    return g_mem_in_use;
+}
+
+void set_mem_limit(uint64_t bytes)
+{
+    read_env_limit();
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    g_mem_limit = bytes;
+}
+
+cudaError_t dmalloc_raw(void **p, size_t bytes)
+{
+    read_env_limit();
+    *p = nullptr;
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    if (g_mem_limit && g_mem_in_use + bytes > g_mem_limit) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return e;
+    g_mem_sizes[*p] = bytes;
+    g_mem_in_use += bytes;
+    return cudaSuccess;
+}
+
+void dfree(const void *p)
+{
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lk(g_mem_mu);
+        auto it = g_mem_sizes.find(p);
+        if (it != g_mem_sizes.end()) {
+            g_mem_in_use -= it->second;
+            g_mem_sizes.erase(it);
+        }
+    }
+    cudaFree(const_cast<void *>(p));
+}
+
 BinGrid make_bin_grid(const mlens_grid &g)
 {
     BinGrid b;
@@ -208,6 +268,14 @@ extern "C" {
 
 const char *mlens_last_error(void) { return g_err.c_str(); }
 
+int mlens_set_device_memory_limit(uint64_t bytes)
+{
+    mlens::set_mem_limit(bytes);
+    return MLENS_OK;
+}
+
+uint64_t mlens_device_memory_in_use(void) { return mlens::mem_in_use(); }
+
 int mlens_version(void) { return 10000; }
 
 int mlens_create(mlens_ctx **out, const double *xy, const double *m, int64_t n, double kappa_c, double gamma1,
@@ -245,8 +313,8 @@ int mlens_create(mlens_ctx **out, const double *xy, const double *m, int64_t n, 
     c->lens = make_lens_terms(kappa_c, gamma1, gamma2);
     c->precision = precision;
     cudaError_t e = cudaSuccess;
-    if (n_pad > 0) e = cudaMalloc(&c->d_stars, (size_t)n_pad * sizeof(float4));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_stats, 4 * sizeof(unsigned long long));
+    if (n_pad > 0) e = dmalloc(&c->d_stars, (size_t)n_pad * sizeof(float4));
+    if (e == cudaSuccess) e = dmalloc(&c->d_stats, 4 * sizeof(unsigned long long));
     if (e == cudaSuccess && n_pad > 0)
         e = cudaMemcpy(c->d_stars, h.data(), (size_t)n_pad * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->d_stats, 0, 4 * sizeof(unsigned long long));
@@ -303,12 +371,12 @@ int mlens_trace(mlens_ctx *ctx, const double *theta, int64_t k, double *beta, vo
     if ((rc = check_current_device(ctx->device))) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     double2 *d = nullptr;
-    MLENS_CUDA(cudaMalloc(&d, (size_t)k * 2 * sizeof(double2)), "cudaMalloc(trace)");
+    MLENS_CUDA(dmalloc(&d, (size_t)k * 2 * sizeof(double2)), "cudaMalloc(trace)");
     cudaError_t e = cudaMemcpyAsync(d, theta, (size_t)k * sizeof(double2), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = launch_trace_fp64(ctx->d_stars, ctx->n_pad, ctx->lens, d, d + k, k, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(beta, d + k, (size_t)k * sizeof(double2), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(d);
+    dfree(d);
     if (e != cudaSuccess) return cuda_fail(e, "mlens_trace");
     return MLENS_OK;
 }
@@ -351,8 +419,8 @@ void mlens_destroy(mlens_ctx *ctx)
     if (ctx->device >= 0 && prev != ctx->device) cudaSetDevice(ctx->device);
     if (ctx->d_stars || ctx->d_stats) cudaDeviceSynchronize();
     mlens_free_far_field(ctx);
-    if (ctx->d_stars) cudaFree(ctx->d_stars);
-    if (ctx->d_stats) cudaFree(ctx->d_stats);
+    if (ctx->d_stars) dfree(ctx->d_stars);
+    if (ctx->d_stats) dfree(ctx->d_stats);
     if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
     delete ctx;
 }

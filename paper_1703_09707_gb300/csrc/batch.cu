@@ -236,11 +236,11 @@ int mlens_batch_create(mlens_batch **out, mlens_ctx *const *ctxs, int32_t nfield
     b->counts.assign(counts_dev, counts_dev + nfields);
     b->h_fields.resize(nfields);
     b->n_pad.resize(nfields);
-    cudaError_t e = cudaMalloc(&b->d_fields, sizeof(ShootArgs) * nfields);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_order, sizeof(int) * nfields);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_begin, sizeof(int64_t) * (nfields + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_stats, sizeof(unsigned long long) * 3 * nfields);
+    cudaError_t e = dmalloc(&b->d_fields, sizeof(ShootArgs) * nfields);
+    if (e == cudaSuccess) e = dmalloc(&b->d_order, sizeof(int) * nfields);
+    if (e == cudaSuccess) e = dmalloc(&b->d_begin, sizeof(int64_t) * (nfields + 1));
+    if (e == cudaSuccess) e = dmalloc(&b->d_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = dmalloc(&b->d_stats, sizeof(unsigned long long) * 3 * nfields);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         int rc = bcuda(e, "mlens_batch_create device setup");
@@ -385,11 +385,11 @@ void mlens_batch_destroy(mlens_batch *b)
     if (b->d_fields || b->cap) cudaDeviceSynchronize();
     drop_graph(b);
     if (b->cap) cudaStreamDestroy(b->cap);
-    cudaFree(b->d_fields);
-    cudaFree(b->d_order);
-    cudaFree(b->d_begin);
-    cudaFree(b->d_counter);
-    cudaFree(b->d_stats);
+    dfree(b->d_fields);
+    dfree(b->d_order);
+    dfree(b->d_begin);
+    dfree(b->d_counter);
+    dfree(b->d_stats);
     delete b;
 }
 

@@ -68,7 +68,7 @@ int fcuda(cudaError_t e, const char *what)
 template <class T>
 void ffree(T *&p)
 {
-    if (p) cudaFree((void *)p);
+    if (p) dfree((void *)p);
     p = nullptr;
 }
 
@@ -122,31 +122,31 @@ int alloc_state(FarState *f, int64_t nstars)
 {
     const int nrc = f->nrc, nc = f->next;
     const int64_t np = mlp::kParams + (int64_t)nrc * mlp::kLat;
-    FCUDA(cudaMalloc(&f->scell, sizeof(int) * std::max<int64_t>(nstars, 1)), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->perm, sizeof(int) * std::max<int64_t>(nstars, 1)), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->cstars, sizeof(float4) * std::max<int64_t>(nstars, 1)), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->count, sizeof(int) * nc), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->fill, sizeof(int) * nc), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->start, sizeof(int) * (nc + 1)), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->coef64, sizeof(double) * 2 * (size_t)nrc * (kPtMax + 1)), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->coef, sizeof(float) * (size_t)nrc * kCoefStride), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->tail, sizeof(float) * 2 * (size_t)nrc * kPtMax), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->sc, sizeof(float) * nrc), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->params, sizeof(float) * np), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->m, sizeof(float) * np), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->v, sizeof(float) * np), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->grads, sizeof(float) * np), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->loss, sizeof(float) * 2), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->w1zb, sizeof(__nv_bfloat16) * mlp::kHid * mlp::kLat), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->w1ztb, sizeof(__nv_bfloat16) * mlp::kHid * mlp::kLat), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->w2b, sizeof(__nv_bfloat16) * mlp::kHid * mlp::kHid), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->w2tb, sizeof(__nv_bfloat16) * mlp::kHid * mlp::kHid), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->ec, sizeof(float) * (size_t)nrc * mlp::kHid), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->flags, sizeof(int) * nrc), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->vmax_net, sizeof(unsigned) * nrc), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->vmax_series, sizeof(unsigned) * nrc), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->vsum, sizeof(double) * 2), "cudaMalloc");
-    FCUDA(cudaMalloc(&f->counter, sizeof(unsigned long long)), "cudaMalloc");
+    FCUDA(dmalloc(&f->scell, sizeof(int) * std::max<int64_t>(nstars, 1)), "cudaMalloc");
+    FCUDA(dmalloc(&f->perm, sizeof(int) * std::max<int64_t>(nstars, 1)), "cudaMalloc");
+    FCUDA(dmalloc(&f->cstars, sizeof(float4) * std::max<int64_t>(nstars, 1)), "cudaMalloc");
+    FCUDA(dmalloc(&f->count, sizeof(int) * nc), "cudaMalloc");
+    FCUDA(dmalloc(&f->fill, sizeof(int) * nc), "cudaMalloc");
+    FCUDA(dmalloc(&f->start, sizeof(int) * (nc + 1)), "cudaMalloc");
+    FCUDA(dmalloc(&f->coef64, sizeof(double) * 2 * (size_t)nrc * (kPtMax + 1)), "cudaMalloc");
+    FCUDA(dmalloc(&f->coef, sizeof(float) * (size_t)nrc * kCoefStride), "cudaMalloc");
+    FCUDA(dmalloc(&f->tail, sizeof(float) * 2 * (size_t)nrc * kPtMax), "cudaMalloc");
+    FCUDA(dmalloc(&f->sc, sizeof(float) * nrc), "cudaMalloc");
+    FCUDA(dmalloc(&f->params, sizeof(float) * np), "cudaMalloc");
+    FCUDA(dmalloc(&f->m, sizeof(float) * np), "cudaMalloc");
+    FCUDA(dmalloc(&f->v, sizeof(float) * np), "cudaMalloc");
+    FCUDA(dmalloc(&f->grads, sizeof(float) * np), "cudaMalloc");
+    FCUDA(dmalloc(&f->loss, sizeof(float) * 2), "cudaMalloc");
+    FCUDA(dmalloc(&f->w1zb, sizeof(__nv_bfloat16) * mlp::kHid * mlp::kLat), "cudaMalloc");
+    FCUDA(dmalloc(&f->w1ztb, sizeof(__nv_bfloat16) * mlp::kHid * mlp::kLat), "cudaMalloc");
+    FCUDA(dmalloc(&f->w2b, sizeof(__nv_bfloat16) * mlp::kHid * mlp::kHid), "cudaMalloc");
+    FCUDA(dmalloc(&f->w2tb, sizeof(__nv_bfloat16) * mlp::kHid * mlp::kHid), "cudaMalloc");
+    FCUDA(dmalloc(&f->ec, sizeof(float) * (size_t)nrc * mlp::kHid), "cudaMalloc");
+    FCUDA(dmalloc(&f->flags, sizeof(int) * nrc), "cudaMalloc");
+    FCUDA(dmalloc(&f->vmax_net, sizeof(unsigned) * nrc), "cudaMalloc");
+    FCUDA(dmalloc(&f->vmax_series, sizeof(unsigned) * nrc), "cudaMalloc");
+    FCUDA(dmalloc(&f->vsum, sizeof(double) * 2), "cudaMalloc");
+    FCUDA(dmalloc(&f->counter, sizeof(unsigned long long)), "cudaMalloc");
     return MLENS_OK;
 }
 
@@ -222,7 +222,7 @@ int schedule(FarState *f, cudaStream_t s)
     heavy.insert(heavy.end(), light.begin(), light.end());
     f->nitems = (int64_t)heavy.size();
     ffree(f->items);
-    FCUDA(cudaMalloc(&f->items, sizeof(int) * std::max<int64_t>(f->nitems, 1)), "cudaMalloc(items)");
+    FCUDA(dmalloc(&f->items, sizeof(int) * std::max<int64_t>(f->nitems, 1)), "cudaMalloc(items)");
     FCUDA(cudaMemcpy(f->items, heavy.data(), sizeof(int) * f->nitems, cudaMemcpyHostToDevice), "memcpy(items)");
     f->h_items = heavy;
     ffree(f->sub_items);
@@ -418,7 +418,7 @@ int mlens_shoot_learned(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid
             const int by = t / ntx;
             if (by * 32 >= row_begin && by * 32 < row_end) sub.push_back(t);
         }
-        if (!f->sub_items) FCUDA(cudaMalloc(&f->sub_items, sizeof(int) * std::max<int64_t>(f->nitems, 1)), "cudaMalloc");
+        if (!f->sub_items) FCUDA(dmalloc(&f->sub_items, sizeof(int) * std::max<int64_t>(f->nitems, 1)), "cudaMalloc");
         FCUDA(cudaMemcpyAsync(f->sub_items, sub.data(), sizeof(int) * sub.size(), cudaMemcpyHostToDevice, s),
               "memcpy(sub items)");
         FCUDA(cudaStreamSynchronize(s), "sync");
@@ -618,8 +618,8 @@ int mlens_ff_eval(const float *params_dev, const float *z_dev, const float *u_de
     cudaStream_t s = (cudaStream_t)stream;
     __nv_bfloat16 *w = nullptr;
     float *dl = nullptr;
-    FCUDA(cudaMalloc(&w, sizeof(__nv_bfloat16) * (2 * mlp::kHid * mlp::kLat + 2 * mlp::kHid * mlp::kHid)), "cudaMalloc");
-    cudaError_t e = cudaMalloc(&dl, sizeof(float));
+    FCUDA(dmalloc(&w, sizeof(__nv_bfloat16) * (2 * mlp::kHid * mlp::kLat + 2 * mlp::kHid * mlp::kHid)), "cudaMalloc");
+    cudaError_t e = dmalloc(&dl, sizeof(float));
     __nv_bfloat16 *w1zb = w, *w1ztb = w + mlp::kHid * mlp::kLat, *w2b = w1ztb + mlp::kHid * mlp::kLat,
                   *w2tb = w2b + mlp::kHid * mlp::kHid;
     if (e == cudaSuccess) e = cudaMemsetAsync(dl, 0, sizeof(float), s);
@@ -648,8 +648,8 @@ int mlens_ff_eval(const float *params_dev, const float *z_dev, const float *u_de
     float h = 0.0f;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, dl, sizeof(float), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(w);
-    cudaFree(dl);
+    dfree(w);
+    dfree(dl);
     if (e != cudaSuccess) return fcuda(e, "mlens_ff_eval");
     if (loss_host) *loss_host = h;
     return MLENS_OK;

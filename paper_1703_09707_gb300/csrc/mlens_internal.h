@@ -93,6 +93,16 @@ cudaError_t launch_bin(const BinArgs &a, cudaStream_t s);
 
 // helpers (api.cu)
 void set_last_error(const std::string &msg);
+// Every device allocation of the library goes through these: they keep count of
+// the bytes in use and refuse (cudaErrorMemoryAllocation) an allocation that would
+// exceed the budget set with mlens_set_device_memory_limit.
+cudaError_t dmalloc_raw(void **p, size_t bytes);
+void dfree(const void *p);
+template <class T>
+inline cudaError_t dmalloc(T **p, size_t bytes)
+{
+    return dmalloc_raw(reinterpret_cast<void **>(p), bytes);
+}
 BinGrid make_bin_grid(const mlens_grid &g);
 RayGrid make_ray_grid(const mlens_grid &g);
 LensTerms make_lens_terms(double kc, double g1, double g2);

@@ -32,11 +32,11 @@
 namespace mlens {
 
 template <int NP, int SC, bool NAIVE, int NRP>
-__global__ void __launch_bounds__(kThreads, 2) k_shoot_fp32(ShootArgs a)
+__global__ void __launch_bounds__(kThreads, 2) k_shoot_fp32(ShootArgs a, int by0)
 {
     __shared__ __align__(16) ShootSmem<SC> sm;
     __shared__ TileShared ts;
-    shoot_tile<NP, SC, NAIVE, NRP>(a, blockIdx.x, blockIdx.y, sm, ts);
+    shoot_tile<NP, SC, NAIVE, NRP>(a, blockIdx.x, by0 + (int)blockIdx.y, sm, ts);
 }
 
 // Persistent kernel over many fields: CTAs pull (field, tile) items from one
@@ -73,10 +73,15 @@ __global__ void __launch_bounds__(kThreads, 2)
 template <int NP, int SC, bool NAIVE, int NRP>
 static cudaError_t launch_t(const ShootArgs &a, cudaStream_t s)
 {
-    dim3 grid((unsigned)((a.rays.nx + kTileX - 1) / kTileX), (unsigned)((a.rays.ny + tile_rows(NP) - 1) / tile_rows(NP)));
-    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
-    k_shoot_fp32<NP, SC, NAIVE, NRP><<<grid, kThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    // tile rows in launches of at most 65535 (the grid's y limit)
+    const int tx = (a.rays.nx + kTileX - 1) / kTileX, ty = (a.rays.ny + tile_rows(NP) - 1) / tile_rows(NP);
+    for (int by0 = 0; by0 < ty; by0 += 65535) {
+        const dim3 grid((unsigned)tx, (unsigned)min(65535, ty - by0));
+        k_shoot_fp32<NP, SC, NAIVE, NRP><<<grid, kThreads, 0, s>>>(a, by0);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <bool NAIVE, int NRP>

@@ -44,7 +44,7 @@ __device__ __forceinline__ int pixel_fp64(double bx, double by, const BinGrid &g
 // GRID: rays of a grid (one per thread, 32 x 4 threads per CTA), binned;
 // otherwise: k arbitrary positions from `theta`, beta written, nothing binned.
 template <bool GRID>
-__global__ void __launch_bounds__(kT64) k_fp64(ShootArgs a, const double2 *theta, double2 *beta, int64_t k)
+__global__ void __launch_bounds__(kT64) k_fp64(ShootArgs a, const double2 *theta, double2 *beta, int64_t k, int by0)
 {
     __shared__ float4 sq[kT64];
     __shared__ unsigned sred[3];
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kT64) k_fp64(ShootArgs a, const double2 *theta
     double tx, ty;
     if (GRID) {
         i = blockIdx.x * 32 + (tid & 31);
-        j = blockIdx.y * 4 + (tid >> 5);
+        j = (by0 + (int)blockIdx.y) * 4 + (tid >> 5);
         ok = i < a.rays.nx && j < a.rays.ny;
         tx = ray_coord(a.rays.x0, a.rays.x1, a.rays.nx, i);
         ty = ray_coord(a.rays.y0, a.rays.y1, a.rays.ny, j);
@@ -102,10 +102,14 @@ __global__ void __launch_bounds__(kT64) k_fp64(ShootArgs a, const double2 *theta
 
 cudaError_t launch_shoot_fp64(const ShootArgs &a, cudaStream_t s)
 {
-    dim3 grid((unsigned)((a.rays.nx + 31) / 32), (unsigned)((a.rays.ny + 3) / 4));
-    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
-    k_fp64<true><<<grid, kT64, 0, s>>>(a, nullptr, nullptr, 0);
-    return cudaGetLastError();
+    const int tx = (a.rays.nx + 31) / 32, ty = (a.rays.ny + 3) / 4;
+    for (int by0 = 0; by0 < ty; by0 += 65535) {
+        const dim3 grid((unsigned)tx, (unsigned)min(65535, ty - by0));
+        k_fp64<true><<<grid, kT64, 0, s>>>(a, nullptr, nullptr, 0, by0);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_trace_fp64(const float4 *stars, int64_t nstars, const LensTerms &lens, const double2 *theta,
@@ -118,7 +122,7 @@ cudaError_t launch_trace_fp64(const float4 *stars, int64_t nstars, const LensTer
     a.lens = lens;
     int64_t nb = (k + kT64 - 1) / kT64;
     if (nb > 0x7fffffff) return cudaErrorInvalidConfiguration;
-    k_fp64<false><<<(unsigned)nb, kT64, 0, s>>>(a, theta, beta, k);
+    k_fp64<false><<<(unsigned)nb, kT64, 0, s>>>(a, theta, beta, k, 0);
     return cudaGetLastError();
 }
 

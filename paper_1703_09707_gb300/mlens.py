@@ -116,6 +116,8 @@ SIGNATURES = {
     "mlens_ff_eval": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, _vp, _vp, _vp, C.POINTER(C.c_float), _vp]),
     "mlens_destroy": (None, [_vp]),
     "mlens_last_error": (C.c_char_p, []),
+    "mlens_set_device_memory_limit": (C.c_int, [C.c_uint64]),
+    "mlens_device_memory_in_use": (C.c_uint64, []),
     "mlens_version": (C.c_int, []),
 }
 
@@ -147,6 +149,14 @@ def _check(rc: int):
 
 def mlens_last_error() -> str:
     return load().mlens_last_error().decode()
+
+
+def mlens_set_device_memory_limit(nbytes: int):
+    _check(load().mlens_set_device_memory_limit(int(nbytes)))
+
+
+def mlens_device_memory_in_use() -> int:
+    return int(load().mlens_device_memory_in_use())
 
 
 def mlens_version() -> int:
