@@ -66,7 +66,8 @@ def parse():
     ap.add_argument("--print-kernel-hash", action="store_true", help="print the FP32 kernel source hash and exit")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-fields and learned-far-field measurements that ride along the main line")
-    ap.add_argument("--extras", default="batched,learned", help="comma list of extra sections: batched, learned")
+    ap.add_argument("--extras", default="batched,binning,learned",
+                    help="comma list of extra sections: batched, binning, learned")
     ap.add_argument("--learned-tol", type=float, default=5e-6, help="per-cell validation bound of the learned field")
     ap.add_argument("--learned-order", type=int, default=8)
     return ap.parse_args()
@@ -261,6 +262,66 @@ def bench_batched(M, torch, steps: int, warmup: int, flush):
         "tuned": {"rays_per_thread": rpt, "star_stage": stage, "fma_pairs": fma, "tune_s": tune_s},
         "gpu_launches_per_batch": 1,
     }
+
+
+# --------------------------------------------------------------- binning
+def measured_hbm_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def bench_binning(M, torch, steps: int, warmup: int, flush):
+    """The binning step alone on the paper-shaped workload: the 8192^2 float-pair beta
+    records of one map (1.07 GB, above L2) binned into the 1024^2 map by the standalone
+    kernel in grid order (64 x 32 ray blocks per CTA) and in flat order (2048
+    consecutive records per CTA), and the fused epilogue's cost: the same grid shot
+    through a star-free field (ray generation, the smooth term, beta and binning)."""
+    wl = W.config("paper")
+    f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
+    stream = torch.cuda.current_stream()
+    ctx = M.mlens_create(f.xy, f.m, f.kappa_c, f.gamma1, f.gamma2, M.MLENS_PREC_FP32)
+    counts = torch.empty(src.n, dtype=torch.int32, device="cuda")
+    beta = torch.empty(rays.n * 4, dtype=torch.float32, device="cuda")
+    st = M.mlens_shoot_beta(ctx, rays, src, counts, beta, stats=True)
+    ref = counts.clone()
+    ctx.close()
+
+    def timed(fn):
+        for _ in range(warmup):
+            flush.fill_(0.0)
+            fn()
+        ms = []
+        for i in range(steps):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.mean(ms)
+
+    peak, basis = measured_hbm_gbs()
+    algo_bytes = 16 * rays.n + 4 * src.n  # records read once, map written once
+    out = {"workload": f"paper: {rays.nx}x{rays.ny} beta records (float pairs, {16 * rays.n / 1e9:.2f} GB), "
+                       f"{src.nx}x{src.ny} map", "rays_binned": st["rays_binned"],
+           "algorithmic_bytes": algo_bytes, "hbm_peak_gbs": peak, "hbm_peak_basis": basis}
+    for name, fn in (("grid_order", lambda: M.mlens_bin_grid(beta, rays, src, counts)),
+                     ("flat_order", lambda: M.mlens_bin(beta, rays.n, src, counts))):
+        ms = timed(fn)
+        assert torch.equal(counts, ref), name
+        gbs = algo_bytes / (ms / 1e3) / 1e9
+        out[name] = {"ms": ms, "records_per_s": rays.n / (ms / 1e3), "gbs": gbs, "hbm_frac": gbs / peak}
+    del beta
+    empty = M.mlens_create(np.zeros((0, 2)), np.zeros(0), f.kappa_c, f.gamma1, f.gamma2, M.MLENS_PREC_FP32)
+    ms = timed(lambda: M.mlens_shoot(empty, rays, src, counts))
+    empty.close()
+    out["fused_epilogue"] = {"ms": ms, "rays_per_s": rays.n / (ms / 1e3),
+                             "note": "mlens_shoot over a field without stars: everything but the direct sum"}
+    return out
 
 
 # --------------------------------------------------------------- learned
@@ -515,6 +576,10 @@ def run_mine(args):
             peak_b = n_sm * MUFU_RCP_PER_SM_CLK * SM_MAX_MHZ * 1e6
             bt["roofline_frac"] = bt["interactions_per_s"] / peak_b
             line["batched"] = bt
+        if "binning" in extras:
+            bn = bench_binning(M, torch, max(3, min(args.steps, 10)), 3, flush)
+            bn["fused_epilogue"]["share_of_paper_step"] = bn["fused_epilogue"]["ms"] / kernel_ms
+            line["binning"] = bn
         if "learned" in extras:
             line["learned"] = bench_learned(M, torch, max(2, min(args.steps, 3)), flush, args.learned_tol,
                                             args.learned_order)

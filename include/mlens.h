@@ -170,6 +170,18 @@ int mlens_bin(const void *beta_dev, int64_t n, const mlens_grid *src, uint32_t *
               mlens_stats *stats_host, void *stream);
 
 /*
+ * mlens_bin_grid -- mlens_bin for records that form a ray grid: beta_dev holds
+ * rays->nx * rays->ny records in the row-major order mlens_shoot_beta writes
+ * (record j * nx + i is ray (i, j); only nx and ny of `rays` are used, and they
+ * are checked like a shooting grid's).  The map is the same as mlens_bin's on
+ * the same records; the kernel bins 64 x 32 blocks of neighbouring rays per CTA,
+ * which keeps most increments in its shared-memory window.  Stats count all
+ * nx * ny records.
+ */
+int mlens_bin_grid(const void *beta_dev, const mlens_grid *rays, const mlens_grid *src, uint32_t *counts_dev,
+                   uint32_t flags, mlens_stats *stats_host, void *stream);
+
+/*
  * mlens_shoot_noalloc -- mlens_shoot for callers that must not allocate device
  * memory: code that runs while a CUDA stream is being captured into a graph
  * (cudaMalloc is not allowed there), plugins whose host application owns every

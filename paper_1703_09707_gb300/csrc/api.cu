@@ -264,6 +264,39 @@ LensTerms make_lens_terms(double kc, double g1, double g2)
 
 }  // namespace mlens
 
+namespace {
+int bin_impl(const void *beta_dev, int64_t n, int rnx, int rny, const mlens_grid *src, uint32_t *counts_dev,
+             uint32_t flags, mlens_stats *stats_host, void *stream)
+{
+    int rc;
+    if ((rc = check_src(src))) return rc;
+    if (n > 0 && !beta_dev) return fail(MLENS_ERR_ARG, "beta_dev is NULL");
+    if (!counts_dev) return fail(MLENS_ERR_ARG, "counts_dev is NULL");
+    if (((uintptr_t)counts_dev & 3u) != 0) return fail(MLENS_ERR_ARG, "counts_dev must be 4-byte aligned");
+    if (((uintptr_t)beta_dev & 15u) != 0) return fail(MLENS_ERR_ARG, "beta_dev must be 16-byte aligned");
+    if (flags & ~MLENS_ACCUMULATE) return fail(MLENS_ERR_ARG, "unknown flag bits");
+    unsigned long long *st = nullptr;
+    if ((rc = device_scratch(&st))) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t npix = (size_t)src->nx * (size_t)src->ny;
+    if (!(flags & MLENS_ACCUMULATE))
+        MLENS_CUDA(cudaMemsetAsync(counts_dev, 0, npix * sizeof(uint32_t), s), "cudaMemsetAsync(counts)");
+    MLENS_CUDA(cudaMemsetAsync(st, 0, 3 * sizeof(unsigned long long), s), "cudaMemsetAsync(stats)");
+    BinArgs a{};
+    a.beta = reinterpret_cast<const float4 *>(beta_dev);
+    a.n = n;
+    a.rnx = rnx;
+    a.rny = rny;
+    a.bin = make_bin_grid(*src);
+    a.counts = counts_dev;
+    a.stats = st;
+    cudaError_t e = launch_bin(a, s);
+    if (e != cudaSuccess) return cuda_fail(e, "bin kernel launch");
+    if (stats_host) return read_stats(st, (uint64_t)n, stats_host, s);
+    return MLENS_OK;
+}
+}  // namespace
+
 extern "C" {
 
 const char *mlens_last_error(void) { return g_err.c_str(); }
@@ -384,31 +417,17 @@ int mlens_trace(mlens_ctx *ctx, const double *theta, int64_t k, double *beta, vo
 int mlens_bin(const void *beta_dev, int64_t n, const mlens_grid *src, uint32_t *counts_dev, uint32_t flags,
               mlens_stats *stats_host, void *stream)
 {
-    int rc;
-    if ((rc = check_src(src))) return rc;
     if (n < 0 || n >= (int64_t(1) << 40)) return fail(MLENS_ERR_ARG, "n must satisfy 0 <= n < 2^40");
-    if (n > 0 && !beta_dev) return fail(MLENS_ERR_ARG, "beta_dev is NULL");
-    if (!counts_dev) return fail(MLENS_ERR_ARG, "counts_dev is NULL");
-    if (((uintptr_t)counts_dev & 3u) != 0) return fail(MLENS_ERR_ARG, "counts_dev must be 4-byte aligned");
-    if (((uintptr_t)beta_dev & 15u) != 0) return fail(MLENS_ERR_ARG, "beta_dev must be 16-byte aligned");
-    if (flags & ~MLENS_ACCUMULATE) return fail(MLENS_ERR_ARG, "unknown flag bits");
-    unsigned long long *st = nullptr;
-    if ((rc = device_scratch(&st))) return rc;
-    cudaStream_t s = (cudaStream_t)stream;
-    const size_t npix = (size_t)src->nx * (size_t)src->ny;
-    if (!(flags & MLENS_ACCUMULATE))
-        MLENS_CUDA(cudaMemsetAsync(counts_dev, 0, npix * sizeof(uint32_t), s), "cudaMemsetAsync(counts)");
-    MLENS_CUDA(cudaMemsetAsync(st, 0, 3 * sizeof(unsigned long long), s), "cudaMemsetAsync(stats)");
-    BinArgs a{};
-    a.beta = reinterpret_cast<const float4 *>(beta_dev);
-    a.n = n;
-    a.bin = make_bin_grid(*src);
-    a.counts = counts_dev;
-    a.stats = st;
-    cudaError_t e = launch_bin(a, s);
-    if (e != cudaSuccess) return cuda_fail(e, "bin kernel launch");
-    if (stats_host) return read_stats(st, (uint64_t)n, stats_host, s);
-    return MLENS_OK;
+    return bin_impl(beta_dev, n, 0, 0, src, counts_dev, flags, stats_host, stream);
+}
+
+int mlens_bin_grid(const void *beta_dev, const mlens_grid *rays, const mlens_grid *src, uint32_t *counts_dev,
+                   uint32_t flags, mlens_stats *stats_host, void *stream)
+{
+    int rc;
+    if ((rc = check_rays(rays))) return rc;
+    return bin_impl(beta_dev, (int64_t)rays->nx * rays->ny, rays->nx, rays->ny, src, counts_dev, flags, stats_host,
+                    stream);
 }
 
 void mlens_destroy(mlens_ctx *ctx)

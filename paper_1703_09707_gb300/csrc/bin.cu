@@ -1,7 +1,14 @@
 // bin.cu -- the binning step of Algorithm 1 on its own: float-pair source
-// positions -> exact pixel -> warp-aggregated, shared-memory-privatised
-// window histogram -> global uint32 counts.  Same rule and same epilogue as
-// the fused shooting kernels.
+// positions -> exact pixel -> run-aggregated, shared-memory-privatised window
+// histogram -> global uint32 counts.  Same rule and same epilogue as the fused
+// shooting kernels.
+//
+// Two record orders.  Flat: a CTA takes 4096 consecutive records.  Grid: the
+// records are a row-major nx x ny ray grid and a CTA takes a 64 x 64 block of
+// it; neighbouring rays land on neighbouring pixels, so most of the block's
+// records hit its 64 x 64 window, placed on the record nearest the block's
+// centre (consecutive records of one grid row would instead spread along a
+// strip of the map far longer than the window).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -10,53 +17,119 @@
 namespace mlens {
 
 constexpr int kBinThreads = 256;
-constexpr int kBinPer = 8;  // records per thread; a CTA takes 2048 consecutive records
+constexpr int kBinPer = 8;                                    // records per thread and round
+constexpr int kBinRounds = 2;                                 // the window is placed after round 0's loads
+constexpr int kBinRecs = kBinThreads * kBinPer * kBinRounds;  // 4096 records per CTA
+constexpr int kBinTileX = 64;                                 // grid order: 64 x 64 records per CTA
+constexpr int kBinTileY = kBinRecs / kBinTileX;
+constexpr int kBinRowStep = kBinThreads / kBinTileX;          // rows between a thread's records
 
+// Record r (0 <= r < kBinPer * kBinRounds) of thread tid: index, validity, and a
+// placement priority (unique per record; lowest = nearest the block's centre in
+// grid order, first in flat order).
+template <bool GRID>
+__device__ __forceinline__ int64_t bin_record(const BinArgs &a, int tid, int r, bool &ok, unsigned &prio)
+{
+    if (GRID) {
+        const int c = tid % kBinTileX, rr = tid / kBinTileX + r * kBinRowStep;
+        const int col = blockIdx.x * kBinTileX + c;
+        const int64_t row = (int64_t)blockIdx.y * kBinTileY + rr;
+        ok = col < a.rnx && row < a.rny;
+        prio = ((unsigned)(abs(rr - kBinTileY / 2) + abs(c - kBinTileX / 2)) << 12) | (unsigned)(rr * kBinTileX + c);
+        return row * a.rnx + col;  // a warp reads 32 consecutive records of one row
+    }
+    const int64_t idx = (int64_t)blockIdx.x * kBinRecs + (int64_t)r * kBinThreads + tid;
+    ok = idx < a.n;
+    prio = (unsigned)(r * kBinThreads + tid);
+    return idx;
+}
+
+template <bool GRID>
+__device__ __forceinline__ void bin_one(const BinArgs &a, const float4 &v, bool ok, const WinHist &W, unsigned &nb,
+                                        unsigned &no, unsigned &nn)
+{
+    uint32_t key = kNoKey;
+    if (ok) {
+        int gpx = 0, gpy = 0;
+        const int pix = pair_pixel(v.x, v.y, v.z, v.w, a.bin, gpx, gpy);
+        if (pix >= 0) {
+            ++nb;
+            key = hist_key(pix, gpx, gpy, W, a.bin);
+        } else if (pix == -1) {
+            ++no;
+        } else {
+            ++nn;
+        }
+    }
+    hist_add_warp(key, W, a.counts);
+}
+
+template <bool GRID>
 __global__ void __launch_bounds__(kBinThreads) k_bin(BinArgs a)
 {
-    __shared__ uint32_t hist[kWin * kWin];
+    __shared__ __align__(16) uint32_t hist[kWin * kWin];
     __shared__ int win[2];
+    __shared__ unsigned wq;
     __shared__ unsigned sred[3];
     const int tid = threadIdx.x;
-    const int64_t base = (int64_t)blockIdx.x * kBinThreads * kBinPer;
-    for (int b = tid; b < kWin * kWin; b += kBinThreads) hist[b] = 0u;
+    hist_zero(hist);
     if (tid == 0) {
+        wq = 0xffffffffu;
         sred[0] = sred[1] = sred[2] = 0u;
-        // window on the first finite record of this CTA's range (rays of one grid
-        // row segment land close together)
-        int wx = -(1 << 30), wy = -(1 << 30);
-        for (int r = 0; r < kBinThreads * kBinPer && base + r < a.n; ++r) {
-            float4 v = a.beta[base + r];
-            if (isfinite(v.x) && isfinite(v.y)) {
-                wx = pair_axis_rough(v.x, a.bin.ax) - kWin / 2;
-                wy = pair_axis_rough(v.y, a.bin.ay) - kWin / 2;
-                break;
-            }
-        }
-        win[0] = wx;
-        win[1] = wy;
     }
     __syncthreads();
-    WinHist W{hist, win[0], win[1]};
-    unsigned nb = 0, no = 0, nn = 0;
+
+    // round 0: loads first (all in flight together), then the window
+    float4 v[kBinPer];
+    bool ok[kBinPer];
+    unsigned best = 0xffffffffu;
 #pragma unroll
     for (int r = 0; r < kBinPer; ++r) {
-        const int64_t idx = base + (int64_t)r * kBinThreads + tid;  // coalesced
-        uint32_t key = kNoKey;
-        if (idx < a.n) {
-            const float4 v = a.beta[idx];
-            int gpx = 0, gpy = 0;
-            const int pix = pair_pixel(v.x, v.y, v.z, v.w, a.bin, gpx, gpy);
-            if (pix >= 0) {
-                ++nb;
-                key = hist_key(pix, gpx, gpy, W, a.bin);
-            } else if (pix == -1) {
-                ++no;
-            } else {
-                ++nn;
+        unsigned prio;
+        const int64_t idx = bin_record<GRID>(a, tid, r, ok[r], prio);
+        v[r] = ok[r] ? a.beta[idx] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int r = 0; r < kBinPer; ++r) {
+        bool okr;
+        unsigned prio;
+        bin_record<GRID>(a, tid, r, okr, prio);
+        if (ok[r] && isfinite(v[r].x) && isfinite(v[r].y)) best = min(best, prio);
+    }
+    const unsigned wbest = __reduce_min_sync(0xffffffffu, best);
+    if ((tid & 31) == 0 && wbest != 0xffffffffu) atomicMin(&wq, wbest);
+    __syncthreads();
+    const unsigned q = wq;
+    if (q == 0xffffffffu) {
+        if (tid == 0) win[0] = win[1] = -(1 << 30);  // no finite record: every key is global
+    } else {
+#pragma unroll
+        for (int r = 0; r < kBinPer; ++r) {
+            bool okr;
+            unsigned prio;
+            bin_record<GRID>(a, tid, r, okr, prio);
+            if (prio == q) {
+                win[0] = pair_axis_rough(v[r].x, a.bin.ax) - kWin / 2;
+                win[1] = pair_axis_rough(v[r].y, a.bin.ay) - kWin / 2;
             }
         }
-        hist_add_warp(key, W, a.counts);
+    }
+    __syncthreads();
+    const WinHist W{hist, win[0], win[1]};
+    unsigned nb = 0, no = 0, nn = 0;
+#pragma unroll
+    for (int r = 0; r < kBinPer; ++r) bin_one<GRID>(a, v[r], ok[r], W, nb, no, nn);
+
+#pragma unroll
+    for (int k = 1; k < kBinRounds; ++k) {
+#pragma unroll
+        for (int r = 0; r < kBinPer; ++r) {
+            unsigned prio;
+            const int64_t idx = bin_record<GRID>(a, tid, k * kBinPer + r, ok[r], prio);
+            v[r] = ok[r] ? a.beta[idx] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int r = 0; r < kBinPer; ++r) bin_one<GRID>(a, v[r], ok[r], W, nb, no, nn);
     }
     __syncthreads();
     hist_flush(W, a.bin, a.counts);
@@ -66,10 +139,15 @@ __global__ void __launch_bounds__(kBinThreads) k_bin(BinArgs a)
 cudaError_t launch_bin(const BinArgs &a, cudaStream_t s)
 {
     if (a.n <= 0) return cudaSuccess;
-    const int64_t per = (int64_t)kBinThreads * kBinPer;
-    const int64_t nb = (a.n + per - 1) / per;
+    if (a.rnx > 0) {
+        const int64_t tx = (a.rnx + kBinTileX - 1) / kBinTileX, ty = (a.rny + kBinTileY - 1) / kBinTileY;
+        if (tx > 0x7fffffff || ty > 65535) return cudaErrorInvalidConfiguration;
+        k_bin<true><<<dim3((unsigned)tx, (unsigned)ty), kBinThreads, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    const int64_t nb = (a.n + kBinRecs - 1) / kBinRecs;
     if (nb > 0x7fffffff) return cudaErrorInvalidConfiguration;
-    k_bin<<<(unsigned)nb, kBinThreads, 0, s>>>(a);
+    k_bin<false><<<(unsigned)nb, kBinThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

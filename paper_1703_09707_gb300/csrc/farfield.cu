@@ -995,7 +995,7 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
     const int ix = i0 + tx;
     const bool col_ok = ix < R.nx;
     __syncthreads();
-    for (int b = tid; b < kWin * kWin; b += kThreads) sm.hist[b] = 0u;
+    hist_zero(sm.hist);
     if (tid == 0) {
         ts.win[0] = pair_axis_rough(bxh[0], a.bin.ax) - kWin / 2;
         ts.win[1] = pair_axis_rough(byh[0], a.bin.ay) - kWin / 2;

@@ -35,7 +35,7 @@ __device__ __forceinline__ float rcp_approx(float x)
 // float pairs and floored exactly; -1 when outside [0, n).  The operation
 // sequence is part of the library's contract (a CPU re-binning with the same
 // float32 operations reproduces the GPU map bit for bit).
-__device__ __forceinline__ int pair_axis(float bh, float bl, const AxisPair &A)
+__device__ __forceinline__ int pair_axis_exact(float bh, float bl, const AxisPair &A)
 {
     float dh, dl;
     two_sum(bh, -A.x0h, dh, dl);
@@ -52,6 +52,30 @@ __device__ __forceinline__ int pair_axis(float bh, float bl, const AxisPair &A)
     if (p == uh && ul < 0.0f) p = __fsub_rn(p, 1.0f);
     if (p < 0.0f || p >= (float)A.n) return -1;
     return (int)p;
+}
+
+// The same pixel, usually without the pair arithmetic.  u = fl(fl(bh - x0h) sh)
+// differs from the pair value P = uh + ul that pair_axis_exact floors by at most
+//     |u - P| <= 2^-23 |u| (two roundings) + |d sl| + (|bl| + |x0l|)(|sh| + |sl|)
+//                + 2^-23 (|bl| + |x0l|) |s| + 2^-45 |u| (the pair's own error),
+// d = bh - x0h.  del below is at least 1.5x that bound even after its own
+// rounding and the rounding of u -/+ del (|sl| <= 2^-24 |sh| by construction),
+// plus 2^-100 so that del > 0 even where the products underflow.  If no pixel
+// edge lies in [u - del, u + del], floor(P) = floor(u): the result equals
+// pair_axis_exact's bit for bit; otherwise (a fraction ~ 2 del of the rays, and
+// every non-finite u) the exact rule runs.
+__device__ __forceinline__ int pair_axis(float bh, float bl, const AxisPair &A)
+{
+    const float d = __fsub_rn(bh, A.x0h);
+    const float u = __fmul_rn(d, A.sh);
+    const float tail = __fmul_rn(__fadd_rn(fabsf(bl), fabsf(A.x0l)), 2.0f * fabsf(A.sh));
+    const float del = __fmaf_rn(0x1p-22f, fabsf(u), __fmaf_rn(fabsf(d), 2.0f * fabsf(A.sl), __fadd_rn(tail, 0x1p-100f)));
+    const float lo = floorf(__fsub_rn(u, del));
+    if (lo == floorf(__fadd_rn(u, del))) {  // false for NaN
+        if (lo < 0.0f || lo >= (float)A.n) return -1;
+        return (int)lo;
+    }
+    return pair_axis_exact(bh, bl, A);
 }
 
 // Unclamped floor of the hi part (used only to place the histogram window).
@@ -97,13 +121,26 @@ __device__ __forceinline__ uint32_t hist_key(int pix, int px, int py, const WinH
     return (uint32_t)(kWin * kWin) + (uint32_t)pix;
 }
 
+// Clear the window (uint4 stores; the window is 16-byte aligned).
+__device__ __forceinline__ void hist_zero(uint32_t *h)
+{
+    uint4 *h4 = reinterpret_cast<uint4 *>(h);
+    for (int b = threadIdx.x; b < kWin * kWin / 4; b += blockDim.x) h4[b] = make_uint4(0u, 0u, 0u, 0u);
+}
+
 // Warp-cooperative increment: every lane of the warp must call this together.
+// Lanes hold neighbouring rays, whose pixels repeat in runs: the first lane of
+// each run of equal keys adds the run's length (one atomic per run instead of
+// one per ray; cheaper than matching all equal keys of the warp).
 __device__ __forceinline__ void hist_add_warp(uint32_t key, const WinHist &W, uint32_t *counts)
 {
     const unsigned lane = threadIdx.x & 31u;
-    unsigned peers = __match_any_sync(0xffffffffu, key);
-    if (key != kNoKey && lane == (unsigned)(__ffs(peers) - 1)) {
-        unsigned c = __popc(peers);
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const bool start = lane == 0u || prev != key;
+    const unsigned starts = __ballot_sync(0xffffffffu, start);
+    if (start && key != kNoKey) {
+        const unsigned later = starts & (0xfffffffeu << lane);
+        const unsigned c = (later ? (unsigned)(__ffs(later) - 1) : 32u) - lane;
         if (key < (uint32_t)(kWin * kWin))
             atomicAdd(&W.h[key], c);
         else
@@ -114,12 +151,15 @@ __device__ __forceinline__ void hist_add_warp(uint32_t key, const WinHist &W, ui
 // Add the window to the global map (bins outside the map are never filled).
 __device__ __forceinline__ void hist_flush(const WinHist &W, const BinGrid &g, uint32_t *counts)
 {
-    for (int b = threadIdx.x; b < kWin * kWin; b += blockDim.x) {
-        uint32_t v = W.h[b];
-        if (v) {
-            int gx = W.wx0 + (b % kWin), gy = W.wy0 + (b / kWin);
-            atomicAdd(&counts[(int64_t)gy * g.nx + gx], v);
-        }
+    const uint4 *h4 = reinterpret_cast<const uint4 *>(W.h);
+    for (int b = threadIdx.x; b < kWin * kWin / 4; b += blockDim.x) {
+        const uint4 v = h4[b];
+        if ((v.x | v.y | v.z | v.w) == 0u) continue;
+        const int64_t base = (int64_t)(W.wy0 + b / (kWin / 4)) * g.nx + (W.wx0 + 4 * (b % (kWin / 4)));
+        if (v.x) atomicAdd(&counts[base + 0], v.x);
+        if (v.y) atomicAdd(&counts[base + 1], v.y);
+        if (v.z) atomicAdd(&counts[base + 2], v.z);
+        if (v.w) atomicAdd(&counts[base + 3], v.w);
     }
 }
 

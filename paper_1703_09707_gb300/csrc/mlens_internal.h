@@ -61,6 +61,7 @@ struct ShootArgs {
 struct BinArgs {
     const float4 *beta;
     int64_t n;
+    int rnx, rny;  // records form a row-major rnx x rny ray grid (0 = flat order)
     BinGrid bin;
     uint32_t *counts;
     unsigned long long *stats;

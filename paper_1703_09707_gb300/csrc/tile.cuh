@@ -255,7 +255,7 @@ __device__ __forceinline__ void shoot_tile(const ShootArgs &a, int bx, int by, S
     const int ix = i0 + tx;
     const bool col_ok = ix < R.nx;
     __syncthreads();  // star stages are dead: reuse the memory as the window
-    for (int b = tid; b < kWin * kWin; b += kThreads) sm.hist[b] = 0u;
+    hist_zero(sm.hist);
     if (tid == 0) {
         ts.win[0] = pair_axis_rough(bxh[0], a.bin.ax) - kWin / 2;
         ts.win[1] = pair_axis_rough(byh[0], a.bin.ay) - kWin / 2;

@@ -96,6 +96,7 @@ SIGNATURES = {
     "mlens_shoot_beta": (C.c_int, [_vp, _gp, _gp, _vp, _vp, C.c_uint32, _sp, _vp]),
     "mlens_trace": (C.c_int, [_vp, _dp, C.c_int64, _dp, _vp]),
     "mlens_bin": (C.c_int, [_vp, C.c_int64, _gp, _vp, C.c_uint32, _sp, _vp]),
+    "mlens_bin_grid": (C.c_int, [_vp, _gp, _gp, _vp, C.c_uint32, _sp, _vp]),
     "mlens_shoot_noalloc": (C.c_int, [_vp, C.c_int64, C.c_double, C.c_double, C.c_double, _gp, _gp, _vp, C.c_uint32,
                                       _sp, _vp]),
     "mlens_batch_create": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int32, _gp, _gp, C.POINTER(_vp),
@@ -264,6 +265,15 @@ def mlens_bin(beta, n: int, src, counts, flags: int = 0, stats: bool = False, st
     s = grid(src)
     _check(load().mlens_bin(_dev_ptr(beta), int(n), C.byref(s), _dev_ptr(counts), int(flags),
                             C.byref(st) if stats else None, _stream_ptr(stream)))
+    return st.asdict() if stats else None
+
+
+def mlens_bin_grid(beta, rays, src, counts, flags: int = 0, stats: bool = False, stream=None):
+    """beta: rays.nx * rays.ny float-pair records in ray-grid row order."""
+    st = mlens_stats()
+    g, s = grid(rays), grid(src)
+    _check(load().mlens_bin_grid(_dev_ptr(beta), C.byref(g), C.byref(s), _dev_ptr(counts), int(flags),
+                                 C.byref(st) if stats else None, _stream_ptr(stream)))
     return st.asdict() if stats else None
 
 

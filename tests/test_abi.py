@@ -73,6 +73,13 @@ def test_bad_arguments_are_rejected_before_any_device_call(lib):
     assert lib.mlens_bin(C.c_void_p(16), 4, C.byref(zg), C.c_void_p(16), 0, None, None) == M.MLENS_ERR_ARG
     assert lib.mlens_bin(C.c_void_p(16), 4, C.byref(g), C.c_void_p(18), 0, None, None) == M.MLENS_ERR_ARG
     assert lib.mlens_bin(C.c_void_p(16), 4, C.byref(g), C.c_void_p(16), 8, None, None) == M.MLENS_ERR_ARG
+    bigr = M.mlens_grid(-1.0, 1.0, -1.0, 1.0, 1 << 21, 4)
+    assert lib.mlens_bin_grid(C.c_void_p(16), C.byref(bigr), C.byref(g), C.c_void_p(16), 0, None,
+                              None) == M.MLENS_ERR_ARG
+    assert lib.mlens_bin_grid(C.c_void_p(16), None, C.byref(g), C.c_void_p(16), 0, None, None) == M.MLENS_ERR_ARG
+    assert lib.mlens_bin_grid(C.c_void_p(24), C.byref(g), C.byref(g), C.c_void_p(16), 0, None,
+                              None) == M.MLENS_ERR_ARG
+    assert lib.mlens_bin_grid(None, C.byref(g), C.byref(g), C.c_void_p(16), 0, None, None) == M.MLENS_ERR_ARG
     lib.mlens_destroy(None)  # must be a no-op
 
 

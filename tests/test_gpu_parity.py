@@ -205,6 +205,62 @@ def test_standalone_bin_matches_fused_map():
     st2 = M.mlens_bin(beta, rays.n, src, counts2, stats=True)
     assert torch.equal(counts, counts2)
     assert st == st2
+    counts3 = torch.empty_like(counts)
+    st3 = M.mlens_bin_grid(beta, rays, src, counts3, stats=True)
+    assert torch.equal(counts, counts3) and st == st3
+    ctx.close()
+
+
+@pytest.mark.parametrize("nx,x0,w", [(1024, -10.0, 20.0), (4096, 3.25, 0.1), (37, -120.5, 300.0), (32768, -4.0, 8.0)])
+def test_bin_records_on_pixel_edges(nx, x0, w):
+    """Records placed on pixel edges (as float pairs, and hi parts a few ulps off an
+    edge, and lo parts that straddle it): the kernels decide most pixels from the hi
+    parts and fall back to the pair rule near edges; every pixel must equal the
+    float-pair rule's (re-binned on the CPU)."""
+    rng = np.random.default_rng(nx)
+    src = W.Grid(x0, x0 + w, x0, x0 + w, nx, nx)
+    k = 1 << 20
+    f32 = np.float32
+    i = rng.integers(-2, nx + 2, k)
+    edge = x0 + i * (w / nx)
+    bh = edge.astype(f32)
+    mode = rng.integers(0, 4, k)
+    ulp = np.spacing(np.abs(bh)).astype(f32)
+    bh = np.where(mode == 1, bh + rng.integers(-3, 4, k).astype(f32) * ulp, bh).astype(f32)
+    bl = np.where(mode == 0, (edge - bh.astype(np.float64)).astype(f32), f32(0))
+    bl = np.where(mode == 2, (rng.uniform(-0.5, 0.5, k) * ulp).astype(f32), bl).astype(f32)
+    bh = np.where(mode == 3, rng.uniform(x0 - 0.1 * w, x0 + 1.1 * w, k).astype(f32), bh).astype(f32)
+    perm = rng.permutation(k)
+    b4 = np.stack([bh, bh[perm], bl, bl[perm]], 1).astype(f32)
+    c_ref, st_ref = oracle.rebin_pair(b4, src)
+    beta = torch.from_numpy(b4.reshape(-1)).cuda()
+    counts = torch.empty(src.n, dtype=torch.int32, device="cuda")
+    st = M.mlens_bin(beta, k, src, counts, stats=True)
+    assert np.array_equal(counts.cpu().numpy().view(np.uint32).reshape(src.ny, src.nx), c_ref) and st == st_ref
+    rays = W.Grid(0.0, 1.0, 0.0, 1.0, 1000, k // 1000)
+    n = rays.n
+    st = M.mlens_bin_grid(beta, rays, src, counts, stats=True)
+    c_ref, st_ref = oracle.rebin_pair(b4[:n], src)
+    assert np.array_equal(counts.cpu().numpy().view(np.uint32).reshape(src.ny, src.nx), c_ref) and st == st_ref
+
+
+def test_grid_ordered_bin_on_ragged_grid():
+    """1000 x 1000 rays: neither dimension is a multiple of the 64 x 32 binning block."""
+    wl = W.config("tiny")
+    f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
+    assert rays.nx % 64 and rays.ny % 32
+    ctx = make_ctx(f)
+    counts = torch.empty(src.n, dtype=torch.int32, device="cuda")
+    beta = torch.empty(rays.n * 4, dtype=torch.float32, device="cuda")
+    st = M.mlens_shoot_beta(ctx, rays, src, counts, beta, stats=True)
+    c_flat, c_grid = torch.empty_like(counts), torch.empty_like(counts)
+    st_flat = M.mlens_bin(beta, rays.n, src, c_flat, stats=True)
+    st_grid = M.mlens_bin_grid(beta, rays, src, c_grid, stats=True)
+    assert torch.equal(counts, c_flat) and torch.equal(counts, c_grid)
+    assert st == st_flat == st_grid
+    # accumulate on top of an existing map
+    M.mlens_bin_grid(beta, rays, src, c_grid, flags=M.MLENS_ACCUMULATE)
+    assert torch.equal(c_grid, 2 * counts)
     ctx.close()
 
 
