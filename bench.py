@@ -66,8 +66,8 @@ def parse():
     ap.add_argument("--print-kernel-hash", action="store_true", help="print the FP32 kernel source hash and exit")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-fields and learned-far-field measurements that ride along the main line")
-    ap.add_argument("--extras", default="batched,binning,learned",
-                    help="comma list of extra sections: batched, binning, learned")
+    ap.add_argument("--extras", default="batched,binning,split,learned",
+                    help="comma list of extra sections: batched, binning, split, learned")
     ap.add_argument("--learned-tol", type=float, default=5e-6, help="per-cell validation bound of the learned field")
     ap.add_argument("--learned-order", type=int, default=8)
     return ap.parse_args()
@@ -321,6 +321,41 @@ def bench_binning(M, torch, steps: int, warmup: int, flush):
     empty.close()
     out["fused_epilogue"] = {"ms": ms, "rays_per_s": rays.n / (ms / 1e3),
                              "note": "mlens_shoot over a field without stars: everything but the direct sum"}
+    return out
+
+
+# ----------------------------------------------------------------- split
+def bench_split(M, torch, flush, peak):
+    """10^7 stars on ray grids of 256^2 and 512^2 rays (32 and 128 tiles of 64 x 32
+    rays, fewer than the GPU's 152 SMs): each tile's star sum split over clusters of
+    1, 2, 4 and 8 CTAs, one CUDA-event-timed map per setting after a warm-up map."""
+    wl = W.config("large_n")
+    f, rays0, src = wl.fields[0], wl.rays[0], wl.srcs[0]
+    stream = torch.cuda.current_stream()
+    ctx = M.mlens_create(f.xy, f.m, f.kappa_c, f.gamma1, f.gamma2, M.MLENS_PREC_FP32)
+    counts = torch.empty(src.n, dtype=torch.int32, device="cuda")
+    out = {"workload": f"large_n: {f.n} stars, {src.nx}x{src.ny} map; ray grids over the same box"}
+    for n in (256, 512):
+        rays = W.Grid(rays0.x0, rays0.x1, rays0.y0, rays0.y1, n, n)
+        M.mlens_set_star_split(ctx, 0)
+        auto = M.mlens_star_split_for(ctx, rays)
+        inter = rays.n * f.n
+        by = {}
+        for split in (1, 2, 4, 8):
+            M.mlens_set_star_split(ctx, split)
+            M.mlens_shoot(ctx, rays, src, counts)
+            flush.fill_(float(split))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            M.mlens_shoot(ctx, rays, src, counts)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            by[str(split)] = {"ms": ms, "interactions_per_s": inter / (ms / 1e3),
+                              "roofline_frac": inter / (ms / 1e3) / peak}
+        out[f"rays_{n}"] = {"tiles": -(-n // 64) * -(-n // 32), "auto_split": auto, "by_split": by,
+                            "speedup_auto_vs_unsplit": by["1"]["ms"] / by[str(auto)]["ms"]}
+    ctx.close()
     return out
 
 
@@ -580,6 +615,8 @@ def run_mine(args):
             bn = bench_binning(M, torch, max(3, min(args.steps, 10)), 3, flush)
             bn["fused_epilogue"]["share_of_paper_step"] = bn["fused_epilogue"]["ms"] / kernel_ms
             line["binning"] = bn
+        if "split" in extras:
+            line["split"] = bench_split(M, torch, flush, peak)
         if "learned" in extras:
             line["learned"] = bench_learned(M, torch, max(2, min(args.steps, 3)), flush, args.learned_tol,
                                             args.learned_order)

@@ -115,6 +115,31 @@ int mlens_set_precision(mlens_ctx *ctx, int32_t precision);
 int mlens_set_tuning(mlens_ctx *ctx, int32_t rays_per_thread, int32_t star_stage, int32_t fma_pairs);
 
 /*
+ * mlens_set_star_split -- how many CTAs share one ray tile's star sum in the
+ * FP32 re-centred kernel (MLENS_PREC_FP32 with the default 256-star stage and
+ * fma_pairs = 0; other settings never split).  The paper's closing discussion
+ * of very large star fields proposes splitting the bending-angle sum of one
+ * image position over several threads; here split = 2, 4 or 8 CTAs form a
+ * thread-block cluster on the tile, each sums one of `split` consecutive
+ * 32-star-aligned slices of the stars with the same compensated loop, and the
+ * first CTA folds the others' partial sums (read through distributed shared
+ * memory, in slice order) into its own before beta and binning.  That keeps the
+ * GPU full when a grid has few tiles for its star count.  split = 1 never
+ * splits; 0 (the default) chooses per call from the number of tiles, the SM
+ * count and the star count (at least 2048 stars per slice).  The sum's order
+ * depends on the split, so beta may differ in its last bits between splits
+ * (never by more than the error bar); a given split is deterministic.
+ * Errors: MLENS_ERR_ARG.
+ */
+int mlens_set_star_split(mlens_ctx *ctx, int32_t split);
+
+/*
+ * mlens_star_split_for -- the split mlens_shoot / mlens_shoot_beta will use on
+ * this context for the ray grid `rays` (1 = none).  Errors: MLENS_ERR_ARG.
+ */
+int mlens_star_split_for(const mlens_ctx *ctx, const mlens_grid *rays, int32_t *split_out);
+
+/*
  * mlens_shoot -- Algorithm 1 over a whole ray grid: deflect every ray by Eq. (3),
  * map it to the source plane by Eq. (2) and count it in its source pixel.
  *   rays       ray grid; 1 <= nx, ny <= 2^20 and nx*ny <= 2^40.

@@ -32,6 +32,7 @@ int fail(int code, const std::string &msg)
 int cuda_fail(cudaError_t e, const char *what)
 {
     g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    clear_pending_error();
     return e == cudaErrorMemoryAllocation ? MLENS_ERR_NOMEM : MLENS_ERR_CUDA;
 }
 
@@ -113,6 +114,15 @@ int read_stats(unsigned long long *d_stats, uint64_t total, mlens_stats *st, cud
     return MLENS_OK;
 }
 
+// CTAs per tile for the FP32 re-centred kernel: the split star sum runs with the
+// default stage and MUFU reciprocals only.
+int effective_split(const mlens_ctx *ctx, const RayGrid &r)
+{
+    if (ctx->precision != MLENS_PREC_FP32 || ctx->star_stage != kSplitStage || ctx->fma_pairs) return 1;
+    if (ctx->star_split) return ctx->star_split;
+    return auto_star_split(r, ctx->pairs_per_thread, ctx->n_pad, ctx->nsm);
+}
+
 int shoot_impl(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid *src, uint32_t *counts, void *beta,
                uint32_t flags, mlens_stats *stats, void *stream)
 {
@@ -139,8 +149,11 @@ int shoot_impl(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid *src, ui
     a.stats = ctx->d_stats;
     a.beta_out = beta;
     cudaError_t e;
+    const int split = effective_split(ctx, a.rays);
     if (ctx->precision == MLENS_PREC_FP64)
         e = launch_shoot_fp64(a, s);
+    else if (split > 1)
+        e = launch_shoot_split(a, ctx->pairs_per_thread, split, s);
     else
         e = launch_shoot_fp32(a, ctx->pairs_per_thread, ctx->precision == MLENS_PREC_FP32_NAIVE, s, ctx->star_stage,
                               ctx->fma_pairs);
@@ -341,6 +354,7 @@ int mlens_create(mlens_ctx **out, const double *xy, const double *m, int64_t n, 
                                                std::to_string(prop.major) + std::to_string(prop.minor));
     mlens_ctx *c = new mlens_ctx();
     c->device = dev;
+    c->nsm = prop.multiProcessorCount;
     c->n = n;
     c->n_pad = n_pad;
     c->lens = make_lens_terms(kappa_c, gamma1, gamma2);
@@ -378,6 +392,25 @@ int mlens_set_tuning(mlens_ctx *ctx, int32_t rays_per_thread, int32_t star_stage
     ctx->pairs_per_thread = rays_per_thread / 2;
     ctx->star_stage = star_stage ? star_stage : 256;
     ctx->fma_pairs = fma_pairs;
+    return MLENS_OK;
+}
+
+int mlens_set_star_split(mlens_ctx *ctx, int32_t split)
+{
+    if (!ctx) return fail(MLENS_ERR_ARG, "context is NULL");
+    if (split != 0 && split != 1 && split != 2 && split != 4 && split != 8)
+        return fail(MLENS_ERR_ARG, "split must be 0 (automatic), 1, 2, 4 or 8");
+    ctx->star_split = split;
+    return MLENS_OK;
+}
+
+int mlens_star_split_for(const mlens_ctx *ctx, const mlens_grid *rays, int32_t *split_out)
+{
+    if (!ctx) return fail(MLENS_ERR_ARG, "context is NULL");
+    if (!split_out) return fail(MLENS_ERR_ARG, "split_out is NULL");
+    int rc;
+    if ((rc = check_rays(rays))) return rc;
+    *split_out = effective_split(ctx, make_ray_grid(*rays));
     return MLENS_OK;
 }
 

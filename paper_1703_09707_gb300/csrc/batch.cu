@@ -59,6 +59,7 @@ int bfail(int code, const std::string &m)
 int bcuda(cudaError_t e, const char *what)
 {
     set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
+    clear_pending_error();
     return e == cudaErrorMemoryAllocation ? MLENS_ERR_NOMEM : MLENS_ERR_CUDA;
 }
 

@@ -90,10 +90,22 @@ int64_t tiles_of(const RayGrid &r, int pairs_per_thread);
 cudaError_t launch_shoot_fp64(const ShootArgs &a, cudaStream_t s);
 cudaError_t launch_trace_fp64(const float4 *stars, int64_t nstars, const LensTerms &lens, const double2 *theta,
                               double2 *beta, int64_t k, cudaStream_t s);
+// Split star sum (re-centred FP32, 256-star stages, MUFU reciprocals): clusters
+// of `split` in {2, 4, 8} CTAs per tile.  auto_star_split picks the split for a
+// grid (1 = none) from the wave efficiency on `nsm` SMs.
+constexpr int kSplitStage = 256;
+constexpr int64_t kMinSplitStars = 2048;
+cudaError_t launch_shoot_split(const ShootArgs &a, int pairs_per_thread, int split, cudaStream_t s);
+int auto_star_split(const RayGrid &r, int pairs_per_thread, int64_t nstars, int nsm);
 cudaError_t launch_bin(const BinArgs &a, cudaStream_t s);
 
 // helpers (api.cu)
 void set_last_error(const std::string &msg);
+// A failed launch (a bad configuration, an exhausted resource) leaves its error
+// pending in the runtime; the next launch's cudaGetLastError would report it
+// again.  Every error path clears it after recording the message (errors that
+// corrupt the context stay sticky regardless).
+inline void clear_pending_error() { (void)cudaGetLastError(); }
 // Every device allocation of the library goes through these: they keep count of
 // the bytes in use and refuse (cudaErrorMemoryAllocation) an allocation that would
 // exceed the budget set with mlens_set_device_memory_limit.
@@ -125,5 +137,7 @@ struct mlens_ctx {
     int pairs_per_thread = 4;
     int star_stage = 256;
     int fma_pairs = 0;
+    int star_split = 0;     // 0 = automatic, else 1, 2, 4 or 8 CTAs per tile
+    int nsm = 0;            // SMs of the context's device
     FarState *ff = nullptr;
 };

@@ -47,6 +47,7 @@ int arg_error(const char *msg)
 int cuda_error(cudaError_t e, const char *what)
 {
     set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
+    clear_pending_error();
     return MLENS_ERR_CUDA;
 }
 

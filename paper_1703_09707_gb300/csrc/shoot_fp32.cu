@@ -27,6 +27,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "tile.cuh"
 
 namespace mlens {
@@ -37,6 +39,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_shoot_fp32(ShootArgs a, int by0
     __shared__ __align__(16) ShootSmem<SC> sm;
     __shared__ TileShared ts;
     shoot_tile<NP, SC, NAIVE, NRP>(a, blockIdx.x, by0 + (int)blockIdx.y, sm, ts);
+}
+
+// Split star sum: clusters of SPLIT CTAs along x share one tile (tile column
+// blockIdx.x / SPLIT); partials are reduced through distributed shared memory.
+template <int NP, int SPLIT>
+__global__ void __launch_bounds__(kThreads, 2) k_shoot_split(ShootArgs a, int by0)
+{
+    __shared__ __align__(16) ShootSmem<kSplitStage> sm;
+    __shared__ TileShared ts;
+    extern __shared__ float4 part[];  // 2 NP float4 per thread
+    shoot_tile<NP, kSplitStage, false, 0, SPLIT>(a, (int)(blockIdx.x / SPLIT), by0 + (int)blockIdx.y, sm, ts, part);
 }
 
 // Persistent kernel over many fields: CTAs pull (field, tile) items from one
@@ -103,6 +116,76 @@ cudaError_t launch_shoot_fp32(const ShootArgs &a, int pairs_per_thread, bool nai
     if (naive) return launch_sel<true, 0>(a, pairs_per_thread, stage, s);
     return fma_pairs ? launch_sel<false, 1>(a, pairs_per_thread, stage, s)
                      : launch_sel<false, 0>(a, pairs_per_thread, stage, s);
+}
+
+template <int NP, int SPLIT>
+static cudaError_t launch_split_t(const ShootArgs &a, cudaStream_t s)
+{
+    const int tx = (a.rays.nx + kTileX - 1) / kTileX, ty = (a.rays.ny + tile_rows(NP) - 1) / tile_rows(NP);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = SPLIT;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 2 * NP * kThreads * sizeof(float4);
+    // static (the stage/window union) + dynamic (partials) exceeds the 48 KB a
+    // launch gets without opting in for NP = 4
+    cudaError_t e0 = cudaFuncSetAttribute(k_shoot_split<NP, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)cfg.dynamicSmemBytes);
+    if (e0 != cudaSuccess) return e0;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    for (int by0 = 0; by0 < ty; by0 += 65535) {
+        cfg.gridDim = dim3((unsigned)(tx * SPLIT), (unsigned)min(65535, ty - by0));
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, k_shoot_split<NP, SPLIT>, a, by0);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_shoot_split(const ShootArgs &a, int pairs_per_thread, int split, cudaStream_t s)
+{
+    if (pairs_per_thread == 2) {
+        if (split == 2) return launch_split_t<2, 2>(a, s);
+        if (split == 4) return launch_split_t<2, 4>(a, s);
+        if (split == 8) return launch_split_t<2, 8>(a, s);
+    } else {
+        if (split == 2) return launch_split_t<4, 2>(a, s);
+        if (split == 4) return launch_split_t<4, 4>(a, s);
+        if (split == 8) return launch_split_t<4, 8>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int auto_star_split(const RayGrid &r, int pairs_per_thread, int64_t nstars, int nsm)
+{
+    // One CTA per SM already keeps the SM's reciprocal unit near its peak, and
+    // a second resident CTA (both kernels are launch-bounded to two per SM)
+    // shares it.  For C = tiles * R equal CTAs of work T / R the map therefore
+    // takes T / R when C <= nsm (one CTA per SM) and about
+    // ceil(C / (2 nsm)) * 2 T / R otherwise (rounds of two CTAs at half speed).
+    // Pick the R in {1, 2, 4, 8} with the shortest time, if it gains 5 % and
+    // leaves every slice kMinSplitStars stars.
+    const double tiles = (double)tiles_of(r, pairs_per_thread);
+    const double sms = (double)(nsm > 0 ? nsm : 1);
+    auto cost = [&](int R) {
+        const double c = tiles * R;
+        return c <= sms ? 1.0 / R : std::ceil(c / (2.0 * sms)) * 2.0 / R;
+    };
+    int best = 1;
+    double bc = cost(1);
+    for (int R = 2; R <= 8; R *= 2) {
+        if (nstars / R < kMinSplitStars) break;
+        const double c = cost(R);
+        if (c < bc / 1.05) {
+            best = R;
+            bc = c;
+        }
+    }
+    return best;
 }
 
 int64_t tiles_of(const RayGrid &r, int pairs_per_thread)

@@ -4,12 +4,15 @@
 // of the learned-far-field kernel.  See shoot_fp32.cu for the design notes.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "mlens_dev.cuh"
 
 namespace mlens {
+
+namespace cg = cooperative_groups;
 
 constexpr int kThreads = 256;
 constexpr int kTileX = 64;                 // rays per tile row = threads per row group
@@ -78,9 +81,18 @@ __device__ __forceinline__ float2 rcp_nr2(float2 x)
 // stages, beta, binning, counters.  Every thread of the CTA must call it.
 // NRP of the NP ray pairs take their reciprocals from rcp_nr2 (FMA pipe), the
 // others from the MUFU unit.
-template <int NP, int SC, bool NAIVE, int NRP = 0>
-__device__ __forceinline__ void shoot_tile(const ShootArgs &a, int bx, int by, ShootSmem<SC> &sm, TileShared &ts)
+//
+// SPLIT > 1 (re-centred FP32 only): the CTA is rank r of a cluster of SPLIT CTAs
+// that share the tile; it sums the r-th of SPLIT consecutive 32-aligned slices
+// of the stars.  Ranks 1.. leave their (S, C) partials in `part` (2 NP float4
+// per thread, in their own shared memory); rank 0 reads them through
+// distributed shared memory in rank order, folds each in with two Kahan steps
+// (S_r, then -C_r) and alone goes on to beta and binning.
+template <int NP, int SC, bool NAIVE, int NRP = 0, int SPLIT = 1>
+__device__ __forceinline__ void shoot_tile(const ShootArgs &a, int bx, int by, ShootSmem<SC> &sm, TileShared &ts,
+                                           float4 *part = nullptr)
 {
+    static_assert(SPLIT == 1 || !NAIVE, "the split sum is for the re-centred kernel");
     constexpr int kTileY = tile_rows(NP);
     constexpr int kLoads = (SC + kThreads - 1) / kThreads;
     const int tid = threadIdx.x;
@@ -152,7 +164,14 @@ __device__ __forceinline__ void shoot_tile(const ShootArgs &a, int bx, int by, S
     }
 
     // ---------------------------------------------------------- star stages
-    const int64_t nst = a.nstars;  // multiple of kKahan
+    const float4 *stars = a.stars;
+    int64_t nst = a.nstars;  // multiple of kKahan
+    if (SPLIT > 1) {
+        const int64_t chunk = ((nst + SPLIT - 1) / SPLIT + kKahan - 1) / kKahan * kKahan;
+        const int64_t s0 = min(nst, (int64_t)cg::this_cluster().block_rank() * chunk);
+        stars += s0;
+        nst = min(chunk, nst - s0);
+    }
     const int nstage = (int)((nst + SC - 1) / SC);
     float4 nxt[kLoads];
     auto stage_load = [&](int s) {
@@ -160,7 +179,7 @@ __device__ __forceinline__ void shoot_tile(const ShootArgs &a, int bx, int by, S
 #pragma unroll
         for (int l = 0; l < kLoads; ++l) {
             const int k = tid + l * kThreads;
-            nxt[l] = (k < SC && base + k < nst) ? __ldg(&a.stars[base + k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            nxt[l] = (k < SC && base + k < nst) ? __ldg(&stars[base + k]) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     };
     auto stage_store = [&](int buf) {
@@ -218,6 +237,35 @@ __device__ __forceinline__ void shoot_tile(const ShootArgs &a, int bx, int by, S
         }
         if (s + 1 < nstage) stage_store(buf ^ 1);
         __syncthreads();
+    }
+
+    if constexpr (SPLIT > 1) {
+        cg::cluster_group cl = cg::this_cluster();
+        const unsigned rank = cl.block_rank();
+        if (rank != 0) {
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                part[(2 * p) * kThreads + tid] = make_float4(Sx[p].x, Sx[p].y, Sy[p].x, Sy[p].y);
+                part[(2 * p + 1) * kThreads + tid] = make_float4(Cx[p].x, Cx[p].y, Cy[p].x, Cy[p].y);
+            }
+        }
+        cl.sync();  // every rank's partials are in place
+        if (rank == 0) {
+#pragma unroll 1
+            for (int r = 1; r < SPLIT; ++r) {
+                const float4 *rp = cl.map_shared_rank(part, r);
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const float4 sr = rp[(2 * p) * kThreads + tid], cr = rp[(2 * p + 1) * kThreads + tid];
+                    kahan2(Sx[p], Cx[p], f2(sr.x, sr.y));
+                    kahan2(Sy[p], Cy[p], f2(sr.z, sr.w));
+                    kahan2(Sx[p], Cx[p], f2(-cr.x, -cr.y));
+                    kahan2(Sy[p], Cy[p], f2(-cr.z, -cr.w));
+                }
+            }
+        }
+        cl.sync();  // rank 0 has read them: the other ranks may exit
+        if (rank != 0) return;
     }
 
     // ------------------------------------------------ beta as float pairs

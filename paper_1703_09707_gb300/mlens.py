@@ -92,6 +92,8 @@ SIGNATURES = {
     "mlens_create": (C.c_int, [C.POINTER(_vp), _dp, _dp, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int32]),
     "mlens_set_precision": (C.c_int, [_vp, C.c_int32]),
     "mlens_set_tuning": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32]),
+    "mlens_set_star_split": (C.c_int, [_vp, C.c_int32]),
+    "mlens_star_split_for": (C.c_int, [_vp, _gp, C.POINTER(C.c_int32)]),
     "mlens_shoot": (C.c_int, [_vp, _gp, _gp, _vp, C.c_uint32, _sp, _vp]),
     "mlens_shoot_beta": (C.c_int, [_vp, _gp, _gp, _vp, _vp, C.c_uint32, _sp, _vp]),
     "mlens_trace": (C.c_int, [_vp, _dp, C.c_int64, _dp, _vp]),
@@ -234,6 +236,18 @@ def mlens_set_precision(ctx: Ctx, precision):
 
 def mlens_set_tuning(ctx: Ctx, rays_per_thread: int, star_stage: int = 0, fma_pairs: int = 0):
     _check(load().mlens_set_tuning(ctx.handle, int(rays_per_thread), int(star_stage), int(fma_pairs)))
+
+
+def mlens_set_star_split(ctx: Ctx, split: int):
+    """0 = automatic, 1 = never, 2/4/8 CTAs per tile."""
+    _check(load().mlens_set_star_split(ctx.handle, int(split)))
+
+
+def mlens_star_split_for(ctx: Ctx, rays) -> int:
+    out = C.c_int32(0)
+    g = grid(rays)
+    _check(load().mlens_star_split_for(ctx.handle, C.byref(g), C.byref(out)))
+    return int(out.value)
 
 
 def mlens_shoot(ctx: Ctx, rays, src, counts, flags: int = 0, stats: bool = False, stream=None):

@@ -9,16 +9,20 @@ import oracle
 from paper_1703_09707_gb300 import mlens as M
 
 
-def make_ctx(f, prec=M.MLENS_PREC_FP32):
-    return M.mlens_create(f.xy, f.m, f.kappa_c, f.gamma1, f.gamma2, prec)
+def make_ctx(f, prec=M.MLENS_PREC_FP32, split=None):
+    ctx = M.mlens_create(f.xy, f.m, f.kappa_c, f.gamma1, f.gamma2, prec)
+    if split is not None:
+        M.mlens_set_star_split(ctx, split)
+    return ctx
 
 
-def shoot_gpu(f, rays, src, prec=M.MLENS_PREC_FP32, want_beta=True, ctx=None, flags=0, counts=None):
+def shoot_gpu(f, rays, src, prec=M.MLENS_PREC_FP32, want_beta=True, ctx=None, flags=0, counts=None, split=None):
     """Returns (counts[ny,nx] uint32, stats, beta) with beta as (n,4) float32 pairs
-    {x_hi, y_hi, x_lo, y_lo} for the FP32 variants or (n,2) float64 for FP64."""
+    {x_hi, y_hi, x_lo, y_lo} for the FP32 variants or (n,2) float64 for FP64.
+    `split` (own context only): the star split, None = the library's default."""
     own = ctx is None
     if own:
-        ctx = make_ctx(f, prec)
+        ctx = make_ctx(f, prec, split=split)
     if counts is None:
         counts = torch.empty(src.ny * src.nx, dtype=torch.int32, device="cuda")
     beta = None

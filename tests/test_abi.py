@@ -66,6 +66,9 @@ def test_bad_arguments_are_rejected_before_any_device_call(lib):
     assert lib.mlens_shoot(None, C.byref(g), C.byref(g), C.c_void_p(16), 0, None, None) == M.MLENS_ERR_ARG
     assert "context" in M.mlens_last_error()
     assert lib.mlens_set_tuning(None, 8, 0, 0) == M.MLENS_ERR_ARG
+    assert lib.mlens_set_star_split(None, 2) == M.MLENS_ERR_ARG
+    out = C.c_int32(-7)
+    assert lib.mlens_star_split_for(None, C.byref(g), C.byref(out)) == M.MLENS_ERR_ARG and out.value == -7
     assert lib.mlens_set_precision(None, 0) == M.MLENS_ERR_ARG
     badg = M.mlens_grid(1.0, -1.0, -1.0, 1.0, 4, 4)
     assert lib.mlens_bin(C.c_void_p(16), 4, C.byref(badg), C.c_void_p(16), 0, None, None) == M.MLENS_ERR_ARG

@@ -18,7 +18,8 @@ def small_batch():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     wl = W.batched_config(nfields=12, nrays=384, nsrc=96, seed=W.SEED_BASE + 50)
-    ctxs = [make_ctx(f) for f in wl.fields]
+    # the persistent kernel never splits a tile's star sum: compare with unsplit shots
+    ctxs = [make_ctx(f, split=1) for f in wl.fields]
     counts = [torch.empty(s.n, dtype=torch.int32, device="cuda") for s in wl.srcs]
     yield wl, ctxs, counts
     for c in ctxs:

@@ -43,7 +43,8 @@ def host(c, src):
 
 
 def plain_map(f):
-    c, st, b4 = shoot_gpu(f, RAYS, SRC)
+    # fallback tiles run the unsplit tile function
+    c, st, b4 = shoot_gpu(f, RAYS, SRC, split=1)
     return c, st, b4
 
 

@@ -33,6 +33,7 @@ def test_noalloc_matches_mlens_shoot_on_two_calls_in_a_row():
     wl = W.config("paper", rays_scale=1 / 8)
     f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
     ctx = M.mlens_create(f.xy, f.m, f.kappa_c, f.gamma1, f.gamma2, M.MLENS_PREC_FP32)
+    M.mlens_set_star_split(ctx, 1)  # the no-alloc entry never splits the star sum
     ref = torch.empty(src.n, dtype=torch.int32, device="cuda")
     st_ref = M.mlens_shoot(ctx, rays, src, ref, stats=True)
     ctx.close()

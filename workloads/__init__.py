@@ -14,6 +14,8 @@ the five benchmark configurations:
   precision 1e5 stars, 16384^2 rays, 2048^2 map over [-10,10]^2
   learned   1e6 stars, 32768^2 rays, 4096^2 map over [-10,10]^2
   batched   256 fields with N in [1e2,1e4] log-uniform, 2048^2 rays, 512^2 maps
+  large_n   1e7 stars (the learned field's parameters), 512^2 rays, 256^2 map over
+            [-2,2]^2: few ray tiles for many stars (the split star sum's regime)
 
 Units follow Eq. (4): angles in Einstein radii of a 1 M_sun lens, masses in M_sun.
 With the deflection of Eq. (3), a uniform sheet of surface mass density rho (M_sun per
@@ -172,6 +174,13 @@ def config(name: str, rays_scale: float = 1.0, src_scale: float = 1.0) -> Worklo
         rays = Grid(-hx, hx, -hy, hy, p["nr"], p["nr"])
         src = Grid(-10.0, 10.0, -10.0, 10.0, p["ns"], p["ns"])
         wl = Workload(name, [f], [rays], [src], cells=256 if name == "learned" else None)
+    elif name == "large_n":
+        f = random_field(SEED_BASE + 6, 10_000_000, 0.45, 0.05, 0.25, 0.0)
+        hx, hy = lens_box(0.5, 0.25, 0.0, 2.0)
+        hx, hy = _round_box(hx), _round_box(hy)
+        rays = Grid(-hx, hx, -hy, hy, 512, 512)
+        src = Grid(-2.0, 2.0, -2.0, 2.0, 256, 256)
+        wl = Workload(name, [f], [rays], [src])
     elif name == "batched":
         wl = batched_config()
     else:
