@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--extras", default="batched,binning,split,learned",
                     help="comma list of extra sections: batched, binning, split, learned")
     ap.add_argument("--learned-tol", type=float, default=5e-6, help="per-cell validation bound of the learned field")
-    ap.add_argument("--learned-order", type=int, default=8)
+    ap.add_argument("--learned-order", type=int, default=10)
     return ap.parse_args()
 
 
@@ -366,7 +366,8 @@ def bench_learned(M, torch, steps: int, flush, tol: float, order: int):
     map of the whole grid takes minutes, so both paths are compared on a strip of
     768 ray rows (two cell rows, 2.5e13 interactions for the plain path): the strip
     gives the plain path's throughput and the map error of the learned path
-    (relative L1 of the strip maps).  Done with and without the network."""
+    (relative L1 of the strip maps).  Done with the network, without it at the same
+    exact order, and without it at order 16."""
     wl = W.config("learned")
     f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
     stream = torch.cuda.current_stream()
@@ -389,9 +390,12 @@ def bench_learned(M, torch, steps: int, flush, tol: float, order: int):
     out = {"workload": f"learned: {f.n} stars, {rays.nx}^2 rays, {src.nx}^2 map, 256 x 86 cells of 0.46875 theta_E",
            "plain": {"interactions_per_s": plain_rate, "map_s_estimated": plain_full_s,
                      "measured_on": f"rows [{j0},{j1}) of the grid ({strip.n} rays)"}}
-    for use_net in (1, 0):
+    # the learned path, the same series without the network (the ablation), and the
+    # exact series at order 16 without a network (the strongest non-learned variant)
+    variants = (("with_network", 1, order), ("series_only", 0, order), ("series_only_order16", 0, 16))
+    for key, use_net, o in variants:
         t0 = time.perf_counter()
-        rep = M.mlens_fit_far_field(ctx, rays, M.fit_params(cells_x=256, order=order, use_network=use_net,
+        rep = M.mlens_fit_far_field(ctx, rays, M.fit_params(cells_x=256, order=o, use_network=use_net,
                                                             tolerance=tol))
         fit_s = time.perf_counter() - t0
         cl = torch.empty(src.n, dtype=torch.int32, device="cuda")
@@ -402,9 +406,10 @@ def bench_learned(M, torch, steps: int, flush, tol: float, order: int):
         b.synchronize()
         strip_s = a.elapsed_time(b) / 1e3
         cl_h = cl.cpu().numpy().view(np.uint32).astype(np.int64)
-        if use_net:
-            # the whole map, timed (a few seconds); the series-only ablation spends most of
-            # its time in fallback tiles (minutes per map), so it is timed on the strip only
+        # whole map timed unless its fallback tiles alone would take minutes (then the
+        # strip's time is scaled to the grid)
+        fallback_s = rep["tiles_fallback"] * 2048 * f.n / plain_rate
+        if fallback_s <= 5.0:
             counts = torch.empty(src.n, dtype=torch.int32, device="cuda")
             M.mlens_shoot_learned(ctx, rays, src, counts)  # warm-up
             ms = []
@@ -422,7 +427,6 @@ def bench_learned(M, torch, steps: int, flush, tol: float, order: int):
             learned_s = strip_s * rays.n / strip.n
             timing = f"estimated from the strip ({strip_s:.3f} s for rows [{j0},{j1}))"
         l1 = float(np.abs(cl_h - cp_h).sum() / max(cp_h.sum(), 1))
-        key = "with_network" if use_net else "series_only"
         out[key] = {
             "map_s": learned_s, "map_s_timing": timing, "maps_per_s": 1.0 / learned_s,
             "effective_interactions_per_s": rays.n * f.n / learned_s,
@@ -434,8 +438,9 @@ def bench_learned(M, torch, steps: int, flush, tol: float, order: int):
             "val_max_err": rep["val_max_err_net"] if use_net else rep["val_max_err_series"],
             "fit_s": fit_s, "fit_seconds": {"coefficients": rep["seconds_coefficients"],
                                             "train": rep["seconds_train"], "validate": rep["seconds_validate"]},
-            "train_steps": rep["train_steps"], "order": order, "tolerance": tol,
+            "train_steps": rep["train_steps"], "order": o, "tolerance": tol,
         }
+    out["network_gain_at_equal_order"] = out["series_only"]["map_s"] / out["with_network"]["map_s"]
     ctx.close()
     return out
 

@@ -318,7 +318,7 @@ int mlens_shoot_batch(mlens_ctx *const *ctxs, int32_t nfields, const mlens_grid 
  */
 typedef struct {
     int32_t cells_x;              /* cells across the ray box in x; rays.nx must be a multiple of 64*cells_x */
-    int32_t order;                /* series order evaluated exactly, 0..16 (default 8) */
+    int32_t order;                /* series order evaluated exactly, 0..16 (default 10) */
     int32_t target_order;         /* order of the far-field expansion the network learns up to, order < . <= 24 (24) */
     int32_t use_network;          /* 1: learn the remainder (default); 0: series only */
     int64_t train_samples;        /* distinct training samples (2^24) */

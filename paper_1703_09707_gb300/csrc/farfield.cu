@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
             const float ux = j < 2 ? uxA : uxB, uy = j < 2 ? uyA : uyB;
             h1[nb][j] = h1[nb][j] + sf[L::fW1u + 2 * col] * ux + sf[L::fW1u + 2 * col + 1] * uy + sf[L::fb1 + col];
             const int row = g + (j < 2 ? 0 : 8);
-            const __nv_bfloat16 v = to_bf16(silu(h1[nb][j]));
+            const __nv_bfloat16 v = to_bf16(silu1(h1[nb][j]));
             sA1[row * kLdH + col] = v;
             sb[L::A1T + col * kLdT + warp * kSampW + row] = v;
         }
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
         for (int j = 0; j < 4; ++j) {
             const int col = nb * 8 + 2 * t + (j & 1);
             h2[nb][j] += sf[L::fb2 + col];
-            const float a2 = silu(h2[nb][j]);
+            const float a2 = silu2(h2[nb][j]);
             yp[j >> 1][0] += sf[L::fW3 + col] * a2;
             yp[j >> 1][1] += sf[L::fW3 + kHid + col] * a2;
         }
@@ -518,8 +518,8 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int col = nb * 8 + 2 * t + h;
-            float w0 = dy[0][0] * silu(h2[nb][h]) + dy[1][0] * silu(h2[nb][2 + h]);
-            float w1 = dy[0][1] * silu(h2[nb][h]) + dy[1][1] * silu(h2[nb][2 + h]);
+            float w0 = dy[0][0] * silu2(h2[nb][h]) + dy[1][0] * silu2(h2[nb][2 + h]);
+            float w1 = dy[0][1] * silu2(h2[nb][h]) + dy[1][1] * silu2(h2[nb][2 + h]);
             for (int o = 4; o < 32; o <<= 1) {
                 w0 += __shfl_xor_sync(0xffffffffu, w0, o);
                 w1 += __shfl_xor_sync(0xffffffffu, w1, o);
@@ -551,7 +551,7 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 const float da2 = dy[r][0] * sf[L::fW3 + col] + dy[r][1] * sf[L::fW3 + kHid + col];
-                const float d = da2 * dsilu(h2[nb][2 * r + h]);
+                const float d = da2 * dsilu2(h2[nb][2 * r + h]);
                 colsum += d;
                 const __nv_bfloat16 v = to_bf16(d);
                 sDH2[rows[r] * kLdH + col] = v;
@@ -585,7 +585,7 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
             float colsum = 0.0f, gu0 = 0.0f, gu1 = 0.0f;
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
-                const float d = d1[nb][2 * r + h] * dsilu(h1[nb][2 * r + h]);
+                const float d = d1[nb][2 * r + h] * dsilu1(h1[nb][2 * r + h]);
                 colsum += d;
                 gu0 += d * wu[2 * rows[r]];
                 gu1 += d * wu[2 * rows[r] + 1];
@@ -897,7 +897,7 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
                     const int col = kb * 16 + 2 * t + (e & 1) + ((e >> 2) ? 8 : 0);
                     const bool rowB = (e >> 1) & 1;
                     const float ux = rowB ? uxB : uxA, uy = rowB ? uyB : uyA;
-                    v[e] = silu(ls.ec[col] + ls.w1u[2 * col] * ux + ls.w1u[2 * col + 1] * uy);
+                    v[e] = silu1(ls.ec[col] + ls.w1u[2 * col] * ux + ls.w1u[2 * col + 1] * uy);
                 }
                 af[kb][0] = pack_bf16(v[0], v[1]);  // row A, cols c, c+1
                 af[kb][1] = pack_bf16(v[2], v[3]);  // row B
@@ -917,7 +917,7 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int col = nb * 8 + 2 * t + (j & 1);
-                    const float a2 = silu(c[j] + ls.b2[col]);
+                    const float a2 = silu2(c[j] + ls.b2[col]);
                     if (j < 2) {
                         yA0 += ls.w3[col] * a2;
                         yA1 += ls.w3[kHid + col] * a2;

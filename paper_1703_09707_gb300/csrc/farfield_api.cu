@@ -258,7 +258,7 @@ void default_params(mlens_fit_params *p)
 {
     memset(p, 0, sizeof(*p));
     p->cells_x = 256;
-    p->order = 8;
+    p->order = 10;
     p->target_order = 24;
     p->use_network = 1;
     p->train_samples = int64_t(1) << 24;

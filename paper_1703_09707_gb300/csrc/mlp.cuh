@@ -3,7 +3,7 @@
 //
 // Network: a per-cell latent z (32) and one shared MLP 34 -> 64 -> 64 -> 2,
 //   h1 = W1z z + W1u u + b1, a1 = silu(h1); h2 = W2 a1 + b2, a2 = silu(h2);
-//   y = W3 a2 + b3,  silu(v) = v (1 + tanh(v/2)) / 2.
+//   y = W3 a2 + b3,  silu(v) = v (1 + tanh(v/2)) / 2 (tanh from the hardware unit).
 // The latent block of layer 1 and layer 2 run on the tensor cores with BF16
 // operands (z, W1z, a1, W2; dh2, dh1 in the backward pass); the position block
 // of layer 1 (W1u u, 2 inputs) and layer 3 stay in FP32.
@@ -29,11 +29,32 @@ constexpr int oW3 = ob2 + kHid;              // [2][64]
 constexpr int ob3 = oW3 + kOut * kHid;       // [2]
 constexpr int kParams = ob3 + kOut;          // 6530
 
-__device__ __forceinline__ float sigm(float v) { return 0.5f * (1.0f + tanhf(0.5f * v)); }
-__device__ __forceinline__ float silu(float v) { return v * sigm(v); }
-__device__ __forceinline__ float dsilu(float v)
+// sigma(v) = (1 + tanh(v/2)) / 2 from the hardware tanh (MUFU.TANH, one
+// special-function op; maximum relative error about 2^-11, below the 2^-8
+// resolution of the BF16 operands the activations feed).  The accurate tanhf
+// costs about 20 instructions and, at 128 activations per ray, dominated the
+// learned kernel.  Training and inference use the same function.
+__device__ __forceinline__ float tanh_hw(float x)
 {
-    const float s = sigm(v);
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// layer 2 may keep the accurate tanhf (its outputs feed the FP32 layer 3)
+constexpr bool kLayer2Hw = true;
+__device__ __forceinline__ float sigm_hw(float v) { return __fmaf_rn(0.5f, tanh_hw(0.5f * v), 0.5f); }
+__device__ __forceinline__ float sigm_acc(float v) { return 0.5f * (1.0f + tanhf(0.5f * v)); }
+__device__ __forceinline__ float sigm2(float v) { return kLayer2Hw ? sigm_hw(v) : sigm_acc(v); }
+__device__ __forceinline__ float silu1(float v) { return v * sigm_hw(v); }
+__device__ __forceinline__ float silu2(float v) { return v * sigm2(v); }
+__device__ __forceinline__ float dsilu1(float v)
+{
+    const float s = sigm_hw(v);
+    return s * (1.0f + v * (1.0f - s));
+}
+__device__ __forceinline__ float dsilu2(float v)
+{
+    const float s = sigm2(v);
     return s * (1.0f + v * (1.0f - s));
 }
 

@@ -103,8 +103,11 @@ def _unflat_grad(g):
 def test_network_forward_and_backward_match_the_oracle(B):
     """The GPU training kernel (BF16 tensor cores, FP32 accumulation) on explicit
     inputs against the FP64 reference with the same BF16 rounding points.  Bound:
-    2e-3 relative (Frobenius) per gradient block, from one BF16 half-ulp (2^-9)
-    of a rounded operand flipping where FP32 and FP64 pre-rounding values differ."""
+    2e-3 relative (Frobenius) per gradient block and for the outputs, from one BF16
+    half-ulp (2^-9) of a rounded operand flipping where the GPU's and the FP64
+    pre-rounding values differ (FP32 arithmetic, and the hardware tanh of the
+    activations, relative error <= 2^-11); no output may be off by more than 1e-3
+    of the largest output."""
     rng = np.random.default_rng(10 + B)
     p = mlp.init_params(rng)
     for k in p:
@@ -122,8 +125,10 @@ def test_network_forward_and_backward_match_the_oracle(B):
     loss = M.mlens_ff_eval(dev(flat), dev(z), dev(u), dev(t), y=y, grads=g, dz=dz)
     lref, gref, yref = mlp.loss_and_grads(p32, z.astype(np.float64), u.astype(np.float64), t.astype(np.float64),
                                           bf16=True)
-    assert np.allclose(y.cpu().numpy(), yref, rtol=1e-4, atol=1e-5)
-    assert abs(loss - lref) <= 1e-4 * abs(lref)
+    yg = y.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(yg - yref) <= 2e-3 * np.linalg.norm(yref)
+    assert np.max(np.abs(yg - yref)) <= 1e-3 * np.max(np.abs(yref))
+    assert abs(loss - lref) <= 2e-3 * abs(lref)
     gg = _unflat_grad(g.cpu().numpy().astype(np.float64))
     for k in gref:
         if k == "z":
