@@ -56,3 +56,49 @@ def test_pins_catch_planted_mistake(name, orig, mut):
         with oracle.using(so):
             failed = _run_pins()
     assert failed, f"no pin caught mutation {name}"
+
+
+# ------------------------------------------- convolution / light-curve oracle (Python)
+import importlib.util  # noqa: E402
+import inspect  # noqa: E402
+
+import test_oracle_lightcurve as PL  # noqa: E402
+from oracle import lightcurve as _LC  # noqa: E402
+
+LC_MUTATIONS = [
+    ("gauss_unnormalised", "return w / w.sum()", "return w"),
+    ("gauss_axes_swapped", "wx, wy = gaussian_weights(size, dx), gaussian_weights(size, dy)",
+     "wx, wy = gaussian_weights(size, dy), gaussian_weights(size, dx)"),
+    ("gauss_3_sigma", "k = int(math.ceil(4.0 * sigma / d))", "k = int(math.ceil(3.0 * sigma / d))"),
+    ("disk_strict_edge", "<= radius * radius:", "< radius * radius:"),
+    ("disk_drops_scale", "f = scale / len(offs)", "f = 1.0 / len(offs)"),
+    ("shift_sign", "s[j0:j1, i0:i1] = c[j0 + dj:j1 + dj, i0 + di:i1 + di]",
+     "s[j0:j1, i0:i1] = c[j0 - dj:j1 - dj, i0 - di:i1 - di]"),
+    ("mu_scale_drops_dy", "return a_lens / (rays.nx * rays.ny * dx * dy)", "return a_lens / (rays.nx * rays.ny * dx * dx)"),
+    ("curve_not_centred", "u = (bx - src.x0) / dx - 0.5", "u = (bx - src.x0) / dx"),
+    ("curve_fx_fy_swapped", "out[k] = ((1 - fy) * ((1 - fx)", "out[k] = ((1 - fx) * ((1 - fy)"),
+]
+
+
+def _lc_mutant(name, orig, mut):
+    src = inspect.getsource(_LC)
+    assert orig in src, f"mutation anchor for {name} not found"
+    spec = importlib.util.spec_from_loader(f"lc_mut_{name}", loader=None)
+    mod = importlib.util.module_from_spec(spec)
+    exec(compile(src.replace(orig, mut, 1), f"lc_mut_{name}", "exec"), mod.__dict__)
+    return mod
+
+
+@pytest.mark.parametrize("name,orig,mut", LC_MUTATIONS, ids=[m[0] for m in LC_MUTATIONS])
+def test_light_curve_pins_catch_planted_mistake(name, orig, mut, monkeypatch):
+    monkeypatch.setattr(PL, "LC", _lc_mutant(name, orig, mut))
+    failed = []
+    for t in [getattr(PL, n) for n in dir(PL) if n.startswith("test_")]:
+        params = inspect.signature(t).parameters
+        cases = [(PL.LC.GAUSSIAN, 0.3), (PL.LC.DISK, 0.45)] if params else [()]
+        for args in cases:
+            try:
+                t(*args)
+            except Exception as e:  # an assertion or a crash
+                failed.append(f"{t.__name__}:{type(e).__name__}")
+    assert failed, f"no pin caught mutation {name}"
