@@ -66,8 +66,8 @@ def parse():
     ap.add_argument("--print-kernel-hash", action="store_true", help="print the FP32 kernel source hash and exit")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-fields and learned-far-field measurements that ride along the main line")
-    ap.add_argument("--extras", default="batched,binning,split,learned",
-                    help="comma list of extra sections: batched, binning, split, learned")
+    ap.add_argument("--extras", default="batched,binning,lightcurve,split,learned",
+                    help="comma list of extra sections: batched, binning, lightcurve, split, learned")
     ap.add_argument("--learned-tol", type=float, default=5e-6, help="per-cell validation bound of the learned field")
     ap.add_argument("--learned-order", type=int, default=10)
     return ap.parse_args()
@@ -321,6 +321,55 @@ def bench_binning(M, torch, steps: int, warmup: int, flush):
     empty.close()
     out["fused_epilogue"] = {"ms": ms, "rays_per_s": rays.n / (ms / 1e3),
                              "note": "mlens_shoot over a field without stars: everything but the direct sum"}
+    return out
+
+
+# ------------------------------------------------------------ light curves
+def bench_lightcurve(M, torch, steps: int, warmup: int, flush):
+    """The paper field's 8192^2 rays binned into a 4096^2 map (the learned workload's
+    map size) and convolved with a Gaussian source (sigma = 0.05 theta_E, 10 pixels)
+    and a uniform disk (R = 0.1 theta_E, 20 pixels), then a 4096-point light curve
+    across it; CUDA events, L2 flushed before each timed call."""
+    wl = W.config("paper")
+    f, rays = wl.fields[0], wl.rays[0]
+    src = W.Grid(-10.0, 10.0, -10.0, 10.0, 4096, 4096)
+    stream = torch.cuda.current_stream()
+    ctx = M.mlens_create(f.xy, f.m, f.kappa_c, f.gamma1, f.gamma2, M.MLENS_PREC_FP32)
+    counts = torch.empty(src.n, dtype=torch.int32, device="cuda")
+    M.mlens_shoot(ctx, rays, src, counts)
+    ctx.close()
+    scale = M.mlens_magnification_scale(rays, src)
+    conv = torch.empty(src.n, dtype=torch.float32, device="cuda")
+    curve = torch.empty(4096, dtype=torch.float32, device="cuda")
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        ms = []
+        for i in range(steps):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.mean(ms)
+
+    peak, basis = measured_hbm_gbs()
+    out = {"workload": f"paper field, {rays.nx}^2 rays into a {src.nx}^2 map over [-10,10]^2",
+           "hbm_peak_gbs": peak, "hbm_peak_basis": basis}
+    for key, prof, size in (("gaussian_sigma_0.05", M.MLENS_PROFILE_GAUSSIAN, 0.05),
+                            ("disk_r_0.1", M.MLENS_PROFILE_DISK, 0.1)):
+        work = torch.empty(M.mlens_convolve_workspace(src, prof, size), dtype=torch.uint8, device="cuda")
+        ms = timed(lambda: M.mlens_convolve(counts, src, prof, size, conv, scale=scale, work=work))
+        # bytes a single pass would move: the uint32 map in, the float32 map out
+        gbs = 8.0 * src.n / (ms / 1e3) / 1e9
+        out[key] = {"ms": ms, "pixels_per_s": src.n / (ms / 1e3), "min_bytes_gbs": gbs, "hbm_frac": gbs / peak,
+                    "note": "asynchronous call with a caller workspace: setup kernel and passes"}
+        del work
+    ms = timed(lambda: M.mlens_light_curve(conv, src, (-8.0, -3.0), (8.0, 4.0), 4096, curve))
+    out["light_curve_4096_points_ms"] = ms
     return out
 
 
@@ -620,6 +669,8 @@ def run_mine(args):
             bn = bench_binning(M, torch, max(3, min(args.steps, 10)), 3, flush)
             bn["fused_epilogue"]["share_of_paper_step"] = bn["fused_epilogue"]["ms"] / kernel_ms
             line["binning"] = bn
+        if "lightcurve" in extras:
+            line["lightcurve"] = bench_lightcurve(M, torch, max(3, min(args.steps, 10)), 2, flush)
         if "split" in extras:
             line["split"] = bench_split(M, torch, flush, peak)
         if "learned" in extras:

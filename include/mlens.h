@@ -206,6 +206,79 @@ int mlens_bin(const void *beta_dev, int64_t n, const mlens_grid *src, uint32_t *
 int mlens_bin_grid(const void *beta_dev, const mlens_grid *rays, const mlens_grid *src, uint32_t *counts_dev,
                    uint32_t flags, mlens_stats *stats_host, void *stream);
 
+/* Source intensity profiles of mlens_convolve. */
+#define MLENS_PROFILE_GAUSSIAN 0
+#define MLENS_PROFILE_DISK 1
+
+/*
+ * mlens_convolve -- the map convolved with a background source's intensity
+ * profile.  Section 1: given a model of the source's size and intensity
+ * profile, the magnification pattern yields simulated light curves; the
+ * convolved map is the source's total magnification at each source position.
+ *   out[j][i] = scale * sum_{(di,dj) in K} w(di,dj) * counts[j+dj][i+di]
+ * with counts = 0 outside the map and the weights normalised to sum 1 over
+ * their support K.  Offsets are measured in theta_E with the map's pixel widths
+ * dx = (x1-x0)/nx, dy = (y1-y0)/ny (pixels need not be square).
+ *   profile MLENS_PROFILE_GAUSSIAN: w proportional to exp(-|d|^2 / (2 size^2)),
+ *              |di| <= ceil(4 size/dx), |dj| <= ceil(4 size/dy); the normalised
+ *              1-D weights multiply.  FP32 arithmetic (two separable passes);
+ *              needs 0 < size and 4 size <= 256 pixels along both axes.
+ *   profile MLENS_PROFILE_DISK: a uniform disk of radius size (>= 0; 0 = the
+ *              map itself): K = {(di dx)^2 + (dj dy)^2 <= size^2}, w = 1/|K|.
+ *              Sums are exact integers; out = (float)(sum * (scale / |K|)) in
+ *              FP64.  At most 4096 pixel rows in the support.
+ *   counts_dev src->ny x src->nx uint32 counts (as mlens_shoot writes), device,
+ *              4-byte aligned; pixel values above 2^24 lose precision in the
+ *              Gaussian's FP32 passes.
+ *   scale      multiplies the result: 1 = weighted counts; the value of
+ *              mlens_magnification_scale turns counts into magnification.
+ *   out_dev    src->ny x src->nx float32, device, 4-byte aligned, not
+ *              overlapping counts_dev.
+ *   work_dev   NULL, or caller-owned device workspace of at least
+ *              mlens_convolve_workspace bytes (work_bytes), 256-byte aligned,
+ *              overlapping neither map.  With a workspace the call allocates
+ *              nothing and is asynchronous on `stream` (it can be captured in a
+ *              CUDA graph); with NULL the library allocates the workspace (4
+ *              bytes per pixel for the Gaussian, 8 for the disk), frees it
+ *              before returning, and so synchronises `stream`.
+ * The weights / half-widths are computed on the device from the definition
+ * above (FP64, no contraction).  Errors: MLENS_ERR_ARG, MLENS_ERR_NOMEM,
+ * MLENS_ERR_CUDA.
+ */
+int mlens_convolve(const uint32_t *counts_dev, const mlens_grid *src, int32_t profile, double size, double scale,
+                   float *out_dev, void *work_dev, uint64_t work_bytes, void *stream);
+
+/*
+ * mlens_convolve_workspace -- bytes of device workspace mlens_convolve needs for
+ * this map, profile and size (the normalised weights or the support's row
+ * half-widths, and one map-sized buffer).  Host arithmetic only.
+ * Errors: MLENS_ERR_ARG (as mlens_convolve's checks of src, profile and size).
+ */
+int mlens_convolve_workspace(const mlens_grid *src, int32_t profile, double size, uint64_t *bytes_out);
+
+/*
+ * mlens_light_curve -- a (convolved) map sampled along a straight source track:
+ * npts points evenly spaced from (bx0, by0) to (bx1, by1) in theta_E (the
+ * first point when npts = 1), each the bilinear interpolation between the
+ * pixel centres (x0 + (i + 1/2) dx, y0 + (j + 1/2) dy) around it, constant
+ * beyond the outermost centres.  FP64 arithmetic, float32 output; asynchronous
+ * on `stream`.
+ *   map_dev    src->ny x src->nx float32 (e.g. mlens_convolve's output), device.
+ *   out_dev    npts float32, device.
+ * Errors: MLENS_ERR_ARG (npts < 1, non-finite end points, bad map grid),
+ * MLENS_ERR_CUDA.
+ */
+int mlens_light_curve(const float *map_dev, const mlens_grid *src, double bx0, double by0, double bx1, double by1,
+                      int32_t npts, float *out_dev, void *stream);
+
+/*
+ * mlens_magnification_scale -- A_lens / (N_rays * A_pix) for a ray grid and a
+ * source map: a pixel receiving its mean share of rays (magnification 1) holds
+ * N_rays * A_pix / A_lens of them, so magnification = counts * scale.
+ * Host arithmetic only.  Errors: MLENS_ERR_ARG.
+ */
+int mlens_magnification_scale(const mlens_grid *rays, const mlens_grid *src, double *scale_out);
+
 /*
  * mlens_shoot_noalloc -- mlens_shoot for callers that must not allocate device
  * memory: code that runs while a CUDA stream is being captured into a graph

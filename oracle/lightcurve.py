@@ -97,6 +97,38 @@ def convolve(counts: np.ndarray, src, profile: int, size: float, scale: float = 
     raise ValueError("unknown profile")
 
 
+def convolve_at(counts: np.ndarray, src, profile: int, size: float, scale: float, js, is_) -> np.ndarray:
+    """The same sum evaluated only at pixels (js[k], is_[k]) -- for maps too large to
+    convolve whole on the host."""
+    c = np.asarray(counts)
+    ny, nx = c.shape
+    dx, dy = _pix(src)
+    out = np.empty(len(js))
+    if profile == GAUSSIAN:
+        wx, wy = gaussian_weights(size, dx), gaussian_weights(size, dy)
+        kx, ky = len(wx) // 2, len(wy) // 2
+        for k, (j, i) in enumerate(zip(js, is_)):
+            acc = 0.0
+            for dj in range(-ky, ky + 1):
+                if 0 <= j + dj < ny:
+                    for di in range(-kx, kx + 1):
+                        if 0 <= i + di < nx:
+                            acc += (wx[di + kx] * wy[dj + ky]) * float(c[j + dj, i + di])
+            out[k] = scale * acc
+        return out
+    if profile == DISK:
+        offs = disk_offsets(size, dx, dy)
+        f = scale / len(offs)
+        for k, (j, i) in enumerate(zip(js, is_)):
+            tot = 0
+            for di, dj in offs:
+                if 0 <= j + dj < ny and 0 <= i + di < nx:
+                    tot += int(c[j + dj, i + di])
+            out[k] = float(tot) * f
+        return out
+    raise ValueError("unknown profile")
+
+
 def light_curve(mp: np.ndarray, src, b0, b1, npts: int) -> np.ndarray:
     """Bilinear samples of map mp[ny, nx] at npts points from b0 to b1 (theta_E)."""
     m = np.asarray(mp, dtype=np.float64)

@@ -31,6 +31,9 @@ MLENS_PREC_FP64 = 2
 
 MLENS_ACCUMULATE = 1
 
+MLENS_PROFILE_GAUSSIAN = 0
+MLENS_PROFILE_DISK = 1
+
 PRECISIONS = {"fp32": MLENS_PREC_FP32, "fp32_naive": MLENS_PREC_FP32_NAIVE, "fp64": MLENS_PREC_FP64}
 
 
@@ -99,6 +102,10 @@ SIGNATURES = {
     "mlens_trace": (C.c_int, [_vp, _dp, C.c_int64, _dp, _vp]),
     "mlens_bin": (C.c_int, [_vp, C.c_int64, _gp, _vp, C.c_uint32, _sp, _vp]),
     "mlens_bin_grid": (C.c_int, [_vp, _gp, _gp, _vp, C.c_uint32, _sp, _vp]),
+    "mlens_convolve": (C.c_int, [_vp, _gp, C.c_int32, C.c_double, C.c_double, _vp, _vp, C.c_uint64, _vp]),
+    "mlens_convolve_workspace": (C.c_int, [_gp, C.c_int32, C.c_double, C.POINTER(C.c_uint64)]),
+    "mlens_light_curve": (C.c_int, [_vp, _gp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32, _vp, _vp]),
+    "mlens_magnification_scale": (C.c_int, [_gp, _gp, _dp]),
     "mlens_shoot_noalloc": (C.c_int, [_vp, C.c_int64, C.c_double, C.c_double, C.c_double, _gp, _gp, _vp, C.c_uint32,
                                       _sp, _vp]),
     "mlens_batch_create": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int32, _gp, _gp, C.POINTER(_vp),
@@ -289,6 +296,36 @@ def mlens_bin_grid(beta, rays, src, counts, flags: int = 0, stats: bool = False,
     _check(load().mlens_bin_grid(_dev_ptr(beta), C.byref(g), C.byref(s), _dev_ptr(counts), int(flags),
                                  C.byref(st) if stats else None, _stream_ptr(stream)))
     return st.asdict() if stats else None
+
+
+def mlens_convolve_workspace(src, profile: int, size: float) -> int:
+    s = grid(src)
+    out = C.c_uint64(0)
+    _check(load().mlens_convolve_workspace(C.byref(s), int(profile), float(size), C.byref(out)))
+    return int(out.value)
+
+
+def mlens_convolve(counts, src, profile: int, size: float, out, scale: float = 1.0, work=None, stream=None):
+    """counts: CUDA int32/uint32 tensor of src.ny*src.nx; out: CUDA float32 tensor of the
+    same size; work: optional CUDA byte tensor of mlens_convolve_workspace bytes (the
+    call is then asynchronous)."""
+    s = grid(src)
+    nb = 0 if work is None else int(work.numel() * work.element_size())
+    _check(load().mlens_convolve(_dev_ptr(counts), C.byref(s), int(profile), float(size), float(scale),
+                                 _dev_ptr(out), _dev_ptr(work), nb, _stream_ptr(stream)))
+
+
+def mlens_light_curve(map_, src, b0, b1, npts: int, out, stream=None):
+    s = grid(src)
+    _check(load().mlens_light_curve(_dev_ptr(map_), C.byref(s), float(b0[0]), float(b0[1]), float(b1[0]),
+                                    float(b1[1]), int(npts), _dev_ptr(out), _stream_ptr(stream)))
+
+
+def mlens_magnification_scale(rays, src) -> float:
+    g, s = grid(rays), grid(src)
+    out = C.c_double(0.0)
+    _check(load().mlens_magnification_scale(C.byref(g), C.byref(s), C.byref(out)))
+    return float(out.value)
 
 
 def mlens_shoot_noalloc(stars, n: int, kappa_c: float, gamma1: float, gamma2: float, rays, src, counts,

@@ -83,6 +83,38 @@ def test_bad_arguments_are_rejected_before_any_device_call(lib):
     assert lib.mlens_bin_grid(C.c_void_p(24), C.byref(g), C.byref(g), C.c_void_p(16), 0, None,
                               None) == M.MLENS_ERR_ARG
     assert lib.mlens_bin_grid(None, C.byref(g), C.byref(g), C.c_void_p(16), 0, None, None) == M.MLENS_ERR_ARG
+    # convolution and light curves: argument checks come before any device call
+    assert lib.mlens_convolve(C.c_void_p(16), C.byref(badg), 1, 0.1, 1.0, C.c_void_p(1 << 20), None, 0, None) == M.MLENS_ERR_ARG
+    assert lib.mlens_convolve(None, C.byref(g), 1, 0.1, 1.0, C.c_void_p(1 << 20), None, 0, None) == M.MLENS_ERR_ARG
+    assert lib.mlens_convolve(C.c_void_p(16), C.byref(g), 1, -0.1, 1.0, C.c_void_p(1 << 20), None, 0, None) == M.MLENS_ERR_ARG
+    assert lib.mlens_convolve(C.c_void_p(16), C.byref(g), 1, 0.1, float("inf"), C.c_void_p(1 << 20),
+                              None, 0, None) == M.MLENS_ERR_ARG
+    assert lib.mlens_convolve(C.c_void_p(16), C.byref(g), 1, 0.1, 1.0, C.c_void_p(32), None, 0, None) == M.MLENS_ERR_ARG
+    assert "overlap" in M.mlens_last_error()
+    # a workspace that is too small or misaligned is refused before any device call
+    assert lib.mlens_convolve(C.c_void_p(16), C.byref(g), 1, 0.1, 1.0, C.c_void_p(1 << 20), C.c_void_p(1 << 24), 16,
+                              None) == M.MLENS_ERR_ARG
+    assert lib.mlens_convolve(C.c_void_p(16), C.byref(g), 1, 0.1, 1.0, C.c_void_p(1 << 20), C.c_void_p((1 << 24) + 8),
+                              1 << 20, None) == M.MLENS_ERR_ARG
+    wb = C.c_uint64(0)
+    mapg = M.mlens_grid(-2.0, 2.0, -1.0, 1.0, 100, 40)  # 0.04 x 0.05 pixels
+    assert lib.mlens_convolve_workspace(C.byref(mapg), 0, 0.1, C.byref(wb)) == M.MLENS_OK
+    kx, ky = 10, 8  # ceil(0.4 / 0.04), ceil(0.4 / 0.05)
+    r256 = lambda b: (b + 255) // 256 * 256  # noqa: E731
+    assert wb.value == r256(4 * (2 * kx + 1 + 2 * ky + 1)) + r256(4 * 4000)
+    assert lib.mlens_convolve_workspace(C.byref(mapg), 1, 0.1, C.byref(wb)) == M.MLENS_OK
+    assert wb.value == r256(4 * (2 * 2 + 1)) + r256(8 * 4000)  # support rows |dj| <= 2
+    assert lib.mlens_convolve_workspace(C.byref(mapg), 0, 0.0, C.byref(wb)) == M.MLENS_ERR_ARG
+    assert lib.mlens_light_curve(C.c_void_p(16), C.byref(g), 0.0, 0.0, 1.0, 1.0, 0, C.c_void_p(16),
+                                 None) == M.MLENS_ERR_ARG
+    assert lib.mlens_light_curve(C.c_void_p(16), C.byref(g), 0.0, float("nan"), 1.0, 1.0, 5, C.c_void_p(16),
+                                 None) == M.MLENS_ERR_ARG
+    sc = C.c_double(0.0)
+    rays = M.mlens_grid(-10.0, 10.0, -10.0, 10.0, 1000, 1000)
+    srcg = M.mlens_grid(-5.0, 5.0, -4.0, 4.0, 100, 40)
+    assert lib.mlens_magnification_scale(C.byref(rays), C.byref(srcg), C.byref(sc)) == M.MLENS_OK
+    assert abs(sc.value - 0.02) < 1e-16
+    assert lib.mlens_magnification_scale(C.byref(badg), C.byref(srcg), C.byref(sc)) == M.MLENS_ERR_ARG
     lib.mlens_destroy(None)  # must be a no-op
 
 

@@ -116,3 +116,13 @@ def test_light_curve_is_exact_on_affine_maps_and_hits_pixel_centres():
     c = LC.light_curve(m, src, (-2.0 + 0.05 * 7, -1.0 + 0.2 * 3.5), (10.0, -1.0 + 0.2 * 3.5), 2)
     assert c[0] == pytest.approx(m[3, 3]) and c[1] == pytest.approx(m[3, 39])
     assert LC.light_curve(m, src, (5.0, 5.0), (5.0, 5.0), 1)[0] == m[19, 39]
+
+
+@pytest.mark.parametrize("profile,size", [(LC.GAUSSIAN, 0.12), (LC.DISK, 0.2)])
+def test_pointwise_form_equals_the_whole_map_form(profile, size):
+    rng = np.random.default_rng(8)
+    src = W.Grid(-1.0, 1.0, -0.6, 0.6, 37, 29)
+    c = _rand_counts(rng, src.ny, src.nx)
+    full = LC.convolve(c, src, profile, size, 0.7)
+    js, is_ = rng.integers(0, src.ny, 60), rng.integers(0, src.nx, 60)
+    assert np.allclose(LC.convolve_at(c, src, profile, size, 0.7, js, is_), full[js, is_], rtol=1e-13, atol=0)
