@@ -439,9 +439,13 @@ int mlens_fit_far_field(mlens_ctx *ctx, const mlens_grid *rays, const mlens_fit_
                         mlens_fit_report *report, void *stream);
 
 /*
- * mlens_shoot_learned -- mlens_shoot with the fitted far field: one persistent
- * launch over the tiles of `rays` (which must be the grid of the fit).  Near
- * stars exact, far field from the series and the network, flagged cells exact.
+ * mlens_shoot_learned -- mlens_shoot with the fitted far field over the tiles of
+ * `rays` (which must be the grid of the fit).  Near stars exact, far field from
+ * the series and the network, flagged cells exact: their tiles run first as the
+ * plain sum split over clusters of 8, 4 or 2 CTAs (the largest leaving 2048 stars
+ * per slice; none below 4096 stars or with fma_pairs = 1), so they equal
+ * mlens_shoot with that mlens_set_star_split bit for bit; then one persistent
+ * launch takes the learned tiles.
  * beta_dev as for mlens_shoot_beta (NULL to skip); other arguments as mlens_shoot.
  * row_begin/row_end restrict the call to ray rows [row_begin, row_end) (both
  * multiples of 32; 0, 0 = all rows); a restricted call copies a filtered work

@@ -116,6 +116,12 @@ cudaError_t ff_build_csr(const float4 *stars, int64_t n, const CellGrid &cg, int
 __global__ void __launch_bounds__(256) k_coeffs(const float4 *stars, const int *scell, int64_t n, CellGrid g, int pt,
                                                 double scale, double *out)
 {
+    // One warp per ray cell.  Per far star: w = s / (z_k - z_c) and the order-0
+    // term -m / (z_k - z_c) in FP64 (one reciprocal), accumulated in FP64; the
+    // higher orders t_p = t_0 w^p by an FP32 recurrence into per-lane FP32
+    // partials.  After each 256-star stage the partials are summed across the
+    // warp (shuffles) and lane p adds coefficient p's stage sum to its FP64
+    // accumulator, so FP64 work stays at about twenty operations per pair.
     __shared__ float4 sq[256];
     __shared__ int scl[256];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -124,10 +130,8 @@ __global__ void __launch_bounds__(256) k_coeffs(const float4 *stars, const int *
     const bool ok = rc < nrc;
     const int ex = (ok ? rc % g.ncx : 0) + 1, ey = (ok ? rc / g.ncx : 0) + 1;
     const double zx = g.x0 + ((double)ex + 0.5) * g.w, zy = g.y0 + ((double)ey + 0.5) * g.w;
-    double ar[kPtMax + 1], ai[kPtMax + 1];
-#pragma unroll
-    for (int p = 0; p <= kPtMax; ++p) ar[p] = ai[p] = 0.0;
-    const float fscale = (float)scale;
+    double b0r = 0.0, b0i = 0.0;   // order 0, this lane's stars
+    double accr = 0.0, acci = 0.0;  // lane p (1 <= p <= pt): coefficient p, all stages
     for (int64_t s0 = 0; s0 < n; s0 += 256) {
         const int cnt = (int)min((int64_t)256, n - s0);
         __syncthreads();
@@ -137,6 +141,9 @@ __global__ void __launch_bounds__(256) k_coeffs(const float4 *stars, const int *
         }
         __syncthreads();
         if (!ok) continue;
+        float pr[kPtMax], pi[kPtMax];
+#pragma unroll
+        for (int p = 0; p < kPtMax; ++p) pr[p] = pi[p] = 0.0f;
         for (int k = lane; k < cnt; k += 32) {
             const int c = scl[k];
             if (c >= 0) {
@@ -145,37 +152,48 @@ __global__ void __launch_bounds__(256) k_coeffs(const float4 *stars, const int *
             }
             const float4 q = sq[k];
             const double dx = (double)q.x - zx, dy = (double)q.y - zy;
-            const double inv = scale / (dx * dx + dy * dy);
-            const double wr = dx * inv, wi = -dy * inv;  // s / (z_k - z_c)
-            const double tr = -(double)q.z * wr / scale, ti = -(double)q.z * wi / scale;
-            ar[0] += tr;
-            ai[0] += ti;
-            const float fwr = (float)wr, fwi = (float)wi;
+            const double inv = 1.0 / (dx * dx + dy * dy);
+            const double mi = (double)q.z * inv;
+            const double tr = -mi * dx, ti = mi * dy;  // -m / (z_k - z_c)
+            b0r += tr;
+            b0i += ti;
+            const double si = scale * inv;
+            const float fwr = (float)(dx * si), fwi = (float)(-dy * si);  // s / (z_k - z_c)
             float fr = (float)tr, fi = (float)ti;
 #pragma unroll
-            for (int p = 1; p <= kPtMax; ++p) {
+            for (int p = 0; p < kPtMax; ++p) {
                 const float nr = fr * fwr - fi * fwi, ni = fr * fwi + fi * fwr;
                 fr = nr;
                 fi = ni;
-                if (p <= pt) {
-                    ar[p] += (double)fr;
-                    ai[p] += (double)fi;
-                }
+                pr[p] += fr;
+                pi[p] += fi;
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < kPtMax; ++p) {
+            float r = pr[p], i = pi[p];
+            for (int o = 16; o; o >>= 1) {
+                r += __shfl_xor_sync(0xffffffffu, r, o);
+                i += __shfl_xor_sync(0xffffffffu, i, o);
+            }
+            if (lane == p + 1) {
+                accr += (double)r;
+                acci += (double)i;
             }
         }
     }
     if (!ok) return;
-#pragma unroll
-    for (int p = 0; p <= kPtMax; ++p) {
-        double r = ar[p], i = ai[p];
-        for (int o = 16; o; o >>= 1) {
-            r += __shfl_xor_sync(0xffffffffu, r, o);
-            i += __shfl_xor_sync(0xffffffffu, i, o);
-        }
-        if (lane == 0 && p <= pt) {
-            out[((int64_t)rc * (pt + 1) + p) * 2] = r;
-            out[((int64_t)rc * (pt + 1) + p) * 2 + 1] = i;
-        }
+    for (int o = 16; o; o >>= 1) {
+        b0r += __shfl_xor_sync(0xffffffffu, b0r, o);
+        b0i += __shfl_xor_sync(0xffffffffu, b0i, o);
+    }
+    double *dst = out + (int64_t)rc * (pt + 1) * 2;
+    if (lane == 0) {
+        dst[0] = b0r;
+        dst[1] = b0i;
+    } else if (lane <= pt) {
+        dst[2 * lane] = accr;
+        dst[2 * lane + 1] = acci;
     }
 }
 

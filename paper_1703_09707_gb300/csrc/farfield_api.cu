@@ -412,12 +412,18 @@ int mlens_shoot_learned(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid
     cudaStream_t s = (cudaStream_t)stream;
     const int *items = f->items;
     int64_t nitems = f->nitems, nrows_total = (int64_t)rays->nx * rays->ny;
+    int64_t nheavy = f->nfallback_tiles;  // the list starts with the fallback tiles
     if (!all_rows) {
         const int ntx = (rays->nx + 63) / 64;
         std::vector<int> sub;
-        for (int t : f->h_items) {
+        nheavy = 0;
+        for (size_t q = 0; q < f->h_items.size(); ++q) {
+            const int t = f->h_items[q];
             const int by = t / ntx;
-            if (by * 32 >= row_begin && by * 32 < row_end) sub.push_back(t);
+            if (by * 32 >= row_begin && by * 32 < row_end) {
+                sub.push_back(t);
+                if ((int64_t)q < f->nfallback_tiles) ++nheavy;
+            }
         }
         if (!f->sub_items) FCUDA(dmalloc(&f->sub_items, sizeof(int) * std::max<int64_t>(f->nitems, 1)), "cudaMalloc");
         FCUDA(cudaMemcpyAsync(f->sub_items, sub.data(), sizeof(int) * sub.size(), cudaMemcpyHostToDevice, s),
@@ -454,7 +460,16 @@ int mlens_shoot_learned(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid
     L.items = items;
     L.nitems = nitems;
     L.counter = f->counter;
-    FCUDA(ff_shoot_learned(L, f->grid, ctx->fma_pairs, s), "learned shoot launch");
+    // Fallback tiles (each a full plain tile over all stars) run first, each split
+    // over a cluster of CTAs so that a few flagged cells do not set the map's
+    // time; the persistent learned kernel then takes the learned tiles.
+    const int split = ctx->fma_pairs ? 1 : fallback_star_split(ctx->n_pad);
+    if (split > 1 && nheavy > 0) {
+        FCUDA(launch_shoot_split_list(L.plain, items, nheavy, split, s), "fallback tiles launch");
+        L.items = items + nheavy;
+        L.nitems = nitems - nheavy;
+    }
+    if (L.nitems > 0) FCUDA(ff_shoot_learned(L, f->grid, ctx->fma_pairs, s), "learned shoot launch");
     if (stats_host) {
         unsigned long long h[3];
         FCUDA(cudaMemcpyAsync(h, ctx->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s), "memcpy(stats)");

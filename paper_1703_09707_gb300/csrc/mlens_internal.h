@@ -97,6 +97,12 @@ constexpr int kSplitStage = 256;
 constexpr int64_t kMinSplitStars = 2048;
 cudaError_t launch_shoot_split(const ShootArgs &a, int pairs_per_thread, int split, cudaStream_t s);
 int auto_star_split(const RayGrid &r, int pairs_per_thread, int64_t nstars, int nsm);
+// Tiles of a list (tile = by * tiles_x + bx; 8 rays per thread), one cluster of
+// `split` CTAs per tile; fallback_star_split is the split used for the learned
+// far field's fallback tiles: the largest of 8, 4, 2 leaving kMinSplitStars
+// stars per slice, else 1 (no split).
+cudaError_t launch_shoot_split_list(const ShootArgs &a, const int *tiles, int64_t ntiles, int split, cudaStream_t s);
+int fallback_star_split(int64_t nstars);
 cudaError_t launch_bin(const BinArgs &a, cudaStream_t s);
 
 // helpers (api.cu)

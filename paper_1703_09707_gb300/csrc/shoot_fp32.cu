@@ -146,6 +146,57 @@ static cudaError_t launch_split_t(const ShootArgs &a, cudaStream_t s)
     return cudaSuccess;
 }
 
+// The split star sum over a list of tiles (tile = by * tiles_x + bx), one
+// cluster per listed tile: the learned far field's fallback tiles.
+template <int SPLIT>
+__global__ void __launch_bounds__(kThreads, 2) k_shoot_split_list(ShootArgs a, const int *tiles)
+{
+    __shared__ __align__(16) ShootSmem<kSplitStage> sm;
+    __shared__ TileShared ts;
+    extern __shared__ float4 part[];  // 2 NP float4 per thread
+    const int ntx = (a.rays.nx + kTileX - 1) / kTileX;
+    const int t = tiles[blockIdx.x / SPLIT];
+    shoot_tile<4, kSplitStage, false, 0, SPLIT>(a, t % ntx, t / ntx, sm, ts, part);
+}
+
+template <int SPLIT>
+static cudaError_t launch_split_list_t(const ShootArgs &a, const int *tiles, int64_t ntiles, cudaStream_t s)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = SPLIT;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 2 * 4 * kThreads * sizeof(float4);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaFuncSetAttribute(k_shoot_split_list<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)cfg.dynamicSmemBytes);
+    if (e != cudaSuccess) return e;
+    cfg.gridDim = dim3((unsigned)(ntiles * SPLIT));
+    return cudaLaunchKernelEx(&cfg, k_shoot_split_list<SPLIT>, a, tiles);
+}
+
+cudaError_t launch_shoot_split_list(const ShootArgs &a, const int *tiles, int64_t ntiles, int split, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    if (ntiles * split > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    if (split == 2) return launch_split_list_t<2>(a, tiles, ntiles, s);
+    if (split == 4) return launch_split_list_t<4>(a, tiles, ntiles, s);
+    if (split == 8) return launch_split_list_t<8>(a, tiles, ntiles, s);
+    return cudaErrorInvalidValue;
+}
+
+int fallback_star_split(int64_t nstars)
+{
+    for (int R = 8; R >= 2; R /= 2)
+        if (nstars / R >= kMinSplitStars) return R;
+    return 1;
+}
+
 cudaError_t launch_shoot_split(const ShootArgs &a, int pairs_per_thread, int split, cudaStream_t s)
 {
     if (pairs_per_thread == 2) {

@@ -42,9 +42,16 @@ def host(c, src):
     return c.cpu().numpy().view(np.uint32).reshape(src.ny, src.nx)
 
 
+def fallback_split(n):
+    """The learned kernel's split of a fallback tile's star sum: the largest of 8, 4, 2
+    leaving 2048 stars per slice of the padded field, else none."""
+    n_pad = (n + 31) // 32 * 32
+    return next((r for r in (8, 4, 2) if n_pad // r >= 2048), 1)
+
+
 def plain_map(f):
-    # fallback tiles run the unsplit tile function
-    c, st, b4 = shoot_gpu(f, RAYS, SRC, split=1)
+    # fallback tiles run the plain tile function with the fallback split
+    c, st, b4 = shoot_gpu(f, RAYS, SRC, split=fallback_split(f.n))
     return c, st, b4
 
 
