@@ -788,6 +788,8 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(
 // One tile of a non-flagged cell: near stars exactly (FP32 recentred + Kahan,
 // as the plain kernel), far field = float-pair b0 + series to order pe +
 // network residual, then beta and the same binning epilogue.
+constexpr int kNearChunk = 8;  // near-field stars per compensated chunk
+
 __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int by, ShootSmem<256> &sm, TileShared &ts,
                                              LearnSmem &ls)
 {
@@ -846,12 +848,14 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
             px[p] = py[p] = Sx[p] = Sy[p] = Cx[p] = Cy[p] = f2(0.f, 0.f);
         }
     }
-    // ---- near field: the 3 x 3 block's stars, staged 256 at a time
+    // ---- near field: the 3 x 3 block's stars (about 1.3 per tile at the learned
+    // workload's density), staged 256 at a time and summed in compensated chunks
+    // of kNearChunk stars, padded with massless far stars
     const int nnear = ls.nnear;
     for (int base = 0; base < nnear; base += 256) {
-        const int cnt = min(256, nnear - base), cnt32 = (cnt + 31) & ~31;
+        const int cnt = min(256, nnear - base), cntp = (cnt + kNearChunk - 1) / kNearChunk * kNearChunk;
         __syncthreads();
-        if (tid < cnt32) {
+        if (tid < cntp) {
             float4 q = make_float4(kPadCoord, kPadCoord, 0.0f, 0.0f);
             if (tid < cnt) {
                 int k = base + tid;
@@ -866,9 +870,9 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
         __syncthreads();
         const float4 *Q = sm.st.q[0];
         const float2 *M = sm.st.mm[0];
-        for (int k0 = 0; k0 < cnt32; k0 += kKahan) {
-#pragma unroll 4
-            for (int k = k0; k < k0 + kKahan; ++k) {
+        for (int k0 = 0; k0 < cntp; k0 += kNearChunk) {
+#pragma unroll
+            for (int k = k0; k < k0 + kNearChunk; ++k) {
                 const float4 q = Q[k];
                 const float2 m2 = M[k];
                 const float2 dx = __fadd2_rn(rx, f2(q.x, q.y));
