@@ -113,15 +113,55 @@ cudaError_t ff_build_csr(const float4 *stars, int64_t n, const CellGrid &cg, int
 // FP32 from the FP64 w (relative error ~p 6e-8 per term, far below what the
 // series needs) and accumulated in FP64, so the sums keep FP64 accuracy while
 // the per-term work moves to the FP32 pipe.
+// Double-float arithmetic (an unevaluated pair of floats, ~48 significant bits) on
+// the FP32 pipe: Knuth's TwoSum, the FMA form of Dekker's TwoProduct, and one
+// Newton step for the reciprocal.  Used for the order-0 far-field term, which
+// needs more than FP32 but not the FP64 pipe's scarce throughput.
+struct DF {
+    float h, l;
+};
+__device__ __forceinline__ DF df_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF df_norm(float a, float b)  // |b| small against a
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    const DF s = df_two_sum(a.h, b.h);
+    return df_norm(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b)
+{
+    const float p = __fmul_rn(a.h, b.h), e = __fmaf_rn(a.h, b.h, -p);
+    return df_norm(p, __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e)));
+}
+__device__ __forceinline__ DF df_mulf(DF a, float b)
+{
+    const float p = __fmul_rn(a.h, b), e = __fmaf_rn(a.h, b, -p);
+    return df_norm(p, __fmaf_rn(a.l, b, e));
+}
+__device__ __forceinline__ DF df_rcp(DF a)
+{
+    const float y = __frcp_rn(a.h);           // relative error <= 2^-24
+    const DF ay = df_mulf(a, y);              // ~1
+    const DF r = df_add({1.0f, 0.0f}, {-ay.h, -ay.l});  // 1 - a y, ~2^-24
+    return df_norm(y, __fmul_rn(y, r.h));     // y (1 + r): error ~2^-47
+}
+
 __global__ void __launch_bounds__(256) k_coeffs(const float4 *stars, const int *scell, int64_t n, CellGrid g, int pt,
                                                 double scale, double *out)
 {
-    // One warp per ray cell.  Per far star: w = s / (z_k - z_c) and the order-0
-    // term -m / (z_k - z_c) in FP64 (one reciprocal), accumulated in FP64; the
-    // higher orders t_p = t_0 w^p by an FP32 recurrence into per-lane FP32
-    // partials.  After each 256-star stage the partials are summed across the
-    // warp (shuffles) and lane p adds coefficient p's stage sum to its FP64
-    // accumulator, so FP64 work stays at about twenty operations per pair.
+    // One warp per ray cell.  Per far star: the order-0 term -m / (z_k - z_c) in
+    // double-float arithmetic on the FP32 pipe, summed per lane over each stage's
+    // stars and added to an FP64 accumulator once per stage; w = s / (z_k - z_c)
+    // in FP32 and the higher orders t_p = t_0 w^p by an FP32 recurrence into
+    // per-lane FP32 partials, summed across the warp after each 256-star stage,
+    // lane p adding coefficient p's stage sum to its FP64 accumulator.
     __shared__ float4 sq[256];
     __shared__ int scl[256];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -130,7 +170,11 @@ __global__ void __launch_bounds__(256) k_coeffs(const float4 *stars, const int *
     const bool ok = rc < nrc;
     const int ex = (ok ? rc % g.ncx : 0) + 1, ey = (ok ? rc / g.ncx : 0) + 1;
     const double zx = g.x0 + ((double)ex + 0.5) * g.w, zy = g.y0 + ((double)ey + 0.5) * g.w;
-    double b0r = 0.0, b0i = 0.0;   // order 0, this lane's stars
+    // the cell centre as float pairs (48 bits of it; the star positions are floats)
+    const float zxh = (float)zx, zxl = (float)(zx - (double)zxh);
+    const float zyh = (float)zy, zyl = (float)(zy - (double)zyh);
+    const float fscale = (float)scale;
+    double b0r = 0.0, b0i = 0.0;    // order 0, this lane's stars
     double accr = 0.0, acci = 0.0;  // lane p (1 <= p <= pt): coefficient p, all stages
     for (int64_t s0 = 0; s0 < n; s0 += 256) {
         const int cnt = (int)min((int64_t)256, n - s0);
@@ -144,6 +188,7 @@ __global__ void __launch_bounds__(256) k_coeffs(const float4 *stars, const int *
         float pr[kPtMax], pi[kPtMax];
 #pragma unroll
         for (int p = 0; p < kPtMax; ++p) pr[p] = pi[p] = 0.0f;
+        DF sr = {0.0f, 0.0f}, si = {0.0f, 0.0f};
         for (int k = lane; k < cnt; k += 32) {
             const int c = scl[k];
             if (c >= 0) {
@@ -151,15 +196,16 @@ __global__ void __launch_bounds__(256) k_coeffs(const float4 *stars, const int *
                 if (sx - ex <= 1 && ex - sx <= 1 && sy - ey <= 1 && ey - sy <= 1) continue;  // near star
             }
             const float4 q = sq[k];
-            const double dx = (double)q.x - zx, dy = (double)q.y - zy;
-            const double inv = 1.0 / (dx * dx + dy * dy);
-            const double mi = (double)q.z * inv;
-            const double tr = -mi * dx, ti = mi * dy;  // -m / (z_k - z_c)
-            b0r += tr;
-            b0i += ti;
-            const double si = scale * inv;
-            const float fwr = (float)(dx * si), fwi = (float)(-dy * si);  // s / (z_k - z_c)
-            float fr = (float)tr, fi = (float)ti;
+            const DF dx = df_add(df_two_sum(q.x, -zxh), {-zxl, 0.0f});
+            const DF dy = df_add(df_two_sum(q.y, -zyh), {-zyl, 0.0f});
+            const DF inv = df_rcp(df_add(df_mul(dx, dx), df_mul(dy, dy)));
+            const DF mi = df_mulf(inv, q.z);
+            const DF tr = df_mul(mi, dx), ti = df_mul(mi, dy);  // -m/(z_k - z_c) = (-tr, ti)
+            sr = df_add(sr, {-tr.h, -tr.l});
+            si = df_add(si, ti);
+            const float si_s = __fmul_rn(inv.h, fscale);
+            const float fwr = __fmul_rn(dx.h, si_s), fwi = -__fmul_rn(dy.h, si_s);  // s / (z_k - z_c)
+            float fr = -tr.h, fi = ti.h;
 #pragma unroll
             for (int p = 0; p < kPtMax; ++p) {
                 const float nr = fr * fwr - fi * fwi, ni = fr * fwi + fi * fwr;
@@ -169,6 +215,8 @@ __global__ void __launch_bounds__(256) k_coeffs(const float4 *stars, const int *
                 pi[p] += fi;
             }
         }
+        b0r += (double)sr.h + (double)sr.l;
+        b0i += (double)si.h + (double)si.l;
 #pragma unroll
         for (int p = 0; p < kPtMax; ++p) {
             float r = pr[p], i = pi[p];
