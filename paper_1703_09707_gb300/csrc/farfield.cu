@@ -355,6 +355,8 @@ constexpr int kSampW = 16;       // samples per warp
 constexpr int kSampC = 128;      // samples per CTA
 constexpr int kLdT = kSampC + 8; // 136
 
+constexpr int kGP = kParams + 2;  // gpart row: the parameters' gradients, then the loss
+
 struct TrainSmemLayout {
     static constexpr int W1z = 0;                          // [64][40]
     static constexpr int W2 = W1z + kHid * kLdZ;           // [64][72] (n=out, k=in)
@@ -371,7 +373,11 @@ struct TrainSmemLayout {
     static constexpr int fW1u = 0, fb1 = 128, fb2 = 192, fW3 = 256, fb3 = 384, fdb1 = 388, fdb2 = 452;
     static constexpr int fWarp = 516;  // per warp: u[16][2], t[16][2], sc[16]
     static constexpr int fWarpSize = 80;
-    static constexpr int EndF = fWarp + 8 * fWarpSize;
+    // per warp gradient slots, summed over the warps in a fixed order:
+    // W3 [128] at 0, b3 [2] at 128, W1u [128] at 130, b1 [64] at 258, b2 [64] at 322, loss at 386
+    static constexpr int fWG = fWarp + 8 * fWarpSize;
+    static constexpr int kWG = 388;
+    static constexpr int EndF = fWG + 8 * kWG;
     static constexpr size_t bytes = (size_t)EndBf * 2 + (size_t)EndF * 4 + 8 * 16 * 4 * 2;
 };
 
@@ -430,8 +436,6 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
     if (tid < 64) {
         sf[L::fb1 + tid] = A.params[ob1 + tid];
         sf[L::fb2 + tid] = A.params[ob2 + tid];
-        sf[L::fdb1 + tid] = 0.0f;
-        sf[L::fdb2 + tid] = 0.0f;
     }
     if (tid < 2) sf[L::fb3 + tid] = A.params[ob3 + tid];
 
@@ -575,7 +579,13 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
         }
     }
     for (int o = 16; o; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-    if (lane == 0 && A.loss) atomicAdd(A.loss, lsum * A.inv_batch);
+    float *wg = sf + L::fWG + warp * L::kWG;  // this warp's gradient slots
+    if (lane == 0) {
+        if (A.backward)
+            wg[386] = lsum * A.inv_batch;
+        else if (A.loss)
+            atomicAdd(A.loss, lsum * A.inv_batch);
+    }
     if (!A.backward) return;
 
     // ---- layer 3 gradients
@@ -591,8 +601,8 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
                 w1 += __shfl_xor_sync(0xffffffffu, w1, o);
             }
             if (g == 0) {
-                atomicAdd(&A.grads[oW3 + col], w0);
-                atomicAdd(&A.grads[oW3 + kHid + col], w1);
+                wg[col] = w0;
+                wg[kHid + col] = w1;
             }
         }
     }
@@ -603,8 +613,8 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
             d1 += __shfl_xor_sync(0xffffffffu, d1, o);
         }
         if (lane == 0) {
-            atomicAdd(&A.grads[ob3], d0);
-            atomicAdd(&A.grads[ob3 + 1], d1);
+            wg[128] = d0;
+            wg[129] = d1;
         }
     }
     // ---- dh2 = (dy W3) * silu'(h2)
@@ -624,7 +634,7 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
                 sb[L::DH2T + col * kLdT + warp * kSampW + rows[r]] = v;
             }
             for (int o = 4; o < 32; o <<= 1) colsum += __shfl_xor_sync(0xffffffffu, colsum, o);
-            if (g == 0) atomicAdd(&sf[L::fdb2 + col], colsum);
+            if (g == 0) wg[322 + col] = colsum;
         }
     }
     __syncwarp();
@@ -665,9 +675,9 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
                 gu1 += __shfl_xor_sync(0xffffffffu, gu1, o);
             }
             if (g == 0) {
-                atomicAdd(&sf[L::fdb1 + col], colsum);
-                atomicAdd(&A.grads[oW1u + 2 * col], gu0);
-                atomicAdd(&A.grads[oW1u + 2 * col + 1], gu1);
+                wg[258 + col] = colsum;
+                wg[130 + 2 * col] = gu0;
+                wg[130 + 2 * col + 1] = gu1;
             }
         }
     }
@@ -697,13 +707,14 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
                 if (expl) {
                     if (A.dzout) A.dzout[(cbase + row) * kLat + col] = dzc[nb][j];
                 } else {
-                    atomicAdd(&A.dz[(int64_t)wrc[row] * kLat + col], dzc[nb][j]);
+                    A.dzs[(cbase + row) * kLat + col] = dzc[nb][j];
                 }
             }
         }
     }
     __syncthreads();
-    // ---- CTA-level weight gradients over the 128 samples
+    // ---- CTA-level weight gradients over the 128 samples, into this CTA's row
+    float *gp = A.gpart + (int64_t)blockIdx.x * kGP;
     {
         // dW2[out][in] = sum_s dh2[s][out] a1[s][in]: warp w takes in-block w
         float c[4][4];
@@ -725,7 +736,7 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int out = mb * 16 + g + (j < 2 ? 0 : 8), in = warp * 8 + 2 * t + (j & 1);
-                atomicAdd(&A.grads[oW2 + out * kHid + in], c[mb][j]);
+                gp[oW2 + out * kHid + in] = c[mb][j];
             }
     }
     if (warp < 4) {
@@ -749,11 +760,21 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int out = mb * 16 + g + (j < 2 ? 0 : 8), in = warp * 8 + 2 * t + (j & 1);
-                atomicAdd(&A.grads[oW1z + out * kLat + in], c[mb][j]);
+                gp[oW1z + out * kLat + in] = c[mb][j];
             }
     }
-    if (tid < 64) atomicAdd(&A.grads[ob1 + tid], sf[L::fdb1 + tid]);
-    else if (tid < 128) atomicAdd(&A.grads[ob2 + tid - 64], sf[L::fdb2 + tid - 64]);
+    // the per-warp slots, summed over the warps in order
+    for (int e = tid; e < 387; e += 256) {
+        float acc = 0.0f;
+        for (int w = 0; w < 8; ++w) acc += sf[L::fWG + w * L::kWG + e];
+        const int dst = e < 128 ? oW3 + e
+                      : e < 130 ? ob3 + (e - 128)
+                      : e < 258 ? oW1u + (e - 130)
+                      : e < 322 ? ob1 + (e - 258)
+                      : e < 386 ? ob2 + (e - 322)
+                                : kParams;  // the loss
+        gp[dst] = acc;
+    }
 }
 
 cudaError_t ff_train_step(const TrainArgs &t, int64_t nsamples, cudaStream_t s)
@@ -764,6 +785,51 @@ cudaError_t ff_train_step(const TrainArgs &t, int64_t nsamples, cudaStream_t s)
     if (nsamples <= 0) return cudaSuccess;
     const unsigned nb = (unsigned)((nsamples + kSampC - 1) / kSampC);
     k_ff_train<<<nb, 256, TrainSmemLayout::bytes, s>>>(t);
+    return cudaGetLastError();
+}
+
+int64_t ff_gpart_stride() { return kGP; }
+int64_t ff_train_blocks(int64_t nsamples) { return (nsamples + kSampC - 1) / kSampC; }
+
+// grads[p] = sum over the CTA rows of gpart in row order (and the loss).
+__global__ void k_reduce_grads(const float *__restrict__ gpart, int64_t nblk, float *__restrict__ grads,
+                               float *__restrict__ loss)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > kParams) return;
+    float acc = 0.0f;
+#pragma unroll 8
+    for (int64_t b = 0; b < nblk; ++b) acc += gpart[b * kGP + p];
+    if (p < kParams)
+        grads[p] = acc;
+    else if (loss)
+        *loss = acc;
+}
+
+// dz[c][k] = sum of the step's samples of cell c in sample order: sample li of
+// the step is sample offset + li of the sequence, whose cell is its index mod nrc.
+__global__ void k_reduce_latents(const float *__restrict__ dzs, int64_t count, int64_t offset, int nrc,
+                                 float *__restrict__ dz)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)nrc * kLat) return;
+    const int c = (int)(e / kLat), k = (int)(e % kLat);
+    int64_t li = ((int64_t)c - offset % nrc + nrc) % nrc;
+    float acc = 0.0f;
+    for (; li < count; li += nrc) acc += dzs[li * kLat + k];
+    dz[e] = acc;
+}
+
+cudaError_t ff_reduce_grads(const float *gpart, int64_t nblk, float *grads, float *loss, cudaStream_t s)
+{
+    k_reduce_grads<<<(kParams + 1 + 255) / 256, 256, 0, s>>>(gpart, nblk, grads, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t ff_reduce_latents(const float *dzs, int64_t count, int64_t offset, int nrc, float *dz, cudaStream_t s)
+{
+    const int64_t n = (int64_t)nrc * kLat;
+    k_reduce_latents<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dzs, count, offset, nrc, dz);
     return cudaGetLastError();
 }
 

@@ -71,8 +71,14 @@ struct TrainArgs {
     // network
     float *params;                     // FP32 master (read)
     const __nv_bfloat16 *w1zb, *w2b, *w2tb, *w1ztb;  // BF16 copies: [64][32], [64][64], [64(in)][64(out)], [32][64]
-    float *grads;                      // FP32 gradient accumulators (flat layout)
-    float *loss;                       // accumulated loss (sum of squared errors / B)
+    float *grads;                      // host-side bookkeeping: the reduced gradients (flat layout)
+    float *loss;                       // validation / forward-only: accumulated loss (sum of squared errors / B)
+    // backward: each CTA writes its weight gradients and loss to row blockIdx.x of
+    // gpart (ff_gpart_stride floats per row) and each sample its latent gradient
+    // to dzs[sample][32]; ff_reduce_grads / ff_reduce_latents sum them in a fixed
+    // order (deterministic training)
+    float *gpart;
+    float *dzs;
     // generated samples (training / validation)
     const float *z;                    // latents [nrc][32]
     float *dz;                         // latent gradients [nrc][32]
@@ -105,6 +111,10 @@ cudaError_t ff_prep_bf16(const float *params, __nv_bfloat16 *w1zb, __nv_bfloat16
 cudaError_t ff_train_step(const TrainArgs &t, int64_t nsamples, cudaStream_t s);
 cudaError_t ff_adam(float *p, float *m, float *v, const float *g, int64_t n, float lr, float b1, float b2, float eps,
                     float bc1, float bc2, cudaStream_t s);
+int64_t ff_gpart_stride();                 // floats per CTA row of gpart
+int64_t ff_train_blocks(int64_t nsamples);  // CTAs of one ff_train_step
+cudaError_t ff_reduce_grads(const float *gpart, int64_t nblk, float *grads, float *loss, cudaStream_t s);
+cudaError_t ff_reduce_latents(const float *dzs, int64_t count, int64_t offset, int nrc, float *dz, cudaStream_t s);
 cudaError_t ff_embed(const float *params, const float *z, int nrc, float *ec, cudaStream_t s);
 cudaError_t ff_flags(const unsigned *maxerr, int nrc, float tol, int *flags, cudaStream_t s);
 // fallback tiles use the plain tile function with the context's fma_pairs setting

@@ -31,6 +31,8 @@ struct FarState {
     double *coef64 = nullptr;
     float *coef = nullptr, *tail = nullptr, *sc = nullptr;
     float *params = nullptr, *m = nullptr, *v = nullptr, *grads = nullptr, *loss = nullptr;  // params then Z
+    float *gpart = nullptr, *dzs = nullptr;  // per-CTA gradient rows and per-sample latent gradients of a step
+    int64_t gpart_rows = 0, dzs_samples = 0;
     __nv_bfloat16 *w1zb = nullptr, *w2b = nullptr, *w2tb = nullptr, *w1ztb = nullptr;
     float *ec = nullptr;
     int *flags = nullptr;
@@ -81,6 +83,8 @@ void free_state(FarState *f)
     ffree(f->w1zb), ffree(f->w2b), ffree(f->w2tb), ffree(f->w1ztb), ffree(f->ec), ffree(f->flags);
     ffree(f->vmax_net), ffree(f->vmax_series), ffree(f->vsum), ffree(f->items), ffree(f->counter);
     ffree(f->sub_items);
+    ffree(f->gpart), ffree(f->dzs);
+    f->gpart_rows = f->dzs_samples = 0;
     f->ready = false;
 }
 
@@ -161,6 +165,8 @@ TrainArgs train_args(FarState *f)
     t.w1ztb = f->w1ztb;
     t.grads = f->grads;
     t.loss = f->loss;
+    t.gpart = f->gpart;
+    t.dzs = f->dzs;
     t.z = f->params + mlp::kParams;
     t.dz = f->grads + mlp::kParams;
     t.tail = f->tail;
@@ -341,6 +347,17 @@ int mlens_fit_far_field(mlens_ctx *ctx, const mlens_grid *rays, const mlens_fit_
     if (f->use_net) {
         const int64_t per_epoch = (p.train_samples + p.batch - 1) / p.batch;
         const int64_t total = per_epoch * p.epochs;
+        const int64_t rows = ff_train_blocks(p.batch);
+        if (f->gpart_rows < rows) {
+            ffree(f->gpart);
+            FCUDA(dmalloc(&f->gpart, sizeof(float) * rows * ff_gpart_stride()), "cudaMalloc(gradient rows)");
+            f->gpart_rows = rows;
+        }
+        if (f->dzs_samples < p.batch) {
+            ffree(f->dzs);
+            FCUDA(dmalloc(&f->dzs, sizeof(float) * p.batch * mlp::kLat), "cudaMalloc(latent gradients)");
+            f->dzs_samples = p.batch;
+        }
         TrainArgs t = train_args(f);
         t.spec.seed = p.seed * 0x9E3779B97F4A7C15ull + 17;
         for (int64_t k = 0; k < total; ++k) {
@@ -349,10 +366,12 @@ int mlens_fit_far_field(mlens_ctx *ctx, const mlens_grid *rays, const mlens_fit_
             t.spec.offset = j * p.batch;
             t.spec.count = cnt;
             t.inv_batch = 1.0f / (float)cnt;
-            FCUDA(cudaMemsetAsync(f->grads, 0, sizeof(float) * np, s), "memset(grads)");
-            FCUDA(cudaMemsetAsync(f->loss, 0, sizeof(float), s), "memset(loss)");
             FCUDA(ff_prep_bf16(f->params, f->w1zb, f->w2b, f->w2tb, f->w1ztb, s), "prep");
             FCUDA(ff_train_step(t, cnt, s), "train step");
+            // gradients summed in a fixed order: training is bit-reproducible
+            FCUDA(ff_reduce_grads(f->gpart, ff_train_blocks(cnt), f->grads, f->loss, s), "gradient reduction");
+            FCUDA(ff_reduce_latents(f->dzs, cnt, t.spec.offset, f->nrc, f->grads + mlp::kParams, s),
+                  "latent gradient reduction");
             // cosine decay to 5% of the initial rates
             const double fr = (double)k / (double)std::max<int64_t>(total - 1, 1);
             const double sc = 0.05 + 0.95 * 0.5 * (1.0 + std::cos(3.14159265358979323846 * fr));
@@ -638,8 +657,10 @@ int mlens_ff_eval(const float *params_dev, const float *z_dev, const float *u_de
     cudaError_t e = dmalloc(&dl, sizeof(float));
     __nv_bfloat16 *w1zb = w, *w1ztb = w + mlp::kHid * mlp::kLat, *w2b = w1ztb + mlp::kHid * mlp::kLat,
                   *w2tb = w2b + mlp::kHid * mlp::kHid;
+    float *gpart = nullptr;
+    const int64_t nblk = ff_train_blocks(nsamples);
+    if (e == cudaSuccess && grads_dev) e = dmalloc(&gpart, sizeof(float) * nblk * ff_gpart_stride());
     if (e == cudaSuccess) e = cudaMemsetAsync(dl, 0, sizeof(float), s);
-    if (e == cudaSuccess && grads_dev) e = cudaMemsetAsync(grads_dev, 0, sizeof(float) * mlp::kParams, s);
     if (e == cudaSuccess) e = ff_prep_bf16(params_dev, w1zb, w2b, w2tb, w1ztb, s);
     if (e == cudaSuccess) {
         TrainArgs t{};
@@ -650,6 +671,7 @@ int mlens_ff_eval(const float *params_dev, const float *z_dev, const float *u_de
         t.w1ztb = w1ztb;
         t.grads = grads_dev;
         t.loss = dl;
+        t.gpart = gpart;
         t.spec.count = nsamples;
         t.spec.nrc = 1;
         t.inv_batch = 1.0f / (float)nsamples;
@@ -660,12 +682,15 @@ int mlens_ff_eval(const float *params_dev, const float *z_dev, const float *u_de
         t.dzout = dz_dev;
         t.backward = grads_dev ? 1 : 0;
         e = ff_train_step(t, nsamples, s);
+        if (e == cudaSuccess && grads_dev) e = ff_reduce_grads(gpart, nblk, grads_dev, dl, s);
     }
     float h = 0.0f;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, dl, sizeof(float), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) cudaStreamSynchronize(s);
     dfree(w);
     dfree(dl);
+    dfree(gpart);
     if (e != cudaSuccess) return fcuda(e, "mlens_ff_eval");
     if (loss_host) *loss_host = h;
     return MLENS_OK;

@@ -260,3 +260,23 @@ def test_learned_full_size_workload_against_the_oracle():
     l1 = np.abs(a - b).sum() / b.sum()
     assert l1 <= 1e-3, l1
     ctx.close()
+
+
+def test_fit_is_bit_reproducible(field):
+    """Gradients are summed in a fixed order (per-CTA rows, per-sample latent
+    gradients): two fits of the same field give the same parameters, latents, flags
+    and maps bit for bit."""
+    outs = []
+    for _ in range(2):
+        ctx = make_ctx(field)
+        rep = M.mlens_fit_far_field(ctx, RAYS, M.fit_params(cells_x=CELLS_X, use_network=1, order=6,
+                                                            train_samples=1 << 18, epochs=8, tolerance=1e-6))
+        ex = M.mlens_far_field_export(ctx)
+        cl, st, _ = learned_map(ctx)
+        outs.append((rep, ex, cl, st))
+        ctx.close()
+    (r0, e0, c0, s0), (r1, e1, c1, s1) = outs
+    for k in ("params", "latents", "flags", "val_max_net"):
+        assert np.array_equal(np.asarray(e0[k]).view(np.uint32), np.asarray(e1[k]).view(np.uint32)), k
+    assert r0["final_loss"] == r1["final_loss"] and r0["cells_fallback"] == r1["cells_fallback"]
+    assert np.array_equal(c0, c1) and s0 == s1
