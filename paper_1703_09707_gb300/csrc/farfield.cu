@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include "farfield.h"
+#include "umma.cuh"
 #include "mlp.cuh"
 #include "tile.cuh"
 
@@ -888,7 +889,12 @@ cudaError_t ff_flags(const unsigned *maxerr, int nrc, float tol, int *flags, cud
 
 // ================================================ learned shooting kernel
 struct LearnSmem {
-    __nv_bfloat16 w2[kHid * kLdH];
+    __align__(128) unsigned char w2cm[kHid * kHid * 2];  // W2 [out][in], BF16, core-matrix layout (B operand)
+    uint64_t mbar[2];     // per warpgroup: completion of its tensor-core MMAs
+    uint32_t tmem;        // tensor-memory base: 128 columns, 64 per warpgroup
+    int wg_ok[8];         // per warp: the last wait completed
+    int tc_dead[2];       // per warpgroup: a wait gave up; no more MMAs
+    uint32_t pending[2];  // the phase a dead warpgroup still waits for
     float w1u[2 * kHid], b2[kHid], w3[2 * kHid], b3[2];
     float ec[kHid];
     float coef[kCoefStride];
@@ -903,9 +909,14 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(
 // as the plain kernel), far field = float-pair b0 + series to order pe +
 // network residual, then beta and the same binning epilogue.
 constexpr int kNearChunk = 8;  // near-field stars per compensated chunk
+constexpr int kTcChunk = 128;                            // rays per tensor-core MMA (M)
+constexpr int kTcABytes = kTcChunk * kHid * 2;           // one warpgroup's A operand (16 KB)
+constexpr int kTcSmem = 2 * kTcABytes;                   // dynamic shared memory of the learned kernel
+constexpr int kWaitPolls = 1 << 20;                      // bound on a completion wait
 
+template <bool NET>
 __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int by, ShootSmem<256> &sm, TileShared &ts,
-                                             LearnSmem &ls)
+                                             LearnSmem &ls, unsigned char *abuf_all, uint32_t &phase)
 {
     constexpr int NP = 4;
     constexpr int kTileY = 32;
@@ -1016,66 +1027,83 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
     float *Y = reinterpret_cast<float *>(sm.hist);
     const int ioff = (bx % cg.ktx) * kTileX, joff = (by % cg.kty) * kTileY;
     const float inv_cx = 1.0f / (float)(kTileX * cg.ktx), inv_cy = 1.0f / (float)(kTileY * cg.kty);
-    if (L.use_net) {
-        const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-        for (int blk = 0; blk < 16; ++blk) {
-            const int rA = warp * 256 + blk * 16 + g, rB = rA + 8;
-            const float uxA = (float)(2 * (ioff + (rA & 63)) + 1) * inv_cx - 1.0f;
-            const float uyA = (float)(2 * (joff + (rA >> 6)) + 1) * inv_cy - 1.0f;
-            const float uxB = (float)(2 * (ioff + (rB & 63)) + 1) * inv_cx - 1.0f;
-            const float uyB = (float)(2 * (joff + (rB >> 6)) + 1) * inv_cy - 1.0f;
-            uint32_t af[4][4];
+    if (NET) {
+        // Two warpgroups; warpgroup wg takes the 128-ray chunks wg, wg + 2, ...  Each
+        // thread writes its ray's layer-1 activations (BF16) as row t of the
+        // warpgroup's A operand; one thread issues h2 = A W2^T on the tensor cores
+        // (tcgen05.mma, M = 128, N = 64, K = 64 in four K = 16 steps, FP32
+        // accumulator in tensor memory) and commits to the warpgroup's mbarrier;
+        // then each thread reads its ray's 64 accumulators back and finishes SiLU
+        // and layer 3 in registers.
+        const int warp = tid >> 5, lane = tid & 31, wg = warp >> 2, t = tid & 127;
+        unsigned char *abuf = abuf_all + wg * kTcABytes;
+        const uint32_t dcol = ls.tmem + (uint32_t)(wg * kHid);
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        constexpr uint32_t idesc = umma::idesc_bf16(kTcChunk, kHid);
+        for (int ch = wg; ch < 2048 / kTcChunk; ch += 2) {
+            const int r = ch * kTcChunk + t;  // ray of the tile (row-major 64 x 32)
+            float y0 = 0.0f, y1 = 0.0f;
+            if (!ls.tc_dead[wg]) {
+                const float ux = (float)(2 * (ioff + (r & 63)) + 1) * inv_cx - 1.0f;
+                const float uy = (float)(2 * (joff + (r >> 6)) + 1) * inv_cy - 1.0f;
 #pragma unroll
-            for (int kb = 0; kb < 4; ++kb) {
-                float v[8];
+                for (int k8 = 0; k8 < kHid / 8; ++k8) {
+                    uint32_t pk[4];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int col = kb * 16 + 2 * t + (e & 1) + ((e >> 2) ? 8 : 0);
-                    const bool rowB = (e >> 1) & 1;
-                    const float ux = rowB ? uxB : uxA, uy = rowB ? uyB : uyA;
-                    v[e] = silu1(ls.ec[col] + ls.w1u[2 * col] * ux + ls.w1u[2 * col + 1] * uy);
-                }
-                af[kb][0] = pack_bf16(v[0], v[1]);  // row A, cols c, c+1
-                af[kb][1] = pack_bf16(v[2], v[3]);  // row B
-                af[kb][2] = pack_bf16(v[4], v[5]);  // row A, cols c+8, c+9
-                af[kb][3] = pack_bf16(v[6], v[7]);  // row B
-            }
-            float yA0 = 0.f, yA1 = 0.f, yB0 = 0.f, yB1 = 0.f;
-#pragma unroll
-            for (int nb = 0; nb < 8; ++nb) {
-                float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                for (int kb = 0; kb < 4; ++kb) {
-                    uint32_t b[2];
-                    load_b(b, ls.w2, kLdH, nb * 8, kb * 16);
-                    mma16816(c, af[kb], b);
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int col = nb * 8 + 2 * t + (j & 1);
-                    const float a2 = silu2(c[j] + ls.b2[col]);
-                    if (j < 2) {
-                        yA0 += ls.w3[col] * a2;
-                        yA1 += ls.w3[kHid + col] * a2;
-                    } else {
-                        yB0 += ls.w3[col] * a2;
-                        yB1 += ls.w3[kHid + col] * a2;
+                    for (int q = 0; q < 4; ++q) {
+                        const int c0 = k8 * 8 + 2 * q;
+                        const float v0 = silu1(ls.ec[c0] + ls.w1u[2 * c0] * ux + ls.w1u[2 * c0 + 1] * uy);
+                        const float v1 =
+                            silu1(ls.ec[c0 + 1] + ls.w1u[2 * c0 + 2] * ux + ls.w1u[2 * c0 + 3] * uy);
+                        pk[q] = pack_bf16(v0, v1);
                     }
+                    *reinterpret_cast<uint4 *>(abuf + umma::cm_offset(t, k8 * 8)) =
+                        make_uint4(pk[0], pk[1], pk[2], pk[3]);
                 }
-            }
+                umma::fence_async_smem();
+                umma::fence_before();
+                umma::wg_sync(wg);
+                umma::fence_after();
+                if (t == 0) {
 #pragma unroll
-            for (int o = 1; o <= 2; o <<= 1) {
-                yA0 += __shfl_xor_sync(0xffffffffu, yA0, o);
-                yA1 += __shfl_xor_sync(0xffffffffu, yA1, o);
-                yB0 += __shfl_xor_sync(0xffffffffu, yB0, o);
-                yB1 += __shfl_xor_sync(0xffffffffu, yB1, o);
+                    for (int ks = 0; ks < kHid / 16; ++ks)
+                        umma::mma_bf16(dcol, umma::desc(umma::smem_addr(abuf) + ks * 256, 128, 1024),
+                                       umma::desc(umma::smem_addr(ls.w2cm) + ks * 256, 128, 1024), idesc,
+                                       ks > 0 ? 1u : 0u);
+                    umma::commit(&ls.mbar[wg]);
+                }
+                const bool ok = __all_sync(0xffffffffu, umma::mbar_wait(&ls.mbar[wg], phase, kWaitPolls));
+                if (lane == 0) ls.wg_ok[warp] = ok ? 1 : 0;
+                umma::wg_sync(wg);
+                const bool wg_ok = ls.wg_ok[4 * wg] && ls.wg_ok[4 * wg + 1] && ls.wg_ok[4 * wg + 2] &&
+                                   ls.wg_ok[4 * wg + 3];
+                if (wg_ok) {
+                    phase ^= 1u;
+                    umma::fence_after();
+#pragma unroll
+                    for (int c0 = 0; c0 < kHid; c0 += 16) {
+                        uint32_t acc[16];
+                        umma::ld16(dcol + lane_base + (uint32_t)c0, acc);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int col = c0 + j;
+                            const float a2 = silu2(__uint_as_float(acc[j]) + ls.b2[col]);
+                            y0 += ls.w3[col] * a2;
+                            y1 += ls.w3[kHid + col] * a2;
+                        }
+                    }
+                } else if (t == 0) {
+                    // the MMAs never reported completion: stop using the tensor path,
+                    // remember the phase to drain before tensor memory is freed
+                    ls.tc_dead[wg] = 1;
+                    ls.pending[wg] = phase;
+                    atomicExch(L.err, 1);
+                }
+                umma::fence_before();
+                umma::wg_sync(wg);  // accumulators read and A consumed before the next chunk
             }
-            if (t == 0) {
-                Y[2 * rA] = yA0 + ls.b3[0];
-                Y[2 * rA + 1] = yA1 + ls.b3[1];
-                Y[2 * rB] = yB0 + ls.b3[0];
-                Y[2 * rB + 1] = yB1 + ls.b3[1];
-            }
+            Y[2 * r] = y0 + ls.b3[0];
+            Y[2 * r + 1] = y1 + ls.b3[1];
         }
     }
     __syncthreads();
@@ -1166,22 +1194,39 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
     stats_add_block(nb, no, nn, ts.sred, a.stats);
 }
 
-template <int NRP>
+// NET: the network on the tensor cores (tcgen05; tensor memory and kTcSmem bytes
+// of dynamic shared memory); without it (the series alone) the kernel carries no
+// tensor-core code and no dynamic shared memory.
+template <int NRP, bool NET>
 __global__ void __launch_bounds__(kThreads, 2) k_shoot_learned(LearnedArgs L)
 {
     __shared__ __align__(16) ShootSmem<256> sm;
     __shared__ TileShared ts;
-    __shared__ __align__(16) LearnSmem ls;
+    __shared__ __align__(128) LearnSmem ls;
     __shared__ long long s_item;
+    extern __shared__ __align__(128) unsigned char tc_abuf[];  // two A operands, kTcSmem bytes
     const int tid = threadIdx.x;
-    if (L.use_net) {
-        for (int i = tid; i < kHid * kHid; i += kThreads) ls.w2[(i / kHid) * kLdH + i % kHid] = L.w2b[i];
+    uint32_t phase = 0;  // completed MMA batches of this thread's warpgroup, mod 2
+    if (NET) {
+        for (int i = tid; i < kHid * kHid; i += kThreads)
+            *reinterpret_cast<__nv_bfloat16 *>(ls.w2cm + umma::cm_offset(i / kHid, i % kHid)) = L.w2b[i];
         for (int i = tid; i < 2 * kHid; i += kThreads) {
             ls.w1u[i] = L.params[oW1u + i];
             ls.w3[i] = L.params[oW3 + i];
         }
         if (tid < kHid) ls.b2[tid] = L.params[ob2 + tid];
         if (tid < 2) ls.b3[tid] = L.params[ob3 + tid];
+        if (tid < 2) ls.tc_dead[tid] = 0;
+        if (tid == 0) {
+            umma::mbar_init(&ls.mbar[0], 1);
+            umma::mbar_init(&ls.mbar[1], 1);
+            umma::fence_mbar_init();
+        }
+        if (tid < 32) umma::tmem_alloc(&ls.tmem, 2 * kHid);
+        umma::fence_async_smem();  // W2 is read by the tensor cores
+        umma::fence_before();
+        __syncthreads();
+        umma::fence_after();
     }
     const int ntx = (L.plain.rays.nx + kTileX - 1) / kTileX;
     for (;;) {
@@ -1196,18 +1241,44 @@ __global__ void __launch_bounds__(kThreads, 2) k_shoot_learned(LearnedArgs L)
         if (L.flags[rc])
             shoot_tile<4, 256, false, NRP>(L.plain, bx, by, sm, ts);
         else
-            learned_tile(L, bx, by, sm, ts, ls);
+            learned_tile<NET>(L, bx, by, sm, ts, ls, tc_abuf, phase);
     }
+    if (NET) {
+        // a warpgroup that gave up on a wait drains its MMAs (again bounded) before
+        // the tensor memory is freed
+        if ((tid & 127) == 0 && ls.tc_dead[tid >> 7]) umma::mbar_wait(&ls.mbar[tid >> 7], ls.pending[tid >> 7], kWaitPolls);
+        umma::fence_before();
+        __syncthreads();
+        umma::fence_after();
+        if (tid < 32) umma::tmem_dealloc(ls.tmem, 2 * kHid);
+    }
+}
+
+// Dynamic shared memory for the tensor-core operands, and the largest shared-memory
+// carveout for two CTAs of ~59 KB per SM.
+template <class K>
+static cudaError_t learned_attributes(K kernel)
+{
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    return e;
 }
 
 cudaError_t ff_learned_grid(int *grid)
 {
+    // The persistent grid takes the resident CTAs per SM of the kernel without
+    // tensor-core code (two: registers, launch-bounded to 128 per thread).  The
+    // tensor-core variant has the same register and shared-memory limits (ncu: 2
+    // by registers, 3 by shared memory), though the occupancy query reports one
+    // for it; CTAs beyond those resident only find the shared work queue empty.
     int per_sm = 0, per_sm1 = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shoot_learned<0>, kThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shoot_learned<0, false>, kThreads, 0);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, k_shoot_learned<1>, kThreads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, k_shoot_learned<1, false>, kThreads, 0);
+    if (e != cudaSuccess) return e;
     per_sm = per_sm < per_sm1 ? per_sm : per_sm1;
-    if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
@@ -1215,14 +1286,23 @@ cudaError_t ff_learned_grid(int *grid)
     return cudaSuccess;
 }
 
+template <int NRP>
+static cudaError_t launch_learned(const LearnedArgs &L, unsigned g, cudaStream_t s)
+{
+    if (L.use_net) {
+        cudaError_t e = learned_attributes(k_shoot_learned<NRP, true>);
+        if (e != cudaSuccess) return e;
+        k_shoot_learned<NRP, true><<<g, kThreads, kTcSmem, s>>>(L);
+    } else {
+        k_shoot_learned<NRP, false><<<g, kThreads, 0, s>>>(L);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t ff_shoot_learned(const LearnedArgs &L, int grid, int fma_pairs, cudaStream_t s)
 {
     const int64_t g = L.nitems < grid ? (L.nitems > 0 ? L.nitems : 1) : grid;
-    if (fma_pairs)
-        k_shoot_learned<1><<<(unsigned)g, kThreads, 0, s>>>(L);
-    else
-        k_shoot_learned<0><<<(unsigned)g, kThreads, 0, s>>>(L);
-    return cudaGetLastError();
+    return fma_pairs ? launch_learned<1>(L, (unsigned)g, s) : launch_learned<0>(L, (unsigned)g, s);
 }
 
 }  // namespace mlens

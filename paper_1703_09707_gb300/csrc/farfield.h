@@ -56,6 +56,7 @@ struct LearnedArgs {
     const int *items;          // tile index per work item (fallback tiles first)
     int64_t nitems;
     unsigned long long *counter;
+    int *err;                  // set to 1 if a tensor-core completion wait gave up (results invalid)
 };
 
 // Sample generation for training / validation (counter-based, SplitMix64).

@@ -43,6 +43,7 @@ struct FarState {
     std::vector<int> h_items;      // host copy of the work list
     int *sub_items = nullptr;      // filtered work list for row-restricted calls
     unsigned long long *counter = nullptr;
+    int *d_err = nullptr;  // learned kernel: a tensor-core wait gave up
     int grid = 0;
     mlens_fit_report report{};
 };
@@ -83,7 +84,7 @@ void free_state(FarState *f)
     ffree(f->w1zb), ffree(f->w2b), ffree(f->w2tb), ffree(f->w1ztb), ffree(f->ec), ffree(f->flags);
     ffree(f->vmax_net), ffree(f->vmax_series), ffree(f->vsum), ffree(f->items), ffree(f->counter);
     ffree(f->sub_items);
-    ffree(f->gpart), ffree(f->dzs);
+    ffree(f->gpart), ffree(f->dzs), ffree(f->d_err);
     f->gpart_rows = f->dzs_samples = 0;
     f->ready = false;
 }
@@ -152,6 +153,7 @@ int alloc_state(FarState *f, int64_t nstars)
     FCUDA(dmalloc(&f->vmax_series, sizeof(unsigned) * nrc), "cudaMalloc");
     FCUDA(dmalloc(&f->vsum, sizeof(double) * 2), "cudaMalloc");
     FCUDA(dmalloc(&f->counter, sizeof(unsigned long long)), "cudaMalloc");
+    FCUDA(dmalloc(&f->d_err, sizeof(int)), "cudaMalloc");
     return MLENS_OK;
 }
 
@@ -456,6 +458,7 @@ int mlens_shoot_learned(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid
         FCUDA(cudaMemsetAsync(counts_dev, 0, (size_t)src->nx * src->ny * sizeof(uint32_t), s), "memset(counts)");
     FCUDA(cudaMemsetAsync(ctx->d_stats, 0, 3 * sizeof(unsigned long long), s), "memset(stats)");
     FCUDA(cudaMemsetAsync(f->counter, 0, sizeof(unsigned long long), s), "memset(counter)");
+    FCUDA(cudaMemsetAsync(f->d_err, 0, sizeof(int), s), "memset(err)");
     LearnedArgs L{};
     L.plain.stars = ctx->d_stars;
     L.plain.nstars = ctx->n_pad;
@@ -479,6 +482,7 @@ int mlens_shoot_learned(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid
     L.items = items;
     L.nitems = nitems;
     L.counter = f->counter;
+    L.err = f->d_err;
     // Fallback tiles (each a full plain tile over all stars) run first, each split
     // over a cluster of CTAs so that a few flagged cells do not set the map's
     // time; the persistent learned kernel then takes the learned tiles.
@@ -491,8 +495,11 @@ int mlens_shoot_learned(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid
     if (L.nitems > 0) FCUDA(ff_shoot_learned(L, f->grid, ctx->fma_pairs, s), "learned shoot launch");
     if (stats_host) {
         unsigned long long h[3];
+        int err = 0;
         FCUDA(cudaMemcpyAsync(h, ctx->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s), "memcpy(stats)");
+        FCUDA(cudaMemcpyAsync(&err, f->d_err, sizeof(int), cudaMemcpyDeviceToHost, s), "memcpy(err)");
         FCUDA(cudaStreamSynchronize(s), "sync");
+        if (err) return ffail(MLENS_ERR_CUDA, "a tensor-core completion wait gave up; the map is invalid");
         stats_host->rays_total = (uint64_t)nrows_total;
         stats_host->rays_binned = h[0];
         stats_host->rays_out = h[1];

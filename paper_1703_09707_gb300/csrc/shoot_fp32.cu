@@ -134,6 +134,10 @@ static cudaError_t launch_split_t(const ShootArgs &a, cudaStream_t s)
     // launch gets without opting in for NP = 4
     cudaError_t e0 = cudaFuncSetAttribute(k_shoot_split<NP, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)cfg.dynamicSmemBytes);
+    // two CTAs of ~49 KB per SM: ask for the largest shared-memory carveout
+    if (e0 == cudaSuccess)
+        e0 = cudaFuncSetAttribute(k_shoot_split<NP, SPLIT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared);
     if (e0 != cudaSuccess) return e0;
     cfg.stream = s;
     cfg.attrs = attr;
@@ -175,6 +179,9 @@ static cudaError_t launch_split_list_t(const ShootArgs &a, const int *tiles, int
     cfg.numAttrs = 1;
     cudaError_t e = cudaFuncSetAttribute(k_shoot_split_list<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)cfg.dynamicSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_shoot_split_list<SPLIT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     cfg.gridDim = dim3((unsigned)(ntiles * SPLIT));
     return cudaLaunchKernelEx(&cfg, k_shoot_split_list<SPLIT>, a, tiles);
