@@ -895,8 +895,9 @@ struct LearnSmem {
     int wg_ok[8];         // per warp: the last wait completed
     int tc_dead[2];       // per warpgroup: a wait gave up; no more MMAs
     uint32_t pending[2];  // the phase a dead warpgroup still waits for
-    float w1u[2 * kHid], b2[kHid], w3[2 * kHid], b3[2];
-    float ec[kHid];
+    float4 l1[kHid];  // per hidden unit: {e_c (this tile's cell), W1u[.][0], W1u[.][1], b2}
+    float2 l3[kHid];  // per hidden unit: {W3[0][.], W3[1][.]}
+    float b3[2];
     float coef[kCoefStride];
     float sc;
     int rb[3], re[3];
@@ -956,7 +957,7 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
         ls.sc = L.sc[rc];
     }
     if (tid < kCoefStride) ls.coef[tid] = L.coef[(int64_t)rc * kCoefStride + tid];
-    if (tid < kHid) ls.ec[tid] = L.ec ? L.ec[(int64_t)rc * kHid + tid] : 0.0f;
+    if (tid < kHid) ls.l1[tid].x = L.ec ? L.ec[(int64_t)rc * kHid + tid] : 0.0f;
     __syncthreads();
 
     float2 rx, ry[NP], px[NP], py[NP], Sx[NP], Sy[NP], Cx[NP], Cy[NP];
@@ -1052,9 +1053,9 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int c0 = k8 * 8 + 2 * q;
-                        const float v0 = silu1(ls.ec[c0] + ls.w1u[2 * c0] * ux + ls.w1u[2 * c0 + 1] * uy);
-                        const float v1 =
-                            silu1(ls.ec[c0 + 1] + ls.w1u[2 * c0 + 2] * ux + ls.w1u[2 * c0 + 3] * uy);
+                        const float4 p0 = ls.l1[c0], p1 = ls.l1[c0 + 1];
+                        const float v0 = silu1(p0.x + p0.y * ux + p0.z * uy);
+                        const float v1 = silu1(p1.x + p1.y * ux + p1.z * uy);
                         pk[q] = pack_bf16(v0, v1);
                     }
                     *reinterpret_cast<uint4 *>(abuf + umma::cm_offset(t, k8 * 8)) =
@@ -1087,9 +1088,10 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             const int col = c0 + j;
-                            const float a2 = silu2(__uint_as_float(acc[j]) + ls.b2[col]);
-                            y0 += ls.w3[col] * a2;
-                            y1 += ls.w3[kHid + col] * a2;
+                            const float a2 = silu2(__uint_as_float(acc[j]) + ls.l1[col].w);
+                            const float2 w3 = ls.l3[col];
+                            y0 += w3.x * a2;
+                            y1 += w3.y * a2;
                         }
                     }
                 } else if (t == 0) {
@@ -1210,11 +1212,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_shoot_learned(LearnedArgs L)
     if (NET) {
         for (int i = tid; i < kHid * kHid; i += kThreads)
             *reinterpret_cast<__nv_bfloat16 *>(ls.w2cm + umma::cm_offset(i / kHid, i % kHid)) = L.w2b[i];
-        for (int i = tid; i < 2 * kHid; i += kThreads) {
-            ls.w1u[i] = L.params[oW1u + i];
-            ls.w3[i] = L.params[oW3 + i];
+        if (tid < kHid) {
+            ls.l1[tid].y = L.params[oW1u + 2 * tid];
+            ls.l1[tid].z = L.params[oW1u + 2 * tid + 1];
+            ls.l1[tid].w = L.params[ob2 + tid];
+            ls.l3[tid] = make_float2(L.params[oW3 + tid], L.params[oW3 + kHid + tid]);
         }
-        if (tid < kHid) ls.b2[tid] = L.params[ob2 + tid];
         if (tid < 2) ls.b3[tid] = L.params[ob3 + tid];
         if (tid < 2) ls.tc_dead[tid] = 0;
         if (tid == 0) {

@@ -45,8 +45,14 @@ constexpr bool kLayer2Hw = true;
 __device__ __forceinline__ float sigm_hw(float v) { return __fmaf_rn(0.5f, tanh_hw(0.5f * v), 0.5f); }
 __device__ __forceinline__ float sigm_acc(float v) { return 0.5f * (1.0f + tanhf(0.5f * v)); }
 __device__ __forceinline__ float sigm2(float v) { return kLayer2Hw ? sigm_hw(v) : sigm_acc(v); }
-__device__ __forceinline__ float silu1(float v) { return v * sigm_hw(v); }
-__device__ __forceinline__ float silu2(float v) { return v * sigm2(v); }
+// v sigma(v) = h + h tanh(h) with h = v / 2: three instructions with the hardware tanh
+__device__ __forceinline__ float silu_hw(float v)
+{
+    const float h = 0.5f * v;
+    return __fmaf_rn(h, tanh_hw(h), h);
+}
+__device__ __forceinline__ float silu1(float v) { return silu_hw(v); }
+__device__ __forceinline__ float silu2(float v) { return kLayer2Hw ? silu_hw(v) : v * sigm_acc(v); }
 __device__ __forceinline__ float dsilu1(float v)
 {
     const float s = sigm_hw(v);
