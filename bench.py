@@ -276,7 +276,7 @@ def measured_hbm_gbs():
 def bench_binning(M, torch, steps: int, warmup: int, flush):
     """The binning step alone on the paper-shaped workload: the 8192^2 float-pair beta
     records of one map (1.07 GB, above L2) binned into the 1024^2 map by the standalone
-    kernel in grid order (64 x 32 ray blocks per CTA) and in flat order (2048
+    kernel in grid order (64 x 64 ray blocks per CTA) and in flat order (4096
     consecutive records per CTA), and the fused epilogue's cost: the same grid shot
     through a star-free field (ray generation, the smooth term, beta and binning)."""
     wl = W.config("paper")

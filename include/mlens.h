@@ -199,7 +199,7 @@ int mlens_bin(const void *beta_dev, int64_t n, const mlens_grid *src, uint32_t *
  * rays->nx * rays->ny records in the row-major order mlens_shoot_beta writes
  * (record j * nx + i is ray (i, j); only nx and ny of `rays` are used, and they
  * are checked like a shooting grid's).  The map is the same as mlens_bin's on
- * the same records; the kernel bins 64 x 32 blocks of neighbouring rays per CTA,
+ * the same records; the kernel bins 64 x 64 blocks of neighbouring rays per CTA,
  * which keeps most increments in its shared-memory window.  Stats count all
  * nx * ny records.
  */

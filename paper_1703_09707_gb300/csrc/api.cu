@@ -98,6 +98,10 @@ AxisPair make_axis(double x0, double x1, int n)
     a.x0l = (float)(x0 - (double)a.x0h);
     a.sh = (float)s;
     a.sl = (float)(s - (double)a.sh);
+    a.sh2 = 2.0f * std::fabs(a.sh);
+    const double tq = 2.0 * std::fabs((double)a.x0l) * std::fabs((double)a.sh) + 0x1p-100;
+    a.tq = (float)tq;
+    if ((double)a.tq < tq) a.tq = std::nextafter(a.tq, INFINITY);
     a.n = n;
     return a;
 }

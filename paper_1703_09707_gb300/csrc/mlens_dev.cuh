@@ -56,25 +56,38 @@ __device__ __forceinline__ int pair_axis_exact(float bh, float bl, const AxisPai
 
 // The same pixel, usually without the pair arithmetic.  u = fl(fl(bh - x0h) sh)
 // differs from the pair value P = uh + ul that pair_axis_exact floors by at most
-//     |u - P| <= 2^-23 |u| (two roundings) + |d sl| + (|bl| + |x0l|)(|sh| + |sl|)
-//                + 2^-23 (|bl| + |x0l|) |s| + 2^-45 |u| (the pair's own error),
-// d = bh - x0h.  del below is at least 1.5x that bound even after its own
-// rounding and the rounding of u -/+ del (|sl| <= 2^-24 |sh| by construction),
-// plus 2^-100 so that del > 0 even where the products underflow.  If no pixel
-// edge lies in [u - del, u + del], floor(P) = floor(u): the result equals
+//     B = 2^-23 |u| (two roundings) + |d sl| + (|bl| + |x0l|)(|sh| + |sl|)
+//         + 2^-23 (|bl| + |x0l|) |s| + 2^-45 |u| (the pair's own error),
+// d = bh - x0h.  Since |sl| <= 2^-24 |sh| (sl is the rounding error of sh) and
+// |d sh| <= (1 + 2^-23) |u|, the second term is at most 2^-24 (1 + 2^-23) |u|, so
+//     B < 2^-22 |u| + (1 + 2^-22) (|bl| + |x0l|) |sh|.
+// The quick test widens u by del = 2^-21 |u| + 2 |bl| |sh| + tq, with tq =
+// 2 |x0l| |sh| + 2^-100 rounded up (so del > 0 where the products underflow):
+// about twice B, which leaves room for del's own two roundings and those of
+// u -/+ del (each under 2^-23 |u| + 2^-23 del).  If no pixel edge lies in
+// [u - del, u + del], floor(P) = floor(u) and the result equals
 // pair_axis_exact's bit for bit; otherwise (a fraction ~ 2 del of the rays, and
-// every non-finite u) the exact rule runs.
-__device__ __forceinline__ int pair_axis(float bh, float bl, const AxisPair &A)
+// every non-finite component: u or del is then inf or NaN) the exact rule runs.
+//
+// The quick decision alone: true, with p = pixel or -1 (outside [0, n)), when
+// no pixel edge lies within del of u; false when the exact rule must run.
+__device__ __forceinline__ bool pair_axis_quick(float bh, float bl, const AxisPair &A, int &p)
 {
     const float d = __fsub_rn(bh, A.x0h);
     const float u = __fmul_rn(d, A.sh);
-    const float tail = __fmul_rn(__fadd_rn(fabsf(bl), fabsf(A.x0l)), 2.0f * fabsf(A.sh));
-    const float del = __fmaf_rn(0x1p-22f, fabsf(u), __fmaf_rn(fabsf(d), 2.0f * fabsf(A.sl), __fadd_rn(tail, 0x1p-100f)));
+    const float del = __fmaf_rn(fabsf(u), 0x1p-21f, __fmaf_rn(fabsf(bl), A.sh2, A.tq));
+    // floor(u + del) == lo  <=>  u + del < lo + 1 (u + del >= lo; where lo + 1
+    // rounds to lo the test fails and the exact rule decides; NaN fails too)
     const float lo = floorf(__fsub_rn(u, del));
-    if (lo == floorf(__fadd_rn(u, del))) {  // false for NaN
-        if (lo < 0.0f || lo >= (float)A.n) return -1;
-        return (int)lo;
-    }
+    if (!(__fadd_rn(u, del) < __fadd_rn(lo, 1.0f))) return false;
+    p = (lo < 0.0f || lo >= (float)A.n) ? -1 : (int)lo;
+    return true;
+}
+
+__device__ __forceinline__ int pair_axis(float bh, float bl, const AxisPair &A)
+{
+    int p;
+    if (pair_axis_quick(bh, bl, A, p)) return p;
     return pair_axis_exact(bh, bl, A);
 }
 

@@ -21,6 +21,8 @@ constexpr float kPadCoord = 1.0e15f;
 // s = n / (x1 - x0) = sh + sl, each split from its double value.
 struct AxisPair {
     float x0h, x0l, sh, sl;
+    float sh2;  // 2 |sh|
+    float tq;   // 2 |x0l| |sh| + 2^-100, rounded up: the constant part of the quick test's bound
     int n;
 };
 

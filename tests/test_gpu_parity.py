@@ -211,15 +211,10 @@ def test_standalone_bin_matches_fused_map():
     ctx.close()
 
 
-@pytest.mark.parametrize("nx,x0,w", [(1024, -10.0, 20.0), (4096, 3.25, 0.1), (37, -120.5, 300.0), (32768, -4.0, 8.0)])
-def test_bin_records_on_pixel_edges(nx, x0, w):
-    """Records placed on pixel edges (as float pairs, and hi parts a few ulps off an
-    edge, and lo parts that straddle it): the kernels decide most pixels from the hi
-    parts and fall back to the pair rule near edges; every pixel must equal the
-    float-pair rule's (re-binned on the CPU)."""
-    rng = np.random.default_rng(nx)
-    src = W.Grid(x0, x0 + w, x0, x0 + w, nx, nx)
-    k = 1 << 20
+def edge_records(rng, k, x0, w, nx):
+    """k float-pair records {x_hi, y_hi, x_lo, y_lo} on and near the pixel edges of an
+    nx-pixel axis over [x0, x0 + w]: exact edges as pairs, hi parts a few ulps off an
+    edge, lo parts that straddle it, and uniform positions in and around the map."""
     f32 = np.float32
     i = rng.integers(-2, nx + 2, k)
     edge = x0 + i * (w / nx)
@@ -231,7 +226,19 @@ def test_bin_records_on_pixel_edges(nx, x0, w):
     bl = np.where(mode == 2, (rng.uniform(-0.5, 0.5, k) * ulp).astype(f32), bl).astype(f32)
     bh = np.where(mode == 3, rng.uniform(x0 - 0.1 * w, x0 + 1.1 * w, k).astype(f32), bh).astype(f32)
     perm = rng.permutation(k)
-    b4 = np.stack([bh, bh[perm], bl, bl[perm]], 1).astype(f32)
+    return np.stack([bh, bh[perm], bl, bl[perm]], 1).astype(f32)
+
+
+@pytest.mark.parametrize("nx,x0,w", [(1024, -10.0, 20.0), (4096, 3.25, 0.1), (37, -120.5, 300.0), (32768, -4.0, 8.0)])
+def test_bin_records_on_pixel_edges(nx, x0, w):
+    """Records placed on pixel edges (as float pairs, and hi parts a few ulps off an
+    edge, and lo parts that straddle it): the kernels decide most pixels from the hi
+    parts and fall back to the pair rule near edges; every pixel must equal the
+    float-pair rule's (re-binned on the CPU)."""
+    rng = np.random.default_rng(nx)
+    src = W.Grid(x0, x0 + w, x0, x0 + w, nx, nx)
+    k = 1 << 20
+    b4 = edge_records(rng, k, x0, w, nx)
     c_ref, st_ref = oracle.rebin_pair(b4, src)
     beta = torch.from_numpy(b4.reshape(-1)).cuda()
     counts = torch.empty(src.n, dtype=torch.int32, device="cuda")
@@ -244,8 +251,44 @@ def test_bin_records_on_pixel_edges(nx, x0, w):
     assert np.array_equal(counts.cpu().numpy().view(np.uint32).reshape(src.ny, src.nx), c_ref) and st == st_ref
 
 
+@pytest.mark.parametrize("order", ["flat", "grid"])
+def test_bin_many_blocks_ragged_and_non_finite(order):
+    """About 1200 blocks of 4096 records, more than the GPU holds at once; the record
+    count (flat) or row count (grid) leaves the last blocks' second round empty, and
+    the grid's width is ragged.  Non-finite records are mixed in.  Counts and stats
+    must equal the CPU re-binning."""
+    rng = np.random.default_rng(20 if order == "flat" else 21)
+    nx, x0, w = 700, -3.0, 6.0
+    src = W.Grid(x0, x0 + w, x0, x0 + w, nx, nx)
+    if order == "flat":
+        k = 1200 * 4096 + 777  # 777 < 2048: the last block's second round is empty
+    else:
+        rays = W.Grid(0.0, 1.0, 0.0, 1.0, 1000, 4930)  # 1000 % 64 = 40; 4930 % 64 = 2: second rounds of the last block row empty
+        k = rays.n
+    b4 = edge_records(rng, k, x0, w, nx)
+    bad = rng.choice(k, 5000, replace=False)
+    b4[bad[:2000], rng.integers(0, 4, 2000)] = np.nan
+    b4[bad[2000:], rng.integers(0, 4, 3000)] = np.inf
+    c_ref, st_ref = oracle.rebin_pair(b4, src)
+    assert st_ref["rays_nan"] == 5000
+    beta = torch.from_numpy(b4.reshape(-1)).cuda()
+    counts = torch.empty(src.n, dtype=torch.int32, device="cuda")
+    if order == "flat":
+        st = M.mlens_bin(beta, k, src, counts, stats=True)
+    else:
+        st = M.mlens_bin_grid(beta, rays, src, counts, stats=True)
+    assert np.array_equal(counts.cpu().numpy().view(np.uint32).reshape(src.ny, src.nx), c_ref) and st == st_ref
+    # once more on top of the map
+    if order == "flat":
+        M.mlens_bin(beta, k, src, counts, flags=M.MLENS_ACCUMULATE)
+    else:
+        M.mlens_bin_grid(beta, rays, src, counts, flags=M.MLENS_ACCUMULATE)
+    assert np.array_equal(counts.cpu().numpy().view(np.uint32).reshape(src.ny, src.nx), 2 * c_ref)
+
+
 def test_grid_ordered_bin_on_ragged_grid():
-    """1000 x 1000 rays: neither dimension is a multiple of the 64 x 32 binning block."""
+    """1000 x 1000 rays: neither dimension is a multiple of the 64 x 64 binning block
+    (nor of its 32-row stages)."""
     wl = W.config("tiny")
     f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
     assert rays.nx % 64 and rays.ny % 32
