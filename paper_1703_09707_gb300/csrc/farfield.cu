@@ -323,63 +323,65 @@ cudaError_t ff_init_params(float *params, float *z, int nrc, uint64_t seed, cuda
     return cudaGetLastError();
 }
 
-__global__ void k_prep_bf16(const float *p, __nv_bfloat16 *w1zb, __nv_bfloat16 *w2b, __nv_bfloat16 *w2tb,
-                            __nv_bfloat16 *w1ztb)
+__global__ void k_prep_bf16(const float *p, __nv_bfloat16 *w1zb, __nv_bfloat16 *w2b)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < kHid * kHid) {
-        const int o = i / kHid, k = i % kHid;
-        const __nv_bfloat16 v = to_bf16(p[oW2 + i]);
-        w2b[i] = v;
-        w2tb[k * kHid + o] = v;
-    }
-    if (i < kHid * kLat) {
-        const int o = i / kLat, k = i % kLat;
-        const __nv_bfloat16 v = to_bf16(p[oW1z + i]);
-        w1zb[i] = v;
-        w1ztb[k * kHid + o] = v;
-    }
+    if (i < kHid * kHid) w2b[i] = to_bf16(p[oW2 + i]);
+    if (i < kHid * kLat) w1zb[i] = to_bf16(p[oW1z + i]);
 }
 
-cudaError_t ff_prep_bf16(const float *params, __nv_bfloat16 *w1zb, __nv_bfloat16 *w2b, __nv_bfloat16 *w2tb,
-                         __nv_bfloat16 *w1ztb, cudaStream_t s)
+cudaError_t ff_prep_bf16(const float *params, __nv_bfloat16 *w1zb, __nv_bfloat16 *w2b, cudaStream_t s)
 {
-    k_prep_bf16<<<(kHid * kHid + 255) / 256, 256, 0, s>>>(params, w1zb, w2b, w2tb, w1ztb);
+    k_prep_bf16<<<(kHid * kHid + 255) / 256, 256, 0, s>>>(params, w1zb, w2b);
     return cudaGetLastError();
 }
 
 // ===================================================== training kernel
-// Shared-memory plan (BF16 unless noted), leading dimensions padded by 8.
-constexpr int kLdZ = kLat + 8;   // 40
-constexpr int kLdH = kHid + 8;   // 72
-constexpr int kSampW = 16;       // samples per warp
-constexpr int kSampC = 128;      // samples per CTA
-constexpr int kLdT = kSampC + 8; // 136
+constexpr int kWaitPolls = 1 << 20;  // bound on a tensor-core completion wait
+constexpr int kSampC = 128;          // samples per CTA = tensor-memory lanes of one accumulator
+constexpr int kGP = kParams + 2;     // gpart row: the parameters' gradients, then the loss
 
-constexpr int kGP = kParams + 2;  // gpart row: the parameters' gradients, then the loss
-
-struct TrainSmemLayout {
-    static constexpr int W1z = 0;                          // [64][40]
-    static constexpr int W2 = W1z + kHid * kLdZ;           // [64][72] (n=out, k=in)
-    static constexpr int W2T = W2 + kHid * kLdH;           // [64][72] (n=in, k=out)
-    static constexpr int W1zT = W2T + kHid * kLdH;         // [32][72] (n=in, k=out)
-    static constexpr int Warp = W1zT + kLat * kLdH;        // per warp: Z[16][40], A1, DH2, DH1 [16][72]
-    static constexpr int WarpSize = kSampW * kLdZ + 3 * kSampW * kLdH;
-    static constexpr int A1T = Warp + 8 * WarpSize;        // [64][136] (in, sample)
-    static constexpr int DH2T = A1T + kHid * kLdT;         // [64][136] (out, sample)
-    static constexpr int ZT = DH2T + kHid * kLdT;          // [32][136]
-    static constexpr int DH1T = ZT + kLat * kLdT;          // [64][136]
-    static constexpr int EndBf = DH1T + kHid * kLdT;
-    // FP32 block after the BF16 block
-    static constexpr int fW1u = 0, fb1 = 128, fb2 = 192, fW3 = 256, fb3 = 384, fdb1 = 388, fdb2 = 452;
-    static constexpr int fWarp = 516;  // per warp: u[16][2], t[16][2], sc[16]
-    static constexpr int fWarpSize = 80;
-    // per warp gradient slots, summed over the warps in a fixed order:
-    // W3 [128] at 0, b3 [2] at 128, W1u [128] at 130, b1 [64] at 258, b2 [64] at 322, loss at 386
-    static constexpr int fWG = fWarp + 8 * fWarpSize;
-    static constexpr int kWG = 388;
-    static constexpr int EndF = fWG + 8 * kWG;
-    static constexpr size_t bytes = (size_t)EndBf * 2 + (size_t)EndF * 4 + 8 * 16 * 4 * 2;
+// Shared memory of the training kernel (byte offsets).  Every tensor-core
+// operand is K-major BF16 in 8-row x 16-byte core matrices: element (r, k) of an
+// operand with K columns at tc_off(r, k, K); descriptors take 128 bytes between
+// K-adjacent core matrices and 16 K bytes between 8-row groups.
+__host__ __device__ constexpr int tc_off(int r, int k, int K)
+{
+    return (r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+struct TrainTc {
+    // B operands (N x K): the weights
+    static constexpr int W1z = 0;                        // [64 out][32 in]  layer 1, latent block
+    static constexpr int W2 = W1z + kHid * kLat * 2;     // [64 out][64 in]  layer 2
+    static constexpr int W2T = W2 + kHid * kHid * 2;     // [64 in][64 out]  da1 = dh2 W2
+    static constexpr int W1zT = W2T + kHid * kHid * 2;   // [32 in][64 out]  dz = dh1 W1z
+    // A operands (M = 128 samples x K)
+    static constexpr int Z = W1zT + kLat * kHid * 2;     // [128][32]
+    static constexpr int A1 = Z + kSampC * kLat * 2;     // [128][64]
+    static constexpr int DH2 = A1 + kSampC * kHid * 2;   // [128][64]
+    static constexpr int DH1 = DH2 + kSampC * kHid * 2;  // [128][64]
+    // weight gradients: A = [dh2^T; dh1^T] (128 units x 128 samples), B = a1^T, z^T
+    static constexpr int ST = DH1 + kSampC * kHid * 2;   // [128][128]
+    static constexpr int A1T = ST + 128 * kSampC * 2;    // [64][128]
+    static constexpr int ZT = A1T + kHid * kSampC * 2;   // [32][128]
+    static constexpr int EndOps = ZT + kLat * kSampC * 2;
+    // FP32 / int region
+    static constexpr int W1u = EndOps;                   // [64][2]
+    static constexpr int b1 = W1u + 2 * kHid * 4;
+    static constexpr int b2 = b1 + kHid * 4;
+    static constexpr int W3 = b2 + kHid * 4;             // [2][64]
+    static constexpr int b3 = W3 + 2 * kHid * 4;         // [2], padded
+    static constexpr int U = b3 + 16;                    // [128][2] positions
+    static constexpr int T = U + 2 * kSampC * 4;         // [128][2] targets
+    static constexpr int SV = T + 2 * kSampC * 4;        // [128] s_c |v|^(pe+1)
+    static constexpr int RC = SV + kSampC * 4;           // [128] int cell
+    static constexpr int OK = RC + kSampC * 4;           // [128] int valid
+    static constexpr int YP = OK + kSampC * 4;           // [2 warpgroups][128][2] layer-3 partial sums
+    static constexpr int Slots = YP + 2 * kSampC * 2 * 4;  // [8 warps][6][32] column sums over a warp's samples
+    static constexpr int WS = Slots + 8 * 6 * 32 * 4;    // [8 warps][4]: sum dy0, sum dy1, loss
+    static constexpr int bytes = WS + 8 * 4 * 4;
+    // tensor-memory columns of the six accumulators (all 128 lanes)
+    static constexpr int cH1 = 0, cH2 = 64, cDA1 = 128, cDZ = 192, cDW2 = 256, cDW1z = 320, ncols = 512;
 };
 
 // One training / validation sample: a cell and a uniform position in its ray-covered
@@ -414,44 +416,345 @@ __device__ __forceinline__ void sample_of(const TrainArgs &A, int64_t li, int &r
     vp = powf(vr * vr + vi * vi, 0.5f * (float)(A.pe + 1));
 }
 
+// Warp reduce-scatter of 32 per-lane column vectors: afterwards v[0] of lane j
+// holds the sum over the warp's lanes of column j (fixed order: deterministic).
+__device__ __forceinline__ float warp_colsum(float (&v)[32])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+        const bool up = (lane & step) != 0;
+#pragma unroll
+        for (int i = 0; i < step; ++i) {
+            const float give = up ? v[i] : v[i + step];
+            const float keep = up ? v[i + step] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, give, step);
+        }
+    }
+    return v[0];
+}
+
+__device__ __forceinline__ void st_bf16(unsigned char *S, int off, float v)
+{
+    *reinterpret_cast<__nv_bfloat16 *>(S + off) = to_bf16(v);
+}
+
+// Make this thread's shared-memory operand writes visible to the tensor cores and
+// wait for the whole CTA.
+__device__ __forceinline__ void tc_publish()
+{
+    umma::fence_async_smem();
+    umma::fence_before();
+    __syncthreads();
+    umma::fence_after();
+}
+
+// Wait (bounded) for the MMAs committed to *bar; true when every thread saw them
+// complete.
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t &phase)
+{
+    const bool ok = umma::mbar_wait(bar, phase, kWaitPolls);
+    if (__syncthreads_or(!ok)) return false;
+    phase ^= 1u;
+    umma::fence_after();
+    return true;
+}
+
+// 32 accumulator columns c0 .. c0 + 31 of this thread's lane.
+__device__ __forceinline__ void tc_load32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[16];
+    umma::ld16(taddr, r);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+    umma::ld16(taddr + 16, r);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[16 + j] = __uint_as_float(r[j]);
+}
+
+// One thread issues D = sum_k A[:, k] B[:, k]^T over K / 16 MMAs of K = 16.
+__device__ __forceinline__ void tc_gemm(uint32_t d, const unsigned char *A, const unsigned char *B, int K,
+                                        uint32_t idesc)
+{
+    const uint32_t a = umma::smem_addr(A), b = umma::smem_addr(B), sbo = (uint32_t)(K * 16);
+    for (int ks = 0; ks < K / 16; ++ks)
+        umma::mma_bf16(d, umma::desc(a + ks * 256, 128, sbo), umma::desc(b + ks * 256, 128, sbo), idesc,
+                       ks > 0 ? 1u : 0u);
+}
+
+// The step for the CTA's 128 samples; false if a tensor-core wait gave up (the
+// caller drains and reports).  Thread (warpgroup wg, s = tid % 128) owns sample s
+// and, of each 64-wide accumulator, the columns 32 wg .. 32 wg + 31 (tensor-memory
+// lane s is readable by warp s / 32 of either warpgroup).
+__device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S, uint64_t *bar, uint32_t tm,
+                                           uint32_t &phase)
+{
+    using L = TrainTc;
+    float *F = reinterpret_cast<float *>(S);  // byte offsets / 4 below
+    int *I = reinterpret_cast<int *>(S);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, wg = warp >> 2, s = tid & 127;
+    const int c0 = 32 * wg;  // this thread's first column of a 64-wide accumulator
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    const int64_t cbase = (int64_t)blockIdx.x * kSampC;
+    const bool expl = A.zin != nullptr;
+    float *Slot = F + L::Slots / 4 + warp * 6 * 32;
+
+    // ---- latents: thread (wg, s) takes columns 16 wg .. 16 wg + 15 of z_s
+    {
+        const int rc = I[L::RC / 4 + s];
+        const bool ok = I[L::OK / 4 + s] != 0;
+        float zv[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int k = 16 * wg + j;
+            zv[j] = ok ? (expl ? A.zin[(cbase + s) * kLat + k] : A.z[(int64_t)rc * kLat + k]) : 0.0f;
+            st_bf16(S, L::ZT + tc_off(k, s, kSampC), zv[j]);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            *reinterpret_cast<uint4 *>(S + L::Z + tc_off(s, 16 * wg + 8 * h, kLat)) =
+                make_uint4(pack_bf16(zv[8 * h], zv[8 * h + 1]), pack_bf16(zv[8 * h + 2], zv[8 * h + 3]),
+                           pack_bf16(zv[8 * h + 4], zv[8 * h + 5]), pack_bf16(zv[8 * h + 6], zv[8 * h + 7]));
+    }
+    // ---- layer 1, latent block: H1 = Z W1z^T (M 128, N 64, K 32)
+    tc_publish();
+    if (tid == 0) {
+        tc_gemm(tm + L::cH1, S + L::Z, S + L::W1z, kLat, umma::idesc_bf16(128, kHid));
+        umma::commit(bar);
+    }
+    if (!tc_wait(bar, phase)) return false;
+    const float ux = F[L::U / 4 + 2 * s], uy = F[L::U / 4 + 2 * s + 1];
+    float h1[32];
+    tc_load32(tm + lane_base + L::cH1 + c0, h1);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const int c = c0 + j;
+        h1[j] = h1[j] + F[L::W1u / 4 + 2 * c] * ux + F[L::W1u / 4 + 2 * c + 1] * uy + F[L::b1 / 4 + c];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float a[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            a[j] = silu1(h1[8 * q + j]);
+            st_bf16(S, L::A1T + tc_off(c0 + 8 * q + j, s, kSampC), a[j]);
+        }
+        *reinterpret_cast<uint4 *>(S + L::A1 + tc_off(s, c0 + 8 * q, kHid)) =
+            make_uint4(pack_bf16(a[0], a[1]), pack_bf16(a[2], a[3]), pack_bf16(a[4], a[5]), pack_bf16(a[6], a[7]));
+    }
+    // ---- layer 2: H2 = A1 W2^T (M 128, N 64, K 64); layer 3 in FP32
+    tc_publish();
+    if (tid == 0) {
+        tc_gemm(tm + L::cH2, S + L::A1, S + L::W2, kHid, umma::idesc_bf16(128, kHid));
+        umma::commit(bar);
+    }
+    if (!tc_wait(bar, phase)) return false;
+    float h2[32];
+    tc_load32(tm + lane_base + L::cH2 + c0, h2);
+    {
+        float y0 = 0.0f, y1 = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int c = c0 + j;
+            h2[j] += F[L::b2 / 4 + c];
+            const float a2 = silu2(h2[j]);
+            y0 += F[L::W3 / 4 + c] * a2;
+            y1 += F[L::W3 / 4 + kHid + c] * a2;
+        }
+        F[L::YP / 4 + (wg * kSampC + s) * 2] = y0;
+        F[L::YP / 4 + (wg * kSampC + s) * 2 + 1] = y1;
+    }
+    __syncthreads();
+    // ---- outputs, loss, validation (both warpgroups form the same y and dy)
+    const bool valid = I[L::OK / 4 + s] != 0;
+    const float yv0 = F[L::YP / 4 + 2 * s] + F[L::YP / 4 + (kSampC + s) * 2] + F[L::b3 / 4];
+    const float yv1 = F[L::YP / 4 + 2 * s + 1] + F[L::YP / 4 + (kSampC + s) * 2 + 1] + F[L::b3 / 4 + 1];
+    const float ex = yv0 - F[L::T / 4 + 2 * s], ey = yv1 - F[L::T / 4 + 2 * s + 1];
+    const float dy0 = valid ? 2.0f * ex * A.inv_batch : 0.0f, dy1 = valid ? 2.0f * ey * A.inv_batch : 0.0f;
+    float lsum = valid && wg == 0 ? ex * ex + ey * ey : 0.0f;
+    if (valid && wg == 0) {
+        if (A.yout) {
+            A.yout[2 * (cbase + s)] = yv0;
+            A.yout[2 * (cbase + s) + 1] = yv1;
+        }
+        if (!A.backward && A.val_max_net) {
+            const float scv = F[L::SV / 4 + s];
+            const float en = scv * sqrtf(ex * ex + ey * ey);
+            const float tx = F[L::T / 4 + 2 * s], ty = F[L::T / 4 + 2 * s + 1];
+            const float es = scv * sqrtf(tx * tx + ty * ty);
+            const int rc = I[L::RC / 4 + s];
+            atomicMax(&A.val_max_net[rc], __float_as_uint(en));
+            atomicMax(&A.val_max_series[rc], __float_as_uint(es));
+            atomicAdd(&A.val_sum[0], (double)en);
+            atomicAdd(&A.val_sum[1], (double)es);
+        }
+    }
+    for (int o = 16; o; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (!A.backward) {
+        if (lane == 0 && wg == 0 && A.loss) atomicAdd(A.loss, lsum * A.inv_batch);
+        return true;
+    }
+    {
+        float d0 = wg == 0 ? dy0 : 0.0f, d1 = wg == 0 ? dy1 : 0.0f;
+        for (int o = 16; o; o >>= 1) {
+            d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+            d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+        }
+        if (lane == 0) {
+            F[L::WS / 4 + warp * 4] = d0;
+            F[L::WS / 4 + warp * 4 + 1] = d1;
+            F[L::WS / 4 + warp * 4 + 2] = lsum;
+        }
+    }
+    // ---- dh2 = (dy W3) silu'(h2); FP32 column sums for b2 and W3
+    {
+        float v[32], w0[32], w1[32];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float d[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int jj = 8 * q + j, c = c0 + jj;
+                const float da2 = dy0 * F[L::W3 / 4 + c] + dy1 * F[L::W3 / 4 + kHid + c];
+                d[j] = da2 * dsilu2(h2[jj]);
+                v[jj] = d[j];
+                const float a2 = silu2(h2[jj]);
+                w0[jj] = dy0 * a2;
+                w1[jj] = dy1 * a2;
+                st_bf16(S, L::ST + tc_off(c, s, kSampC), d[j]);
+            }
+            *reinterpret_cast<uint4 *>(S + L::DH2 + tc_off(s, c0 + 8 * q, kHid)) =
+                make_uint4(pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]), pack_bf16(d[6], d[7]));
+        }
+        Slot[0 * 32 + lane] = warp_colsum(v);
+        Slot[1 * 32 + lane] = warp_colsum(w0);
+        Slot[2 * 32 + lane] = warp_colsum(w1);
+    }
+    // ---- da1 = dh2 W2 (M 128, N 64, K 64); dh1 = da1 silu'(h1); sums for b1 and W1u
+    tc_publish();
+    if (tid == 0) {
+        tc_gemm(tm + L::cDA1, S + L::DH2, S + L::W2T, kHid, umma::idesc_bf16(128, kHid));
+        umma::commit(bar);
+    }
+    if (!tc_wait(bar, phase)) return false;
+    {
+        float da1[32];
+        tc_load32(tm + lane_base + L::cDA1 + c0, da1);
+        float g0[32], g1[32];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float d[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int jj = 8 * q + j, c = c0 + jj;
+                d[j] = da1[jj] * dsilu1(h1[jj]);
+                da1[jj] = d[j];
+                g0[jj] = d[j] * ux;
+                g1[jj] = d[j] * uy;
+                st_bf16(S, L::ST + tc_off(kHid + c, s, kSampC), d[j]);
+            }
+            *reinterpret_cast<uint4 *>(S + L::DH1 + tc_off(s, c0 + 8 * q, kHid)) =
+                make_uint4(pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]), pack_bf16(d[6], d[7]));
+        }
+        Slot[3 * 32 + lane] = warp_colsum(da1);
+        Slot[4 * 32 + lane] = warp_colsum(g0);
+        Slot[5 * 32 + lane] = warp_colsum(g1);
+    }
+    // ---- dz = dh1 W1z (N 32, K 64); dW2 = dh2^T a1 and dW1z = dh1^T z from the
+    // stacked [dh2^T; dh1^T] (M 128 units, K 128 samples)
+    tc_publish();
+    if (tid == 0) {
+        tc_gemm(tm + L::cDZ, S + L::DH1, S + L::W1zT, kHid, umma::idesc_bf16(128, kLat));
+        tc_gemm(tm + L::cDW2, S + L::ST, S + L::A1T, kSampC, umma::idesc_bf16(128, kHid));
+        tc_gemm(tm + L::cDW1z, S + L::ST, S + L::ZT, kSampC, umma::idesc_bf16(128, kLat));
+        umma::commit(bar);
+    }
+    if (!tc_wait(bar, phase)) return false;
+    {
+        uint32_t r[16];
+        umma::ld16(tm + lane_base + L::cDZ + 16 * wg, r);
+        if (valid) {
+            float *dst = expl ? A.dzout : A.dzs;
+            if (dst)
+#pragma unroll
+                for (int j = 0; j < 16; ++j) dst[(cbase + s) * kLat + 16 * wg + j] = __uint_as_float(r[j]);
+        }
+    }
+    float *gp = A.gpart + (int64_t)blockIdx.x * kGP;
+    if (s < kHid) {  // lanes 0..63: dW2[out = s][in]
+        float v[32];
+        tc_load32(tm + lane_base + L::cDW2 + c0, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) gp[oW2 + s * kHid + c0 + j] = v[j];
+    } else {  // lanes 64..127: dW1z[out = s - 64][in]
+        uint32_t r[16];
+        umma::ld16(tm + lane_base + L::cDW1z + 16 * wg, r);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) gp[oW1z + (s - kHid) * kLat + 16 * wg + j] = __uint_as_float(r[j]);
+    }
+    __syncthreads();
+    // ---- the FP32 column sums: warps 4 wg .. 4 wg + 3 cover all samples of columns 32 wg ..
+    for (int e = tid; e < 6 * kHid; e += 256) {
+        const int q = e / kHid, c = e % kHid, w0 = 4 * (c / 32);
+        float acc = 0.0f;
+        for (int w = w0; w < w0 + 4; ++w) acc += F[L::Slots / 4 + (w * 6 + q) * 32 + (c % 32)];
+        const int dst = q == 0 ? ob2 + c : q == 1 ? oW3 + c : q == 2 ? oW3 + kHid + c
+                      : q == 3 ? ob1 + c : q == 4 ? oW1u + 2 * c : oW1u + 2 * c + 1;
+        gp[dst] = acc;
+    }
+    if (tid < 3) {
+        float acc = 0.0f;
+        for (int w = 0; w < 4; ++w) acc += F[L::WS / 4 + w * 4 + tid];
+        gp[tid < 2 ? ob3 + tid : kParams] = tid < 2 ? acc : acc * A.inv_batch;
+    }
+    return true;
+}
+
+// Training (backward = 1) or validation step over kSampC samples per CTA: the
+// layer-1 latent block, layer 2 and the four backward products on the
+// fifth-generation tensor cores (tcgen05.mma, BF16 operands in shared memory,
+// FP32 accumulators in tensor memory, mbarrier completion with bounded waits);
+// position block, biases, layer 3 and all column sums in FP32.
 __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    using L = TrainSmemLayout;
-    __nv_bfloat16 *sb = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
-    float *sf = reinterpret_cast<float *>(smem_raw + (size_t)L::EndBf * 2);
-    int *si = reinterpret_cast<int *>(sf + L::EndF);  // per warp: rc[16], valid[16]
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem;
+    using L = TrainTc;
+    float *F = reinterpret_cast<float *>(tsm);
+    int *I = reinterpret_cast<int *>(tsm);
+    const int tid = threadIdx.x;
 
-    // ---- weights into shared memory
-    for (int i = tid; i < kHid * kLat; i += 256) sb[L::W1z + (i / kLat) * kLdZ + i % kLat] = A.w1zb[i];
+    // ---- weights: BF16 operands in core-matrix layout, FP32 small parameters
+    for (int i = tid; i < kHid * kLat; i += 256) {
+        const int o = i / kLat, k = i % kLat;
+        const __nv_bfloat16 w = A.w1zb[i];
+        *reinterpret_cast<__nv_bfloat16 *>(tsm + L::W1z + tc_off(o, k, kLat)) = w;
+        *reinterpret_cast<__nv_bfloat16 *>(tsm + L::W1zT + tc_off(k, o, kHid)) = w;
+    }
     for (int i = tid; i < kHid * kHid; i += 256) {
-        sb[L::W2 + (i / kHid) * kLdH + i % kHid] = A.w2b[i];
-        sb[L::W2T + (i / kHid) * kLdH + i % kHid] = A.w2tb[i];
+        const int o = i / kHid, k = i % kHid;
+        const __nv_bfloat16 w = A.w2b[i];
+        *reinterpret_cast<__nv_bfloat16 *>(tsm + L::W2 + tc_off(o, k, kHid)) = w;
+        *reinterpret_cast<__nv_bfloat16 *>(tsm + L::W2T + tc_off(k, o, kHid)) = w;
     }
-    for (int i = tid; i < kLat * kHid; i += 256) sb[L::W1zT + (i / kHid) * kLdH + i % kHid] = A.w1ztb[i];
-    for (int i = tid; i < 128; i += 256) {
-        sf[L::fW1u + i] = A.params[oW1u + i];
-        sf[L::fW3 + i] = A.params[oW3 + i];
+    if (tid < 2 * kHid) {
+        F[L::W1u / 4 + tid] = A.params[oW1u + tid];
+        F[L::W3 / 4 + tid] = A.params[oW3 + tid];
     }
-    if (tid < 64) {
-        sf[L::fb1 + tid] = A.params[ob1 + tid];
-        sf[L::fb2 + tid] = A.params[ob2 + tid];
+    if (tid < kHid) {
+        F[L::b1 / 4 + tid] = A.params[ob1 + tid];
+        F[L::b2 / 4 + tid] = A.params[ob2 + tid];
     }
-    if (tid < 2) sf[L::fb3 + tid] = A.params[ob3 + tid];
-
-    // ---- samples of this warp
-    float *wu = sf + L::fWarp + warp * L::fWarpSize;  // u[16][2] at 0, t[16][2] at 32, s_c |v|^(pe+1) [16] at 64
-    int *wrc = si + warp * 32;                        // rc[16], valid[16]
-    const int64_t cbase = (int64_t)blockIdx.x * kSampC + warp * kSampW;
-    const bool expl = A.zin != nullptr;
-    if (lane < kSampW) {
-        const int64_t li = cbase + lane;
+    if (tid < 2) F[L::b3 / 4 + tid] = A.params[ob3 + tid];
+    // ---- samples
+    if (tid < kSampC) {
+        const int64_t li = (int64_t)blockIdx.x * kSampC + tid;
         const bool valid = li < A.spec.count;
         int rc = 0;
         float ux = 0.f, uy = 0.f, tx = 0.f, ty = 0.f, scv = 1.0f, vp = 1.0f;
         if (valid) {
-            if (expl) {
+            if (A.zin) {
                 ux = A.uin[2 * li];
                 uy = A.uin[2 * li + 1];
                 tx = A.tin ? A.tin[2 * li] : 0.f;
@@ -460,332 +763,43 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
                 sample_of(A, li, rc, ux, uy, tx, ty, scv, vp);
             }
         }
-        wu[2 * lane] = ux;
-        wu[2 * lane + 1] = uy;
-        wu[32 + 2 * lane] = tx;
-        wu[32 + 2 * lane + 1] = ty;
-        wu[64 + lane] = scv * vp;
-        wrc[lane] = rc;
-        wrc[16 + lane] = valid ? 1 : 0;
+        F[L::U / 4 + 2 * tid] = ux;
+        F[L::U / 4 + 2 * tid + 1] = uy;
+        F[L::T / 4 + 2 * tid] = tx;
+        F[L::T / 4 + 2 * tid + 1] = ty;
+        F[L::SV / 4 + tid] = scv * vp;
+        I[L::RC / 4 + tid] = rc;
+        I[L::OK / 4 + tid] = valid ? 1 : 0;
     }
+    if (tid == 0) {
+        umma::mbar_init(&bar, 1);
+        umma::fence_mbar_init();
+    }
+    if (tid < 32) umma::tmem_alloc(&tmem, L::ncols);
+    umma::fence_before();
     __syncthreads();
-
-    __nv_bfloat16 *sZ = sb + L::Warp + warp * L::WarpSize;
-    __nv_bfloat16 *sA1 = sZ + kSampW * kLdZ;
-    __nv_bfloat16 *sDH2 = sA1 + kSampW * kLdH;
-    __nv_bfloat16 *sDH1 = sDH2 + kSampW * kLdH;
-    for (int e = lane; e < kSampW * kLat; e += 32) {
-        const int r = e >> 5, k = e & 31;
-        float v = 0.0f;
-        if (wrc[16 + r]) v = expl ? A.zin[(cbase + r) * kLat + k] : A.z[(int64_t)wrc[r] * kLat + k];
-        const __nv_bfloat16 b = to_bf16(v);
-        sZ[r * kLdZ + k] = b;
-        sb[L::ZT + k * kLdT + warp * kSampW + r] = b;
+    umma::fence_after();
+    const uint32_t tm = tmem;
+    uint32_t phase = 0;
+    if (!train_step(A, tsm, &bar, tm, phase) && tid == 0) {
+        // a completion wait gave up: flag it and drain (bounded) before freeing
+        // the tensor memory
+        if (A.err) atomicExch(A.err, 1);
+        umma::mbar_wait(&bar, phase, kWaitPolls);
     }
-    __syncwarp();
-
-    // ---- layer 1: h1 = W1z z (tensor cores) + W1u u + b1
-    float h1[8][4];
-#pragma unroll
-    for (int nb = 0; nb < 8; ++nb) h1[nb][0] = h1[nb][1] = h1[nb][2] = h1[nb][3] = 0.0f;
-#pragma unroll
-    for (int kb = 0; kb < 2; ++kb) {
-        uint32_t a[4];
-        load_a(a, sZ, kLdZ, 0, kb * 16);
-#pragma unroll
-        for (int nb = 0; nb < 8; ++nb) {
-            uint32_t b[2];
-            load_b(b, sb + L::W1z, kLdZ, nb * 8, kb * 16);
-            mma16816(h1[nb], a, b);
-        }
-    }
-    const float uxA = wu[2 * g], uyA = wu[2 * g + 1], uxB = wu[2 * (g + 8)], uyB = wu[2 * (g + 8) + 1];
-#pragma unroll
-    for (int nb = 0; nb < 8; ++nb) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int col = nb * 8 + 2 * t + (j & 1);
-            const float ux = j < 2 ? uxA : uxB, uy = j < 2 ? uyA : uyB;
-            h1[nb][j] = h1[nb][j] + sf[L::fW1u + 2 * col] * ux + sf[L::fW1u + 2 * col + 1] * uy + sf[L::fb1 + col];
-            const int row = g + (j < 2 ? 0 : 8);
-            const __nv_bfloat16 v = to_bf16(silu1(h1[nb][j]));
-            sA1[row * kLdH + col] = v;
-            sb[L::A1T + col * kLdT + warp * kSampW + row] = v;
-        }
-    }
-    __syncwarp();
-
-    // ---- layer 2 and 3
-    float h2[8][4];
-#pragma unroll
-    for (int nb = 0; nb < 8; ++nb) h2[nb][0] = h2[nb][1] = h2[nb][2] = h2[nb][3] = 0.0f;
-#pragma unroll
-    for (int kb = 0; kb < 4; ++kb) {
-        uint32_t a[4];
-        load_a(a, sA1, kLdH, 0, kb * 16);
-#pragma unroll
-        for (int nb = 0; nb < 8; ++nb) {
-            uint32_t b[2];
-            load_b(b, sb + L::W2, kLdH, nb * 8, kb * 16);
-            mma16816(h2[nb], a, b);
-        }
-    }
-    float yp[2][2] = {{0.f, 0.f}, {0.f, 0.f}};  // [row A/B][out]
-#pragma unroll
-    for (int nb = 0; nb < 8; ++nb) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int col = nb * 8 + 2 * t + (j & 1);
-            h2[nb][j] += sf[L::fb2 + col];
-            const float a2 = silu2(h2[nb][j]);
-            yp[j >> 1][0] += sf[L::fW3 + col] * a2;
-            yp[j >> 1][1] += sf[L::fW3 + kHid + col] * a2;
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int o = 0; o < 2; ++o) {
-            yp[r][o] += __shfl_xor_sync(0xffffffffu, yp[r][o], 1);
-            yp[r][o] += __shfl_xor_sync(0xffffffffu, yp[r][o], 2);
-            yp[r][o] += sf[L::fb3 + o];
-        }
-    // ---- loss, outputs, validation
-    const int rows[2] = {g, g + 8};
-    float dy[2][2];
-    float lsum = 0.0f;
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int row = rows[r];
-        const bool valid = wrc[16 + row] != 0;
-        const float ex = yp[r][0] - wu[32 + 2 * row], ey = yp[r][1] - wu[32 + 2 * row + 1];
-        dy[r][0] = valid ? 2.0f * ex * A.inv_batch : 0.0f;
-        dy[r][1] = valid ? 2.0f * ey * A.inv_batch : 0.0f;
-        if (valid && t == 0) {
-            lsum += ex * ex + ey * ey;
-            if (A.yout) {
-                A.yout[2 * (cbase + row)] = yp[r][0];
-                A.yout[2 * (cbase + row) + 1] = yp[r][1];
-            }
-            if (!A.backward && A.val_max_net) {
-                const float scv = wu[64 + row];
-                const float en = scv * sqrtf(ex * ex + ey * ey);
-                const float tx = wu[32 + 2 * row], ty = wu[32 + 2 * row + 1];
-                const float es = scv * sqrtf(tx * tx + ty * ty);
-                atomicMax(&A.val_max_net[wrc[row]], __float_as_uint(en));
-                atomicMax(&A.val_max_series[wrc[row]], __float_as_uint(es));
-                atomicAdd(&A.val_sum[0], (double)en);
-                atomicAdd(&A.val_sum[1], (double)es);
-            }
-        }
-    }
-    for (int o = 16; o; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-    float *wg = sf + L::fWG + warp * L::kWG;  // this warp's gradient slots
-    if (lane == 0) {
-        if (A.backward)
-            wg[386] = lsum * A.inv_batch;
-        else if (A.loss)
-            atomicAdd(A.loss, lsum * A.inv_batch);
-    }
-    if (!A.backward) return;
-
-    // ---- layer 3 gradients
-#pragma unroll
-    for (int nb = 0; nb < 8; ++nb) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int col = nb * 8 + 2 * t + h;
-            float w0 = dy[0][0] * silu2(h2[nb][h]) + dy[1][0] * silu2(h2[nb][2 + h]);
-            float w1 = dy[0][1] * silu2(h2[nb][h]) + dy[1][1] * silu2(h2[nb][2 + h]);
-            for (int o = 4; o < 32; o <<= 1) {
-                w0 += __shfl_xor_sync(0xffffffffu, w0, o);
-                w1 += __shfl_xor_sync(0xffffffffu, w1, o);
-            }
-            if (g == 0) {
-                wg[col] = w0;
-                wg[kHid + col] = w1;
-            }
-        }
-    }
-    {
-        float d0 = t == 0 ? dy[0][0] + dy[1][0] : 0.0f, d1 = t == 0 ? dy[0][1] + dy[1][1] : 0.0f;
-        for (int o = 16; o; o >>= 1) {
-            d0 += __shfl_xor_sync(0xffffffffu, d0, o);
-            d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-        }
-        if (lane == 0) {
-            wg[128] = d0;
-            wg[129] = d1;
-        }
-    }
-    // ---- dh2 = (dy W3) * silu'(h2)
-#pragma unroll
-    for (int nb = 0; nb < 8; ++nb) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int col = nb * 8 + 2 * t + h;
-            float colsum = 0.0f;
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const float da2 = dy[r][0] * sf[L::fW3 + col] + dy[r][1] * sf[L::fW3 + kHid + col];
-                const float d = da2 * dsilu2(h2[nb][2 * r + h]);
-                colsum += d;
-                const __nv_bfloat16 v = to_bf16(d);
-                sDH2[rows[r] * kLdH + col] = v;
-                sb[L::DH2T + col * kLdT + warp * kSampW + rows[r]] = v;
-            }
-            for (int o = 4; o < 32; o <<= 1) colsum += __shfl_xor_sync(0xffffffffu, colsum, o);
-            if (g == 0) wg[322 + col] = colsum;
-        }
-    }
-    __syncwarp();
-    // ---- da1 = dh2 W2 (tensor cores), dh1 = da1 * silu'(h1)
-    float d1[8][4];
-#pragma unroll
-    for (int nb = 0; nb < 8; ++nb) d1[nb][0] = d1[nb][1] = d1[nb][2] = d1[nb][3] = 0.0f;
-#pragma unroll
-    for (int kb = 0; kb < 4; ++kb) {
-        uint32_t a[4];
-        load_a(a, sDH2, kLdH, 0, kb * 16);
-#pragma unroll
-        for (int nb = 0; nb < 8; ++nb) {
-            uint32_t b[2];
-            load_b(b, sb + L::W2T, kLdH, nb * 8, kb * 16);
-            mma16816(d1[nb], a, b);
-        }
-    }
-#pragma unroll
-    for (int nb = 0; nb < 8; ++nb) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int col = nb * 8 + 2 * t + h;
-            float colsum = 0.0f, gu0 = 0.0f, gu1 = 0.0f;
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const float d = d1[nb][2 * r + h] * dsilu1(h1[nb][2 * r + h]);
-                colsum += d;
-                gu0 += d * wu[2 * rows[r]];
-                gu1 += d * wu[2 * rows[r] + 1];
-                const __nv_bfloat16 v = to_bf16(d);
-                sDH1[rows[r] * kLdH + col] = v;
-                sb[L::DH1T + col * kLdT + warp * kSampW + rows[r]] = v;
-            }
-            for (int o = 4; o < 32; o <<= 1) {
-                colsum += __shfl_xor_sync(0xffffffffu, colsum, o);
-                gu0 += __shfl_xor_sync(0xffffffffu, gu0, o);
-                gu1 += __shfl_xor_sync(0xffffffffu, gu1, o);
-            }
-            if (g == 0) {
-                wg[258 + col] = colsum;
-                wg[130 + 2 * col] = gu0;
-                wg[130 + 2 * col + 1] = gu1;
-            }
-        }
-    }
-    __syncwarp();
-    // ---- latent gradients dz = dh1 W1z (tensor cores)
-    {
-        float dzc[4][4];
-#pragma unroll
-        for (int nb = 0; nb < 4; ++nb) dzc[nb][0] = dzc[nb][1] = dzc[nb][2] = dzc[nb][3] = 0.0f;
-#pragma unroll
-        for (int kb = 0; kb < 4; ++kb) {
-            uint32_t a[4];
-            load_a(a, sDH1, kLdH, 0, kb * 16);
-#pragma unroll
-            for (int nb = 0; nb < 4; ++nb) {
-                uint32_t b[2];
-                load_b(b, sb + L::W1zT, kLdH, nb * 8, kb * 16);
-                mma16816(dzc[nb], a, b);
-            }
-        }
-#pragma unroll
-        for (int nb = 0; nb < 4; ++nb) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int row = rows[j >> 1], col = nb * 8 + 2 * t + (j & 1);
-                if (!wrc[16 + row]) continue;
-                if (expl) {
-                    if (A.dzout) A.dzout[(cbase + row) * kLat + col] = dzc[nb][j];
-                } else {
-                    A.dzs[(cbase + row) * kLat + col] = dzc[nb][j];
-                }
-            }
-        }
-    }
+    umma::fence_before();
     __syncthreads();
-    // ---- CTA-level weight gradients over the 128 samples, into this CTA's row
-    float *gp = A.gpart + (int64_t)blockIdx.x * kGP;
-    {
-        // dW2[out][in] = sum_s dh2[s][out] a1[s][in]: warp w takes in-block w
-        float c[4][4];
-#pragma unroll
-        for (int mb = 0; mb < 4; ++mb) c[mb][0] = c[mb][1] = c[mb][2] = c[mb][3] = 0.0f;
-#pragma unroll
-        for (int kb = 0; kb < kSampC / 16; ++kb) {
-            uint32_t b[2];
-            load_b(b, sb + L::A1T, kLdT, warp * 8, kb * 16);
-#pragma unroll
-            for (int mb = 0; mb < 4; ++mb) {
-                uint32_t a[4];
-                load_a(a, sb + L::DH2T, kLdT, mb * 16, kb * 16);
-                mma16816(c[mb], a, b);
-            }
-        }
-#pragma unroll
-        for (int mb = 0; mb < 4; ++mb)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int out = mb * 16 + g + (j < 2 ? 0 : 8), in = warp * 8 + 2 * t + (j & 1);
-                gp[oW2 + out * kHid + in] = c[mb][j];
-            }
-    }
-    if (warp < 4) {
-        // dW1z[out][in] = sum_s dh1[s][out] z[s][in]: warp w takes in-block w
-        float c[4][4];
-#pragma unroll
-        for (int mb = 0; mb < 4; ++mb) c[mb][0] = c[mb][1] = c[mb][2] = c[mb][3] = 0.0f;
-#pragma unroll
-        for (int kb = 0; kb < kSampC / 16; ++kb) {
-            uint32_t b[2];
-            load_b(b, sb + L::ZT, kLdT, warp * 8, kb * 16);
-#pragma unroll
-            for (int mb = 0; mb < 4; ++mb) {
-                uint32_t a[4];
-                load_a(a, sb + L::DH1T, kLdT, mb * 16, kb * 16);
-                mma16816(c[mb], a, b);
-            }
-        }
-#pragma unroll
-        for (int mb = 0; mb < 4; ++mb)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int out = mb * 16 + g + (j < 2 ? 0 : 8), in = warp * 8 + 2 * t + (j & 1);
-                gp[oW1z + out * kLat + in] = c[mb][j];
-            }
-    }
-    // the per-warp slots, summed over the warps in order
-    for (int e = tid; e < 387; e += 256) {
-        float acc = 0.0f;
-        for (int w = 0; w < 8; ++w) acc += sf[L::fWG + w * L::kWG + e];
-        const int dst = e < 128 ? oW3 + e
-                      : e < 130 ? ob3 + (e - 128)
-                      : e < 258 ? oW1u + (e - 130)
-                      : e < 322 ? ob1 + (e - 258)
-                      : e < 386 ? ob2 + (e - 322)
-                                : kParams;  // the loss
-        gp[dst] = acc;
-    }
+    umma::fence_after();
+    if (tid < 32) umma::tmem_dealloc(tm, L::ncols);
 }
 
 cudaError_t ff_train_step(const TrainArgs &t, int64_t nsamples, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_ff_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)TrainSmemLayout::bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_ff_train, cudaFuncAttributeMaxDynamicSharedMemorySize, TrainTc::bytes);
     if (e != cudaSuccess) return e;
     if (nsamples <= 0) return cudaSuccess;
     const unsigned nb = (unsigned)((nsamples + kSampC - 1) / kSampC);
-    k_ff_train<<<nb, 256, TrainSmemLayout::bytes, s>>>(t);
+    k_ff_train<<<nb, 256, TrainTc::bytes, s>>>(t);
     return cudaGetLastError();
 }
 
@@ -913,7 +927,6 @@ constexpr int kNearChunk = 8;  // near-field stars per compensated chunk
 constexpr int kTcChunk = 128;                            // rays per tensor-core MMA (M)
 constexpr int kTcABytes = kTcChunk * kHid * 2;           // one warpgroup's A operand (16 KB)
 constexpr int kTcSmem = 2 * kTcABytes;                   // dynamic shared memory of the learned kernel
-constexpr int kWaitPolls = 1 << 20;                      // bound on a completion wait
 
 template <bool NET>
 __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int by, ShootSmem<256> &sm, TileShared &ts,

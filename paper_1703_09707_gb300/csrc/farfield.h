@@ -71,7 +71,7 @@ struct SampleSpec {
 struct TrainArgs {
     // network
     float *params;                     // FP32 master (read)
-    const __nv_bfloat16 *w1zb, *w2b, *w2tb, *w1ztb;  // BF16 copies: [64][32], [64][64], [64(in)][64(out)], [32][64]
+    const __nv_bfloat16 *w1zb, *w2b;   // BF16 copies of W1z [64][32] and W2 [64][64]
     float *grads;                      // host-side bookkeeping: the reduced gradients (flat layout)
     float *loss;                       // validation / forward-only: accumulated loss (sum of squared errors / B)
     // backward: each CTA writes its weight gradients and loss to row blockIdx.x of
@@ -97,6 +97,7 @@ struct TrainArgs {
     unsigned *val_max_net, *val_max_series;
     double *val_sum;                   // [2]: sum of errors (network, series)
     int backward;                      // 0 = forward only (validation)
+    int *err;                          // set to 1 if a tensor-core completion wait gave up (nullable)
 };
 
 // launchers (farfield.cu)
@@ -107,8 +108,7 @@ cudaError_t ff_coefficients(const float4 *stars, const int *scell, int64_t n, co
 cudaError_t ff_convert(const double *coef64, const CellGrid &cg, int pe, int pt, float *coef, float *tail, float *sc,
                        cudaStream_t s);
 cudaError_t ff_init_params(float *params, float *z, int nrc, uint64_t seed, cudaStream_t s);
-cudaError_t ff_prep_bf16(const float *params, __nv_bfloat16 *w1zb, __nv_bfloat16 *w2b, __nv_bfloat16 *w2tb,
-                         __nv_bfloat16 *w1ztb, cudaStream_t s);
+cudaError_t ff_prep_bf16(const float *params, __nv_bfloat16 *w1zb, __nv_bfloat16 *w2b, cudaStream_t s);
 cudaError_t ff_train_step(const TrainArgs &t, int64_t nsamples, cudaStream_t s);
 cudaError_t ff_adam(float *p, float *m, float *v, const float *g, int64_t n, float lr, float b1, float b2, float eps,
                     float bc1, float bc2, cudaStream_t s);

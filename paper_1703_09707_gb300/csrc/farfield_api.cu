@@ -33,7 +33,7 @@ struct FarState {
     float *params = nullptr, *m = nullptr, *v = nullptr, *grads = nullptr, *loss = nullptr;  // params then Z
     float *gpart = nullptr, *dzs = nullptr;  // per-CTA gradient rows and per-sample latent gradients of a step
     int64_t gpart_rows = 0, dzs_samples = 0;
-    __nv_bfloat16 *w1zb = nullptr, *w2b = nullptr, *w2tb = nullptr, *w1ztb = nullptr;
+    __nv_bfloat16 *w1zb = nullptr, *w2b = nullptr;
     float *ec = nullptr;
     int *flags = nullptr;
     unsigned *vmax_net = nullptr, *vmax_series = nullptr;
@@ -81,7 +81,7 @@ void free_state(FarState *f)
     ffree(f->scell), ffree(f->count), ffree(f->start), ffree(f->fill), ffree(f->perm), ffree(f->cstars);
     ffree(f->coef64), ffree(f->coef), ffree(f->tail), ffree(f->sc);
     ffree(f->params), ffree(f->m), ffree(f->v), ffree(f->grads), ffree(f->loss);
-    ffree(f->w1zb), ffree(f->w2b), ffree(f->w2tb), ffree(f->w1ztb), ffree(f->ec), ffree(f->flags);
+    ffree(f->w1zb), ffree(f->w2b), ffree(f->ec), ffree(f->flags);
     ffree(f->vmax_net), ffree(f->vmax_series), ffree(f->vsum), ffree(f->items), ffree(f->counter);
     ffree(f->sub_items);
     ffree(f->gpart), ffree(f->dzs), ffree(f->d_err);
@@ -144,9 +144,7 @@ int alloc_state(FarState *f, int64_t nstars)
     FCUDA(dmalloc(&f->grads, sizeof(float) * np), "cudaMalloc");
     FCUDA(dmalloc(&f->loss, sizeof(float) * 2), "cudaMalloc");
     FCUDA(dmalloc(&f->w1zb, sizeof(__nv_bfloat16) * mlp::kHid * mlp::kLat), "cudaMalloc");
-    FCUDA(dmalloc(&f->w1ztb, sizeof(__nv_bfloat16) * mlp::kHid * mlp::kLat), "cudaMalloc");
     FCUDA(dmalloc(&f->w2b, sizeof(__nv_bfloat16) * mlp::kHid * mlp::kHid), "cudaMalloc");
-    FCUDA(dmalloc(&f->w2tb, sizeof(__nv_bfloat16) * mlp::kHid * mlp::kHid), "cudaMalloc");
     FCUDA(dmalloc(&f->ec, sizeof(float) * (size_t)nrc * mlp::kHid), "cudaMalloc");
     FCUDA(dmalloc(&f->flags, sizeof(int) * nrc), "cudaMalloc");
     FCUDA(dmalloc(&f->vmax_net, sizeof(unsigned) * nrc), "cudaMalloc");
@@ -163,8 +161,6 @@ TrainArgs train_args(FarState *f)
     t.params = f->params;
     t.w1zb = f->w1zb;
     t.w2b = f->w2b;
-    t.w2tb = f->w2tb;
-    t.w1ztb = f->w1ztb;
     t.grads = f->grads;
     t.loss = f->loss;
     t.gpart = f->gpart;
@@ -178,6 +174,7 @@ TrainArgs train_args(FarState *f)
     t.pt = f->pt;
     t.spec.nrc = f->nrc;
     t.backward = 1;
+    t.err = f->d_err;
     return t;
 }
 
@@ -187,7 +184,7 @@ int validate(FarState *f, int64_t per_cell, uint64_t seed, cudaStream_t s, doubl
     FCUDA(cudaMemsetAsync(f->vmax_net, 0, sizeof(unsigned) * f->nrc, s), "memset");
     FCUDA(cudaMemsetAsync(f->vmax_series, 0, sizeof(unsigned) * f->nrc, s), "memset");
     FCUDA(cudaMemsetAsync(f->vsum, 0, sizeof(double) * 2, s), "memset");
-    FCUDA(ff_prep_bf16(f->params, f->w1zb, f->w2b, f->w2tb, f->w1ztb, s), "prep");
+    FCUDA(ff_prep_bf16(f->params, f->w1zb, f->w2b, s), "prep");
     TrainArgs t = train_args(f);
     t.backward = 0;
     t.loss = nullptr;
@@ -257,7 +254,7 @@ int schedule(FarState *f, cudaStream_t s)
 
 int finish_inference_tables(FarState *f, cudaStream_t s)
 {
-    FCUDA(ff_prep_bf16(f->params, f->w1zb, f->w2b, f->w2tb, f->w1ztb, s), "prep");
+    FCUDA(ff_prep_bf16(f->params, f->w1zb, f->w2b, s), "prep");
     FCUDA(ff_embed(f->params, f->params + mlp::kParams, f->nrc, f->ec, s), "embed");
     return MLENS_OK;
 }
@@ -343,6 +340,7 @@ int mlens_fit_far_field(mlens_ctx *ctx, const mlens_grid *rays, const mlens_fit_
     const int64_t np = mlp::kParams + (int64_t)f->nrc * mlp::kLat;
     FCUDA(ff_init_params(f->params, f->params + mlp::kParams, f->nrc, p.seed, s), "init");
     FCUDA(cudaMemsetAsync(f->m, 0, sizeof(float) * np, s), "memset");
+    FCUDA(cudaMemsetAsync(f->d_err, 0, sizeof(int), s), "memset(err)");
     FCUDA(cudaMemsetAsync(f->v, 0, sizeof(float) * np, s), "memset");
     int64_t steps = 0;
     float last_loss = 0.0f;
@@ -368,7 +366,7 @@ int mlens_fit_far_field(mlens_ctx *ctx, const mlens_grid *rays, const mlens_fit_
             t.spec.offset = j * p.batch;
             t.spec.count = cnt;
             t.inv_batch = 1.0f / (float)cnt;
-            FCUDA(ff_prep_bf16(f->params, f->w1zb, f->w2b, f->w2tb, f->w1ztb, s), "prep");
+            FCUDA(ff_prep_bf16(f->params, f->w1zb, f->w2b, s), "prep");
             FCUDA(ff_train_step(t, cnt, s), "train step");
             // gradients summed in a fixed order: training is bit-reproducible
             FCUDA(ff_reduce_grads(f->gpart, ff_train_blocks(cnt), f->grads, f->loss, s), "gradient reduction");
@@ -399,6 +397,11 @@ int mlens_fit_far_field(mlens_ctx *ctx, const mlens_grid *rays, const mlens_fit_
 
     double mn = 0.0, ms = 0.0;
     if ((rc = validate(f, p.val_samples_per_cell, p.seed * 0xD1B54A32D192ED03ull + 99, s, &mn, &ms))) return rc;
+    {
+        int err = 0;
+        FCUDA(cudaMemcpy(&err, f->d_err, sizeof(int), cudaMemcpyDeviceToHost), "memcpy(err)");
+        if (err) return ffail(MLENS_ERR_CUDA, "far-field fit: a tensor-core completion wait gave up");
+    }
     f->report.val_mean_err_net = f->use_net ? mn : -1.0;
     f->report.val_mean_err_series = ms;
     if ((rc = schedule(f, s))) return rc;
@@ -660,22 +663,19 @@ int mlens_ff_eval(const float *params_dev, const float *z_dev, const float *u_de
     cudaStream_t s = (cudaStream_t)stream;
     __nv_bfloat16 *w = nullptr;
     float *dl = nullptr;
-    FCUDA(dmalloc(&w, sizeof(__nv_bfloat16) * (2 * mlp::kHid * mlp::kLat + 2 * mlp::kHid * mlp::kHid)), "cudaMalloc");
-    cudaError_t e = dmalloc(&dl, sizeof(float));
-    __nv_bfloat16 *w1zb = w, *w1ztb = w + mlp::kHid * mlp::kLat, *w2b = w1ztb + mlp::kHid * mlp::kLat,
-                  *w2tb = w2b + mlp::kHid * mlp::kHid;
+    FCUDA(dmalloc(&w, sizeof(__nv_bfloat16) * (mlp::kHid * mlp::kLat + mlp::kHid * mlp::kHid)), "cudaMalloc");
+    cudaError_t e = dmalloc(&dl, 2 * sizeof(float));  // the loss, then the kernel's error flag
+    __nv_bfloat16 *w1zb = w, *w2b = w + mlp::kHid * mlp::kLat;
     float *gpart = nullptr;
     const int64_t nblk = ff_train_blocks(nsamples);
     if (e == cudaSuccess && grads_dev) e = dmalloc(&gpart, sizeof(float) * nblk * ff_gpart_stride());
-    if (e == cudaSuccess) e = cudaMemsetAsync(dl, 0, sizeof(float), s);
-    if (e == cudaSuccess) e = ff_prep_bf16(params_dev, w1zb, w2b, w2tb, w1ztb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dl, 0, 2 * sizeof(float), s);
+    if (e == cudaSuccess) e = ff_prep_bf16(params_dev, w1zb, w2b, s);
     if (e == cudaSuccess) {
         TrainArgs t{};
         t.params = const_cast<float *>(params_dev);
         t.w1zb = w1zb;
         t.w2b = w2b;
-        t.w2tb = w2tb;
-        t.w1ztb = w1ztb;
         t.grads = grads_dev;
         t.loss = dl;
         t.gpart = gpart;
@@ -688,18 +688,22 @@ int mlens_ff_eval(const float *params_dev, const float *z_dev, const float *u_de
         t.yout = y_dev;
         t.dzout = dz_dev;
         t.backward = grads_dev ? 1 : 0;
+        t.err = reinterpret_cast<int *>(dl + 1);
         e = ff_train_step(t, nsamples, s);
         if (e == cudaSuccess && grads_dev) e = ff_reduce_grads(gpart, nblk, grads_dev, dl, s);
     }
-    float h = 0.0f;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, dl, sizeof(float), cudaMemcpyDeviceToHost, s);
+    float h[2] = {0.0f, 0.0f};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, dl, sizeof(h), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) cudaStreamSynchronize(s);
     dfree(w);
     dfree(dl);
     dfree(gpart);
     if (e != cudaSuccess) return fcuda(e, "mlens_ff_eval");
-    if (loss_host) *loss_host = h;
+    int flag = 0;
+    memcpy(&flag, &h[1], sizeof(flag));
+    if (flag) return ffail(MLENS_ERR_CUDA, "mlens_ff_eval: a tensor-core completion wait gave up");
+    if (loss_host) *loss_host = h[0];
     return MLENS_OK;
 }
 

@@ -1,5 +1,6 @@
-// mlp.cuh -- the far-field network of the learned-far-field variant on BF16
-// tensor cores (mma.sync m16n8k16, FP32 accumulation).
+// mlp.cuh -- the far-field network of the learned-far-field variant: sizes,
+// parameter layout and activations.  Its products run on the fifth-generation
+// tensor cores (tcgen05.mma, BF16 operands, FP32 accumulation; umma.cuh).
 //
 // Network: a per-cell latent z (32) and one shared MLP 34 -> 64 -> 64 -> 2,
 //   h1 = W1z z + W1u u + b1, a1 = silu(h1); h2 = W2 a1 + b2, a2 = silu(h2);
@@ -71,36 +72,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 }
 
 __device__ __forceinline__ __nv_bfloat16 to_bf16(float v) { return __float2bfloat16_rn(v); }
-
-// D = A (16x16, row) * B (16x8, col) + D
-__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const uint32_t b[2])
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// Fragment loads from shared memory.  A: row-major [row][k] with leading dim ld;
-// B: stored [n][k] with leading dim ld (k contiguous).  g = lane/4, t = lane%4.
-__device__ __forceinline__ void load_a(uint32_t a[4], const __nv_bfloat16 *A, int ld, int row0, int k0)
-{
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const __nv_bfloat16 *p = A + (row0 + g) * ld + k0 + 2 * t;
-    a[0] = *reinterpret_cast<const uint32_t *>(p);
-    a[1] = *reinterpret_cast<const uint32_t *>(p + 8 * ld);
-    a[2] = *reinterpret_cast<const uint32_t *>(p + 8);
-    a[3] = *reinterpret_cast<const uint32_t *>(p + 8 * ld + 8);
-}
-
-__device__ __forceinline__ void load_b(uint32_t b[2], const __nv_bfloat16 *B, int ld, int n0, int k0)
-{
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const __nv_bfloat16 *p = B + (n0 + g) * ld + k0 + 2 * t;
-    b[0] = *reinterpret_cast<const uint32_t *>(p);
-    b[1] = *reinterpret_cast<const uint32_t *>(p + 8);
-}
 
 }  // namespace mlp
 }  // namespace mlens
