@@ -400,13 +400,20 @@ __device__ __forceinline__ void sample_of(const TrainArgs &A, int64_t li, int &r
     const float covy = fminf(1.0f, (float)(A.cg.rays_ny - cy * 32 * A.cg.kty) / (float)(32 * A.cg.kty));
     ux = 2.0f * unit24(h1) * covx - 1.0f;
     uy = 2.0f * unit24(h2) * covy - 1.0f;
-    // q(v) at v = u / sqrt(2) by Horner
+    // q(v) at v = u / sqrt(2) by Horner, the cell's coefficients loaded first (all
+    // in flight together; the row is 8-byte aligned)
     const float vr = ux * 0.70710678f, vi = uy * 0.70710678f;
-    const float *b = A.tail + (int64_t)rc * 2 * (A.pt - A.pe);
-    float ar = b[2 * (A.pt - A.pe - 1)], ai = b[2 * (A.pt - A.pe - 1) + 1];
-    for (int p = A.pt - 1; p > A.pe; --p) {
-        const float nr = ar * vr - ai * vi + b[2 * (p - A.pe - 1)];
-        const float ni = ar * vi + ai * vr + b[2 * (p - A.pe - 1) + 1];
+    const int nt = A.pt - A.pe;
+    const float2 *b = reinterpret_cast<const float2 *>(A.tail + (int64_t)rc * 2 * nt);
+    float2 bc[kPtMax];
+#pragma unroll
+    for (int i = 0; i < kPtMax; ++i) bc[i] = i < nt ? b[i] : make_float2(0.0f, 0.0f);
+    float ar = 0.0f, ai = 0.0f;
+#pragma unroll
+    for (int i = kPtMax - 1; i >= 0; --i) {
+        if (i >= nt) continue;
+        const float nr = ar * vr - ai * vi + bc[i].x;
+        const float ni = ar * vi + ai * vr + bc[i].y;
         ar = nr;
         ai = ni;
     }
@@ -504,12 +511,23 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
         const int rc = I[L::RC / 4 + s];
         const bool ok = I[L::OK / 4 + s] != 0;
         float zv[16];
+        const float *src = (expl ? A.zin + (cbase + s) * kLat : A.z + (int64_t)rc * kLat) + 16 * wg;
+        if (!ok) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int k = 16 * wg + j;
-            zv[j] = ok ? (expl ? A.zin[(cbase + s) * kLat + k] : A.z[(int64_t)rc * kLat + k]) : 0.0f;
-            st_bf16(S, L::ZT + tc_off(k, s, kSampC), zv[j]);
+            for (int j = 0; j < 16; ++j) zv[j] = 0.0f;
+        } else if (((uintptr_t)src & 7u) == 0) {  // the latents (after the 6530 parameters) are 8-byte aligned
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float2 v = reinterpret_cast<const float2 *>(src)[j];
+                zv[2 * j] = v.x;
+                zv[2 * j + 1] = v.y;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) zv[j] = src[j];
         }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) st_bf16(S, L::ZT + tc_off(16 * wg + j, s, kSampC), zv[j]);
 #pragma unroll
         for (int h = 0; h < 2; ++h)
             *reinterpret_cast<uint4 *>(S + L::Z + tc_off(s, 16 * wg + 8 * h, kLat)) =
@@ -673,24 +691,37 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
     {
         uint32_t r[16];
         umma::ld16(tm + lane_base + L::cDZ + 16 * wg, r);
-        if (valid) {
-            float *dst = expl ? A.dzout : A.dzs;
-            if (dst)
+        float *dst = expl ? A.dzout : A.dzs;
+        if (valid && dst) {
+            dst += (cbase + s) * kLat + 16 * wg;
+            if (((uintptr_t)dst & 15u) == 0) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) dst[(cbase + s) * kLat + 16 * wg + j] = __uint_as_float(r[j]);
+                for (int q = 0; q < 4; ++q)
+                    reinterpret_cast<float4 *>(dst)[q] =
+                        make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                    __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) dst[j] = __uint_as_float(r[j]);
+            }
         }
     }
+    // gradient rows are 16-byte aligned (kGP = 6532 floats; dW2 at 2240, dW1z at 0)
     float *gp = A.gpart + (int64_t)blockIdx.x * kGP;
     if (s < kHid) {  // lanes 0..63: dW2[out = s][in]
         float v[32];
         tc_load32(tm + lane_base + L::cDW2 + c0, v);
+        float4 *g4 = reinterpret_cast<float4 *>(gp + oW2 + s * kHid + c0);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) gp[oW2 + s * kHid + c0 + j] = v[j];
+        for (int q = 0; q < 8; ++q) g4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     } else {  // lanes 64..127: dW1z[out = s - 64][in]
         uint32_t r[16];
         umma::ld16(tm + lane_base + L::cDW1z + 16 * wg, r);
+        float4 *g4 = reinterpret_cast<float4 *>(gp + oW1z + (s - kHid) * kLat + 16 * wg);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) gp[oW1z + (s - kHid) * kLat + 16 * wg + j] = __uint_as_float(r[j]);
+        for (int q = 0; q < 4; ++q)
+            g4[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]), __uint_as_float(r[4 * q + 2]),
+                                __uint_as_float(r[4 * q + 3]));
     }
     __syncthreads();
     // ---- the FP32 column sums: warps 4 wg .. 4 wg + 3 cover all samples of columns 32 wg ..
@@ -726,17 +757,22 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
     const int tid = threadIdx.x;
 
     // ---- weights: BF16 operands in core-matrix layout, FP32 small parameters
-    for (int i = tid; i < kHid * kLat; i += 256) {
-        const int o = i / kLat, k = i % kLat;
-        const __nv_bfloat16 w = A.w1zb[i];
-        *reinterpret_cast<__nv_bfloat16 *>(tsm + L::W1z + tc_off(o, k, kLat)) = w;
-        *reinterpret_cast<__nv_bfloat16 *>(tsm + L::W1zT + tc_off(k, o, kHid)) = w;
+    // (8 BF16 = one 16-byte core-matrix row per load; the copies are 16-byte aligned)
+    for (int i = tid; i < kHid * kLat / 8; i += 256) {
+        const int o = 8 * i / kLat, k = 8 * i % kLat;
+        const uint4 w = reinterpret_cast<const uint4 *>(A.w1zb)[i];
+        *reinterpret_cast<uint4 *>(tsm + L::W1z + tc_off(o, k, kLat)) = w;
+        const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&w);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) *reinterpret_cast<__nv_bfloat16 *>(tsm + L::W1zT + tc_off(k + j, o, kHid)) = e[j];
     }
-    for (int i = tid; i < kHid * kHid; i += 256) {
-        const int o = i / kHid, k = i % kHid;
-        const __nv_bfloat16 w = A.w2b[i];
-        *reinterpret_cast<__nv_bfloat16 *>(tsm + L::W2 + tc_off(o, k, kHid)) = w;
-        *reinterpret_cast<__nv_bfloat16 *>(tsm + L::W2T + tc_off(k, o, kHid)) = w;
+    for (int i = tid; i < kHid * kHid / 8; i += 256) {
+        const int o = 8 * i / kHid, k = 8 * i % kHid;
+        const uint4 w = reinterpret_cast<const uint4 *>(A.w2b)[i];
+        *reinterpret_cast<uint4 *>(tsm + L::W2 + tc_off(o, k, kHid)) = w;
+        const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&w);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) *reinterpret_cast<__nv_bfloat16 *>(tsm + L::W2T + tc_off(k + j, o, kHid)) = e[j];
     }
     if (tid < 2 * kHid) {
         F[L::W1u / 4 + tid] = A.params[oW1u + tid];
@@ -806,19 +842,36 @@ cudaError_t ff_train_step(const TrainArgs &t, int64_t nsamples, cudaStream_t s)
 int64_t ff_gpart_stride() { return kGP; }
 int64_t ff_train_blocks(int64_t nsamples) { return (nsamples + kSampC - 1) / kSampC; }
 
-// grads[p] = sum over the CTA rows of gpart in row order (and the loss).
-__global__ void k_reduce_grads(const float *__restrict__ gpart, int64_t nblk, float *__restrict__ grads,
-                               float *__restrict__ loss)
+// grads[p] = sum over the CTA rows of gpart: a CTA takes 32 columns; its 8 row
+// groups each sum a contiguous eighth of the rows in row order (loads in flight
+// together), then the 8 partial sums are added in group order.  The order is
+// fixed, so training stays bit-reproducible.
+constexpr int kRedCols = 32, kRedGroups = 8;
+
+__global__ void __launch_bounds__(kRedCols * kRedGroups) k_reduce_grads(const float *__restrict__ gpart, int64_t nblk,
+                                                                       float *__restrict__ grads, float *__restrict__ loss)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p > kParams) return;
+    __shared__ float part[kRedGroups][kRedCols];
+    const int c = threadIdx.x % kRedCols, g = threadIdx.x / kRedCols;
+    const int p = blockIdx.x * kRedCols + c;  // parameter index; kParams is the loss
+    const int64_t per = (nblk + kRedGroups - 1) / kRedGroups;
+    const int64_t b0 = g * per, b1 = min(nblk, b0 + per);
     float acc = 0.0f;
-#pragma unroll 8
-    for (int64_t b = 0; b < nblk; ++b) acc += gpart[b * kGP + p];
-    if (p < kParams)
-        grads[p] = acc;
-    else if (loss)
-        *loss = acc;
+    if (p <= kParams) {
+#pragma unroll 16
+        for (int64_t b = b0; b < b1; ++b) acc += gpart[b * kGP + p];
+    }
+    part[g][c] = acc;
+    __syncthreads();
+    if (g == 0 && p <= kParams) {
+        float t = part[0][c];
+#pragma unroll
+        for (int q = 1; q < kRedGroups; ++q) t += part[q][c];
+        if (p < kParams)
+            grads[p] = t;
+        else if (loss)
+            *loss = t;
+    }
 }
 
 // dz[c][k] = sum of the step's samples of cell c in sample order: sample li of
@@ -837,7 +890,7 @@ __global__ void k_reduce_latents(const float *__restrict__ dzs, int64_t count, i
 
 cudaError_t ff_reduce_grads(const float *gpart, int64_t nblk, float *grads, float *loss, cudaStream_t s)
 {
-    k_reduce_grads<<<(kParams + 1 + 255) / 256, 256, 0, s>>>(gpart, nblk, grads, loss);
+    k_reduce_grads<<<(kParams + 1 + kRedCols - 1) / kRedCols, kRedCols * kRedGroups, 0, s>>>(gpart, nblk, grads, loss);
     return cudaGetLastError();
 }
 
@@ -848,8 +901,11 @@ cudaError_t ff_reduce_latents(const float *dzs, int64_t count, int64_t offset, i
     return cudaGetLastError();
 }
 
-__global__ void k_adam(float *p, float *m, float *v, const float *g, int64_t n, float lr, float b1, float b2,
-                       float eps, float bc1, float bc2)
+// One Adam step over the weights (the first nw entries, rate lr_w) and the latents
+// (rate lr_z); the updated W1z and W2 are also written as the BF16 copies the next
+// training step reads.
+__global__ void k_adam(float *p, float *m, float *v, const float *g, int64_t n, int64_t nw, float lr_w, float lr_z,
+                       float b1, float b2, float eps, float bc1, float bc2, __nv_bfloat16 *w1zb, __nv_bfloat16 *w2b)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -858,14 +914,19 @@ __global__ void k_adam(float *p, float *m, float *v, const float *g, int64_t n, 
     const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
-    p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    const float lr = i < nw ? lr_w : lr_z;
+    const float pn = p[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    p[i] = pn;
+    if (i >= oW1z && i < oW1z + kHid * kLat) w1zb[i - oW1z] = to_bf16(pn);
+    if (i >= oW2 && i < oW2 + kHid * kHid) w2b[i - oW2] = to_bf16(pn);
 }
 
-cudaError_t ff_adam(float *p, float *m, float *v, const float *g, int64_t n, float lr, float b1, float b2, float eps,
-                    float bc1, float bc2, cudaStream_t s)
+cudaError_t ff_adam(float *p, float *m, float *v, const float *g, int64_t n, int64_t nw, float lr_w, float lr_z,
+                    float b1, float b2, float eps, float bc1, float bc2, __nv_bfloat16 *w1zb, __nv_bfloat16 *w2b,
+                    cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_adam<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, m, v, g, n, lr, b1, b2, eps, bc1, bc2);
+    k_adam<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, m, v, g, n, nw, lr_w, lr_z, b1, b2, eps, bc1, bc2, w1zb, w2b);
     return cudaGetLastError();
 }
 

@@ -110,8 +110,11 @@ cudaError_t ff_convert(const double *coef64, const CellGrid &cg, int pe, int pt,
 cudaError_t ff_init_params(float *params, float *z, int nrc, uint64_t seed, cudaStream_t s);
 cudaError_t ff_prep_bf16(const float *params, __nv_bfloat16 *w1zb, __nv_bfloat16 *w2b, cudaStream_t s);
 cudaError_t ff_train_step(const TrainArgs &t, int64_t nsamples, cudaStream_t s);
-cudaError_t ff_adam(float *p, float *m, float *v, const float *g, int64_t n, float lr, float b1, float b2, float eps,
-                    float bc1, float bc2, cudaStream_t s);
+// Adam over weights (first nw entries, rate lr_w) and latents (rate lr_z); also
+// refreshes the BF16 copies of W1z and W2.
+cudaError_t ff_adam(float *p, float *m, float *v, const float *g, int64_t n, int64_t nw, float lr_w, float lr_z,
+                    float b1, float b2, float eps, float bc1, float bc2, __nv_bfloat16 *w1zb, __nv_bfloat16 *w2b,
+                    cudaStream_t s);
 int64_t ff_gpart_stride();                 // floats per CTA row of gpart
 int64_t ff_train_blocks(int64_t nsamples);  // CTAs of one ff_train_step
 cudaError_t ff_reduce_grads(const float *gpart, int64_t nblk, float *grads, float *loss, cudaStream_t s);

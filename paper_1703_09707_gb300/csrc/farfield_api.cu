@@ -360,30 +360,27 @@ int mlens_fit_far_field(mlens_ctx *ctx, const mlens_grid *rays, const mlens_fit_
         }
         TrainArgs t = train_args(f);
         t.spec.seed = p.seed * 0x9E3779B97F4A7C15ull + 17;
+        FCUDA(ff_prep_bf16(f->params, f->w1zb, f->w2b, s), "prep");
         for (int64_t k = 0; k < total; ++k) {
             const int64_t j = k % per_epoch;
             const int64_t cnt = std::min<int64_t>(p.batch, p.train_samples - j * p.batch);
             t.spec.offset = j * p.batch;
             t.spec.count = cnt;
             t.inv_batch = 1.0f / (float)cnt;
-            FCUDA(ff_prep_bf16(f->params, f->w1zb, f->w2b, s), "prep");
             FCUDA(ff_train_step(t, cnt, s), "train step");
             // gradients summed in a fixed order: training is bit-reproducible
             FCUDA(ff_reduce_grads(f->gpart, ff_train_blocks(cnt), f->grads, f->loss, s), "gradient reduction");
             FCUDA(ff_reduce_latents(f->dzs, cnt, t.spec.offset, f->nrc, f->grads + mlp::kParams, s),
                   "latent gradient reduction");
-            // cosine decay to 5% of the initial rates
+            // cosine decay to 5% of the initial rates; the update also refreshes the
+            // BF16 weight copies of the next step
             const double fr = (double)k / (double)std::max<int64_t>(total - 1, 1);
             const double sc = 0.05 + 0.95 * 0.5 * (1.0 + std::cos(3.14159265358979323846 * fr));
             const double st = (double)(k + 1);
             const float bc1 = (float)(1.0 - std::pow(0.9, st)), bc2 = (float)(1.0 - std::pow(0.999, st));
-            FCUDA(ff_adam(f->params, f->m, f->v, f->grads, mlp::kParams, (float)(p.lr_weights * sc), 0.9f, 0.999f,
-                          1e-8f, bc1, bc2, s),
+            FCUDA(ff_adam(f->params, f->m, f->v, f->grads, np, mlp::kParams, (float)(p.lr_weights * sc),
+                          (float)(p.lr_latents * sc), 0.9f, 0.999f, 1e-8f, bc1, bc2, f->w1zb, f->w2b, s),
                   "adam");
-            FCUDA(ff_adam(f->params + mlp::kParams, f->m + mlp::kParams, f->v + mlp::kParams,
-                          f->grads + mlp::kParams, (int64_t)f->nrc * mlp::kLat, (float)(p.lr_latents * sc), 0.9f,
-                          0.999f, 1e-8f, bc1, bc2, s),
-                  "adam(latents)");
             if (k + 1 == total) FCUDA(cudaMemcpyAsync(&last_loss, f->loss, sizeof(float), cudaMemcpyDeviceToHost, s),
                                       "memcpy(loss)");
             ++steps;
