@@ -154,6 +154,29 @@ __device__ __forceinline__ DF df_rcp(DF a)
     return df_norm(y, __fmul_rn(y, r.h));     // y (1 + r): error ~2^-47
 }
 
+__device__ __forceinline__ float2 f2c(float x, float y) { return make_float2(x, y); }
+
+// Order-0 term of one far star in double-float: -m / (z_k - z_c) = (-tr, ti), with
+// w = s / (z_k - z_c) in FP32 for the higher orders.
+struct FarTerm {
+    DF tr, ti;
+    float wr, wi;
+};
+__device__ __forceinline__ FarTerm far_term(float4 q, float zxh, float zxl, float zyh, float zyl, float fscale)
+{
+    FarTerm t;
+    const DF dx = df_add(df_two_sum(q.x, -zxh), {-zxl, 0.0f});
+    const DF dy = df_add(df_two_sum(q.y, -zyh), {-zyl, 0.0f});
+    const DF inv = df_rcp(df_add(df_mul(dx, dx), df_mul(dy, dy)));
+    const DF mi = df_mulf(inv, q.z);
+    t.tr = df_mul(mi, dx);
+    t.ti = df_mul(mi, dy);
+    const float si_s = __fmul_rn(inv.h, fscale);
+    t.wr = __fmul_rn(dx.h, si_s);
+    t.wi = -__fmul_rn(dy.h, si_s);
+    return t;
+}
+
 __global__ void __launch_bounds__(256) k_coeffs(const float4 *stars, const int *scell, int64_t n, CellGrid g, int pt,
                                                 double scale, double *out)
 {
@@ -162,9 +185,14 @@ __global__ void __launch_bounds__(256) k_coeffs(const float4 *stars, const int *
     // stars and added to an FP64 accumulator once per stage; w = s / (z_k - z_c)
     // in FP32 and the higher orders t_p = t_0 w^p by an FP32 recurrence into
     // per-lane FP32 partials, summed across the warp after each 256-star stage,
-    // lane p adding coefficient p's stage sum to its FP64 accumulator.
+    // lane p adding coefficient p's stage sum to its FP64 accumulator.  A lane
+    // takes its stars in pairs (k, k + 32) and runs the two recurrences as packed
+    // f32x2 operations (the pair's terms are added before they enter the partials,
+    // which keeps the partials in 48 registers: two CTAs per SM).  Near stars, and the padding of a short stage, enter as a
+    // massless star far away: they contribute exactly zero and keep the loop
+    // uniform across the warp.
     __shared__ float4 sq[256];
-    __shared__ int scl[256];
+    __shared__ int2 scl[256];  // the star's cell (x, y); (-8, -8) outside the grid
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nrc = g.ncx * g.ncy;
     const int rc = blockIdx.x * 8 + warp;
@@ -175,45 +203,50 @@ __global__ void __launch_bounds__(256) k_coeffs(const float4 *stars, const int *
     const float zxh = (float)zx, zxl = (float)(zx - (double)zxh);
     const float zyh = (float)zy, zyl = (float)(zy - (double)zyh);
     const float fscale = (float)scale;
+    const float4 pad = make_float4(kPadCoord, kPadCoord, 0.0f, 0.0f);
     double b0r = 0.0, b0i = 0.0;    // order 0, this lane's stars
     double accr = 0.0, acci = 0.0;  // lane p (1 <= p <= pt): coefficient p, all stages
     for (int64_t s0 = 0; s0 < n; s0 += 256) {
         const int cnt = (int)min((int64_t)256, n - s0);
         __syncthreads();
-        if ((int)threadIdx.x < cnt) {
-            sq[threadIdx.x] = stars[s0 + threadIdx.x];
-            scl[threadIdx.x] = scell[s0 + threadIdx.x];
+        {
+            const int t = threadIdx.x;
+            float4 q = pad;
+            int2 cc = make_int2(-8, -8);
+            if (t < cnt) {
+                q = stars[s0 + t];
+                const int c = scell[s0 + t];
+                if (c >= 0) cc = make_int2(c % g.nx, c / g.nx);
+            }
+            sq[t] = q;
+            scl[t] = cc;
         }
         __syncthreads();
         if (!ok) continue;
-        float pr[kPtMax], pi[kPtMax];
+        float pr[kPtMax], pi[kPtMax];  // partial sums of order p + 1
 #pragma unroll
         for (int p = 0; p < kPtMax; ++p) pr[p] = pi[p] = 0.0f;
         DF sr = {0.0f, 0.0f}, si = {0.0f, 0.0f};
-        for (int k = lane; k < cnt; k += 32) {
-            const int c = scl[k];
-            if (c >= 0) {
-                const int sx = c % g.nx, sy = c / g.nx;
-                if (sx - ex <= 1 && ex - sx <= 1 && sy - ey <= 1 && ey - sy <= 1) continue;  // near star
-            }
-            const float4 q = sq[k];
-            const DF dx = df_add(df_two_sum(q.x, -zxh), {-zxl, 0.0f});
-            const DF dy = df_add(df_two_sum(q.y, -zyh), {-zyl, 0.0f});
-            const DF inv = df_rcp(df_add(df_mul(dx, dx), df_mul(dy, dy)));
-            const DF mi = df_mulf(inv, q.z);
-            const DF tr = df_mul(mi, dx), ti = df_mul(mi, dy);  // -m/(z_k - z_c) = (-tr, ti)
-            sr = df_add(sr, {-tr.h, -tr.l});
-            si = df_add(si, ti);
-            const float si_s = __fmul_rn(inv.h, fscale);
-            const float fwr = __fmul_rn(dx.h, si_s), fwi = -__fmul_rn(dy.h, si_s);  // s / (z_k - z_c)
-            float fr = -tr.h, fi = ti.h;
+        for (int j = 0; j < (cnt + 63) / 64; ++j) {
+            const int ka = lane + 64 * j, kb = ka + 32;
+            const int2 ca = scl[ka], cb = scl[kb];
+            const bool near_a = abs(ca.x - ex) <= 1 && abs(ca.y - ey) <= 1;
+            const bool near_b = abs(cb.x - ex) <= 1 && abs(cb.y - ey) <= 1;
+            const FarTerm A = far_term(near_a ? pad : sq[ka], zxh, zxl, zyh, zyl, fscale);
+            const FarTerm B = far_term(near_b ? pad : sq[kb], zxh, zxl, zyh, zyl, fscale);
+            sr = df_add(sr, {-A.tr.h, -A.tr.l});
+            si = df_add(si, A.ti);
+            sr = df_add(sr, {-B.tr.h, -B.tr.l});
+            si = df_add(si, B.ti);
+            float2 fr = f2c(-A.tr.h, -B.tr.h), fi = f2c(A.ti.h, B.ti.h);
+            const float2 wr = f2c(A.wr, B.wr), wi = f2c(A.wi, B.wi), nwi = f2c(-A.wi, -B.wi);
 #pragma unroll
             for (int p = 0; p < kPtMax; ++p) {
-                const float nr = fr * fwr - fi * fwi, ni = fr * fwi + fi * fwr;
-                fr = nr;
-                fi = ni;
-                pr[p] += fr;
-                pi[p] += fi;
+                const float2 tr = __fmul2_rn(fr, wr), ti = __fmul2_rn(fr, wi);
+                fr = __ffma2_rn(fi, nwi, tr);  // fr wr - fi wi
+                fi = __ffma2_rn(fi, wr, ti);   // fr wi + fi wr
+                pr[p] += __fadd_rn(fr.x, fr.y);
+                pi[p] += __fadd_rn(fi.x, fi.y);
             }
         }
         b0r += (double)sr.h + (double)sr.l;
