@@ -450,6 +450,10 @@ int mlens_fit_far_field(mlens_ctx *ctx, const mlens_grid *rays, const mlens_fit_
  * row_begin/row_end restrict the call to ray rows [row_begin, row_end) (both
  * multiples of 32; 0, 0 = all rows); a restricted call copies a filtered work
  * list into a device buffer the context allocates on first use.
+ * The network's tensor-core waits are bounded: if one gives up (not expected on a
+ * working device) the kernel stops using the tensor cores, drains and frees its
+ * tensor memory, and a call with stats_host returns MLENS_ERR_CUDA (the map is
+ * invalid); a call without stats_host does not check.
  */
 int mlens_shoot_learned(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid *src, uint32_t *counts_dev,
                         void *beta_dev, int32_t row_begin, int32_t row_end, uint32_t flags, mlens_stats *stats_host,
@@ -482,6 +486,17 @@ int mlens_load_far_field(mlens_ctx *ctx, const char *path, void *stream);
  */
 int mlens_ff_eval(const float *params_dev, const float *z_dev, const float *u_dev, const float *t_dev, int64_t n,
                   float *y_dev, float *grads_dev, float *dz_dev, float *loss_host, void *stream);
+
+/*
+ * mlens_debug_wait_probe -- test aid for the failure path of the tensor-core waits
+ * (training, validation, mlens_ff_eval, the learned shoot).  While on (nonzero),
+ * each such launch's first completion wait polls an mbarrier nothing arrives on,
+ * 1024 times, so the bounded wait runs out: the kernel flags it, drains its
+ * in-flight tensor-core work (bounded), frees its tensor memory and returns, and
+ * the call reports MLENS_ERR_CUDA (the learned shoot when stats_host is given).
+ * No fault, no hang; contexts stay usable.  Process-wide; 0 turns it off.
+ */
+int mlens_debug_wait_probe(int32_t on);
 
 /* Free a context's device memory (waits for its device).  NULL is ignored. */
 void mlens_destroy(mlens_ctx *ctx);

@@ -371,6 +371,7 @@ cudaError_t ff_prep_bf16(const float *params, __nv_bfloat16 *w1zb, __nv_bfloat16
 
 // ===================================================== training kernel
 constexpr int kWaitPolls = 1 << 20;  // bound on a tensor-core completion wait
+constexpr int kProbePolls = 1024;    // bound on a probe wait (an mbarrier nothing arrives on)
 constexpr int kSampC = 128;          // samples per CTA = tensor-memory lanes of one accumulator
 constexpr int kGP = kParams + 2;     // gpart row: the parameters' gradients, then the loss
 
@@ -491,9 +492,11 @@ __device__ __forceinline__ void tc_publish()
 
 // Wait (bounded) for the MMAs committed to *bar; true when every thread saw them
 // complete.
-__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t &phase)
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t &phase, uint64_t *probe = nullptr)
 {
-    const bool ok = umma::mbar_wait(bar, phase, kWaitPolls);
+    // probe (test aid): wait instead on an mbarrier nothing arrives on, so the
+    // bounded wait runs out and the failure path is taken
+    const bool ok = probe ? umma::mbar_wait(probe, 0, kProbePolls) : umma::mbar_wait(bar, phase, kWaitPolls);
     if (__syncthreads_or(!ok)) return false;
     phase ^= 1u;
     umma::fence_after();
@@ -526,8 +529,8 @@ __device__ __forceinline__ void tc_gemm(uint32_t d, const unsigned char *A, cons
 // caller drains and reports).  Thread (warpgroup wg, s = tid % 128) owns sample s
 // and, of each 64-wide accumulator, the columns 32 wg .. 32 wg + 31 (tensor-memory
 // lane s is readable by warp s / 32 of either warpgroup).
-__device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S, uint64_t *bar, uint32_t tm,
-                                           uint32_t &phase)
+__device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S, uint64_t *bar, uint64_t *idle,
+                                           uint32_t tm, uint32_t &phase)
 {
     using L = TrainTc;
     float *F = reinterpret_cast<float *>(S);  // byte offsets / 4 below
@@ -573,7 +576,7 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
         tc_gemm(tm + L::cH1, S + L::Z, S + L::W1z, kLat, umma::idesc_bf16(128, kHid));
         umma::commit(bar);
     }
-    if (!tc_wait(bar, phase)) return false;
+    if (!tc_wait(bar, phase, A.wait_probe ? idle : nullptr)) return false;
     const float ux = F[L::U / 4 + 2 * s], uy = F[L::U / 4 + 2 * s + 1];
     float h1[32];
     tc_load32(tm + lane_base + L::cH1 + c0, h1);
@@ -782,7 +785,7 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
 __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
 {
     extern __shared__ __align__(1024) unsigned char tsm[];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar, idle;  // MMA completion; a barrier nothing arrives on (probe)
     __shared__ uint32_t tmem;
     using L = TrainTc;
     float *F = reinterpret_cast<float *>(tsm);
@@ -842,6 +845,7 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
     }
     if (tid == 0) {
         umma::mbar_init(&bar, 1);
+        umma::mbar_init(&idle, 1);
         umma::fence_mbar_init();
     }
     if (tid < 32) umma::tmem_alloc(&tmem, L::ncols);
@@ -850,7 +854,7 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
     umma::fence_after();
     const uint32_t tm = tmem;
     uint32_t phase = 0;
-    if (!train_step(A, tsm, &bar, tm, phase) && tid == 0) {
+    if (!train_step(A, tsm, &bar, &idle, tm, phase) && tid == 0) {
         // a completion wait gave up: flag it and drain (bounded) before freeing
         // the tensor memory
         if (A.err) atomicExch(A.err, 1);
@@ -999,6 +1003,7 @@ cudaError_t ff_flags(const unsigned *maxerr, int nrc, float tol, int *flags, cud
 struct LearnSmem {
     __align__(128) unsigned char w2cm[kHid * kHid * 2];  // W2 [out][in], BF16, core-matrix layout (B operand)
     uint64_t mbar[2];     // per warpgroup: completion of its tensor-core MMAs
+    uint64_t idle;        // an mbarrier nothing arrives on (the wait probe, a test aid)
     uint32_t tmem;        // tensor-memory base: 128 columns, 64 per warpgroup
     int wg_ok[8];         // per warp: the last wait completed
     int tc_dead[2];       // per warpgroup: a wait gave up; no more MMAs
@@ -1180,7 +1185,10 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
                                        ks > 0 ? 1u : 0u);
                     umma::commit(&ls.mbar[wg]);
                 }
-                const bool ok = __all_sync(0xffffffffu, umma::mbar_wait(&ls.mbar[wg], phase, kWaitPolls));
+                // (the wait probe, a test aid, polls ls.idle instead: the wait runs out and
+                // the warpgroup takes the failure path below)
+                const bool ok = __all_sync(0xffffffffu, L.wait_probe ? umma::mbar_wait(&ls.idle, 0, kProbePolls)
+                                                                     : umma::mbar_wait(&ls.mbar[wg], phase, kWaitPolls));
                 if (lane == 0) ls.wg_ok[warp] = ok ? 1 : 0;
                 umma::wg_sync(wg);
                 const bool wg_ok = ls.wg_ok[4 * wg] && ls.wg_ok[4 * wg + 1] && ls.wg_ok[4 * wg + 2] &&
@@ -1333,6 +1341,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_shoot_learned(LearnedArgs L)
         if (tid == 0) {
             umma::mbar_init(&ls.mbar[0], 1);
             umma::mbar_init(&ls.mbar[1], 1);
+            umma::mbar_init(&ls.idle, 1);
             umma::fence_mbar_init();
         }
         if (tid < 32) umma::tmem_alloc(&ls.tmem, 2 * kHid);

@@ -57,6 +57,7 @@ struct LearnedArgs {
     int64_t nitems;
     unsigned long long *counter;
     int *err;                  // set to 1 if a tensor-core completion wait gave up (results invalid)
+    int wait_probe;            // test aid: each warpgroup's first wait polls an mbarrier nothing arrives on
 };
 
 // Sample generation for training / validation (counter-based, SplitMix64).
@@ -98,6 +99,7 @@ struct TrainArgs {
     double *val_sum;                   // [2]: sum of errors (network, series)
     int backward;                      // 0 = forward only (validation)
     int *err;                          // set to 1 if a tensor-core completion wait gave up (nullable)
+    int wait_probe;                    // test aid: the CTA's first wait polls an mbarrier nothing arrives on
 };
 
 // launchers (farfield.cu)

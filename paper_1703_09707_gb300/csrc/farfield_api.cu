@@ -9,6 +9,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <string>
@@ -155,6 +156,10 @@ int alloc_state(FarState *f, int64_t nstars)
     return MLENS_OK;
 }
 
+// Test aid (mlens_debug_wait_probe): tensor-core waits poll an mbarrier nothing
+// arrives on, so their bounded-wait failure path runs.
+std::atomic<int> g_wait_probe{0};
+
 TrainArgs train_args(FarState *f)
 {
     TrainArgs t{};
@@ -175,6 +180,7 @@ TrainArgs train_args(FarState *f)
     t.spec.nrc = f->nrc;
     t.backward = 1;
     t.err = f->d_err;
+    t.wait_probe = g_wait_probe.load();
     return t;
 }
 
@@ -483,6 +489,7 @@ int mlens_shoot_learned(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid
     L.nitems = nitems;
     L.counter = f->counter;
     L.err = f->d_err;
+    L.wait_probe = g_wait_probe.load();
     // Fallback tiles (each a full plain tile over all stars) run first, each split
     // over a cluster of CTAs so that a few flagged cells do not set the map's
     // time; the persistent learned kernel then takes the learned tiles.
@@ -651,6 +658,12 @@ int mlens_load_far_field(mlens_ctx *ctx, const char *path, void *stream)
     return MLENS_OK;
 }
 
+int mlens_debug_wait_probe(int32_t on)
+{
+    g_wait_probe.store(on ? 1 : 0);
+    return MLENS_OK;
+}
+
 // ------------------------------------------- network verification entry
 int mlens_ff_eval(const float *params_dev, const float *z_dev, const float *u_dev, const float *t_dev, int64_t nsamples,
                   float *y_dev, float *grads_dev, float *dz_dev, float *loss_host, void *stream)
@@ -686,6 +699,7 @@ int mlens_ff_eval(const float *params_dev, const float *z_dev, const float *u_de
         t.dzout = dz_dev;
         t.backward = grads_dev ? 1 : 0;
         t.err = reinterpret_cast<int *>(dl + 1);
+        t.wait_probe = g_wait_probe.load();
         e = ff_train_step(t, nsamples, s);
         if (e == cudaSuccess && grads_dev) e = ff_reduce_grads(gpart, nblk, grads_dev, dl, s);
     }

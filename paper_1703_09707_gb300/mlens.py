@@ -127,6 +127,7 @@ SIGNATURES = {
     "mlens_destroy": (None, [_vp]),
     "mlens_last_error": (C.c_char_p, []),
     "mlens_set_device_memory_limit": (C.c_int, [C.c_uint64]),
+    "mlens_debug_wait_probe": (C.c_int, [C.c_int32]),
     "mlens_device_memory_in_use": (C.c_uint64, []),
     "mlens_version": (C.c_int, []),
 }
@@ -163,6 +164,12 @@ def mlens_last_error() -> str:
 
 def mlens_set_device_memory_limit(nbytes: int):
     _check(load().mlens_set_device_memory_limit(int(nbytes)))
+
+
+def mlens_debug_wait_probe(on: bool):
+    """Test aid: tensor-core completion waits poll an mbarrier nothing arrives on
+    (their bounded-wait failure path runs; calls report MLENS_ERR_CUDA)."""
+    _check(load().mlens_debug_wait_probe(1 if on else 0))
 
 
 def mlens_device_memory_in_use() -> int:

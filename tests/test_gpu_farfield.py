@@ -280,3 +280,43 @@ def test_fit_is_bit_reproducible(field):
         assert np.array_equal(np.asarray(e0[k]).view(np.uint32), np.asarray(e1[k]).view(np.uint32)), k
     assert r0["final_loss"] == r1["final_loss"] and r0["cells_fallback"] == r1["cells_fallback"]
     assert np.array_equal(c0, c1) and s0 == s1
+
+
+def test_tensor_core_wait_that_runs_out_is_reported_and_recovered(field):
+    """The bounded tensor-core waits' failure path, without a fault: with the wait
+    probe on, each launch's first completion wait polls an mbarrier nothing arrives
+    on and gives up; the kernel flags it, drains its MMAs (bounded), frees its tensor
+    memory and returns.  The learned shoot, a fit (training and validation) and
+    mlens_ff_eval must each report MLENS_ERR_CUDA; afterwards the same context
+    shoots the same map bit for bit, and a fit succeeds again."""
+    ctx = make_ctx(field)
+    prm = M.fit_params(cells_x=CELLS_X, use_network=1, order=6, train_samples=1 << 16, epochs=1, tolerance=1.0)
+    M.mlens_fit_far_field(ctx, RAYS, prm)
+    ref = learned_map(ctx)
+    rng = np.random.default_rng(5)
+    p = mlp.init_params(rng)
+    flat = torch.from_numpy(_flat(p)).cuda()
+    z = torch.from_numpy(rng.normal(0, 0.5, (256, 32)).astype(np.float32)).cuda()
+    u = torch.from_numpy(rng.uniform(-1, 1, (256, 2)).astype(np.float32)).cuda()
+    t = torch.zeros((256, 2), dtype=torch.float32, device="cuda")
+    g = torch.empty(flat.shape[0], dtype=torch.float32, device="cuda")
+    M.mlens_debug_wait_probe(True)
+    try:
+        with pytest.raises(M.MlensError) as ei:
+            learned_map(ctx)
+        assert ei.value.code == M.MLENS_ERR_CUDA
+        with pytest.raises(M.MlensError) as ei:
+            M.mlens_ff_eval(flat, z, u, t, grads=g)
+        assert ei.value.code == M.MLENS_ERR_CUDA
+        ctx2 = make_ctx(field)
+        with pytest.raises(M.MlensError) as ei:
+            M.mlens_fit_far_field(ctx2, RAYS, prm)
+        assert ei.value.code == M.MLENS_ERR_CUDA
+    finally:
+        M.mlens_debug_wait_probe(False)
+    again = learned_map(ctx)
+    assert np.array_equal(again[0], ref[0]) and again[1] == ref[1]
+    M.mlens_fit_far_field(ctx2, RAYS, prm)
+    learned_map(ctx2)
+    ctx2.close()
+    ctx.close()
