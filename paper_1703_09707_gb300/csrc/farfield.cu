@@ -1008,8 +1008,11 @@ struct LearnSmem {
     int wg_ok[8];         // per warp: the last wait completed
     int tc_dead[2];       // per warpgroup: a wait gave up; no more MMAs
     uint32_t pending[2];  // the phase a dead warpgroup still waits for
-    float4 l1[kHid];  // per hidden unit: {e_c (this tile's cell), W1u[.][0], W1u[.][1], b2}
-    float2 l3[kHid];  // per hidden unit: {W3[0][.], W3[1][.]}
+    // per pair of hidden units (c, c + 1), c = 2 P, in the order packed f32x2 operations take them:
+    float4 l1p[kHid / 2];  // {e_c, e_c+1 (this tile's cell), W1u[c][0], W1u[c+1][0]}
+    float2 l1q[kHid / 2];  // {W1u[c][1], W1u[c+1][1]}
+    float4 l2p[kHid / 2];  // {b2[c], b2[c+1], W3[0][c], W3[0][c+1]}
+    float2 l2q[kHid / 2];  // {W3[1][c], W3[1][c+1]}
     float b3[2];
     float coef[kCoefStride];
     float sc;
@@ -1018,6 +1021,15 @@ struct LearnSmem {
 };
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+
+// SiLU of two hidden units at once, as silu_hw: h = v / 2, h + h tanh(h) with the
+// hardware tanh (packed FP32 for the multiply and the FMA).
+static_assert(kLayer2Hw, "the packed network block uses the hardware-tanh SiLU in both layers");
+__device__ __forceinline__ float2 silu_hw2(float2 v)
+{
+    const float2 h = __fmul2_rn(v, make_float2(0.5f, 0.5f));
+    return __ffma2_rn(h, make_float2(tanh_hw(h.x), tanh_hw(h.y)), h);
+}
 
 // One tile of a non-flagged cell: near stars exactly (FP32 recentred + Kahan,
 // as the plain kernel), far field = float-pair b0 + series to order pe +
@@ -1069,7 +1081,7 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
         ls.sc = L.sc[rc];
     }
     if (tid < kCoefStride) ls.coef[tid] = L.coef[(int64_t)rc * kCoefStride + tid];
-    if (tid < kHid) ls.l1[tid].x = L.ec ? L.ec[(int64_t)rc * kHid + tid] : 0.0f;
+    if (tid < kHid) reinterpret_cast<float *>(&ls.l1p[tid >> 1])[tid & 1] = L.ec ? L.ec[(int64_t)rc * kHid + tid] : 0.0f;
     __syncthreads();
 
     float2 rx, ry[NP], px[NP], py[NP], Sx[NP], Sy[NP], Cx[NP], Cy[NP];
@@ -1159,16 +1171,19 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
             if (!ls.tc_dead[wg]) {
                 const float ux = (float)(2 * (ioff + (r & 63)) + 1) * inv_cx - 1.0f;
                 const float uy = (float)(2 * (joff + (r >> 6)) + 1) * inv_cy - 1.0f;
+                const float2 uxx = make_float2(ux, ux), uyy = make_float2(uy, uy);
 #pragma unroll
                 for (int k8 = 0; k8 < kHid / 8; ++k8) {
                     uint32_t pk[4];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int c0 = k8 * 8 + 2 * q;
-                        const float4 p0 = ls.l1[c0], p1 = ls.l1[c0 + 1];
-                        const float v0 = silu1(p0.x + p0.y * ux + p0.z * uy);
-                        const float v1 = silu1(p1.x + p1.y * ux + p1.z * uy);
-                        pk[q] = pack_bf16(v0, v1);
+                    for (int q = 0; q < 4; ++q) {  // units 8 k8 + 2 q and + 1
+                        const float4 pa = ls.l1p[4 * k8 + q];
+                        const float2 pb = ls.l1q[4 * k8 + q];
+                        // e_c + W1u[.][0] ux + W1u[.][1] uy, then SiLU, for both units
+                        float2 v = __ffma2_rn(make_float2(pa.z, pa.w), uxx, make_float2(pa.x, pa.y));
+                        v = __ffma2_rn(pb, uyy, v);
+                        const float2 a = silu_hw2(v);
+                        pk[q] = pack_bf16(a.x, a.y);
                     }
                     *reinterpret_cast<uint4 *>(abuf + umma::cm_offset(t, k8 * 8)) =
                         make_uint4(pk[0], pk[1], pk[2], pk[3]);
@@ -1196,19 +1211,25 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
                 if (wg_ok) {
                     phase ^= 1u;
                     umma::fence_after();
+                    // layer 2's bias and SiLU, and layer 3, two units at a time (even and
+                    // odd units summed apart, then added)
+                    float2 y0p = make_float2(0.0f, 0.0f), y1p = make_float2(0.0f, 0.0f);
 #pragma unroll
                     for (int c0 = 0; c0 < kHid; c0 += 16) {
                         uint32_t acc[16];
                         umma::ld16(dcol + lane_base + (uint32_t)c0, acc);
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const int col = c0 + j;
-                            const float a2 = silu2(__uint_as_float(acc[j]) + ls.l1[col].w);
-                            const float2 w3 = ls.l3[col];
-                            y0 += w3.x * a2;
-                            y1 += w3.y * a2;
+                        for (int j = 0; j < 16; j += 2) {
+                            const float4 qa = ls.l2p[(c0 + j) >> 1];
+                            const float2 qb = ls.l2q[(c0 + j) >> 1];
+                            const float2 a2 = silu_hw2(__fadd2_rn(
+                                make_float2(__uint_as_float(acc[j]), __uint_as_float(acc[j + 1])), make_float2(qa.x, qa.y)));
+                            y0p = __ffma2_rn(make_float2(qa.z, qa.w), a2, y0p);
+                            y1p = __ffma2_rn(qb, a2, y1p);
                         }
                     }
+                    y0 = y0p.x + y0p.y;
+                    y1 = y1p.x + y1p.y;
                 } else if (t == 0) {
                     // the MMAs never reported completion: stop using the tensor path,
                     // remember the phase to drain before tensor memory is freed
@@ -1331,10 +1352,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_shoot_learned(LearnedArgs L)
         for (int i = tid; i < kHid * kHid; i += kThreads)
             *reinterpret_cast<__nv_bfloat16 *>(ls.w2cm + umma::cm_offset(i / kHid, i % kHid)) = L.w2b[i];
         if (tid < kHid) {
-            ls.l1[tid].y = L.params[oW1u + 2 * tid];
-            ls.l1[tid].z = L.params[oW1u + 2 * tid + 1];
-            ls.l1[tid].w = L.params[ob2 + tid];
-            ls.l3[tid] = make_float2(L.params[oW3 + tid], L.params[oW3 + kHid + tid]);
+            const int P = tid >> 1, h = tid & 1;
+            reinterpret_cast<float *>(&ls.l1p[P])[2 + h] = L.params[oW1u + 2 * tid];
+            reinterpret_cast<float *>(&ls.l1q[P])[h] = L.params[oW1u + 2 * tid + 1];
+            reinterpret_cast<float *>(&ls.l2p[P])[h] = L.params[ob2 + tid];
+            reinterpret_cast<float *>(&ls.l2p[P])[2 + h] = L.params[oW3 + tid];
+            reinterpret_cast<float *>(&ls.l2q[P])[h] = L.params[oW3 + kHid + tid];
         }
         if (tid < 2) ls.b3[tid] = L.params[ob3 + tid];
         if (tid < 2) ls.tc_dead[tid] = 0;
