@@ -36,111 +36,146 @@ constexpr int kMaxDiskRows = 4096;
 
 __host__ __device__ constexpr int taps_padded(int K) { return (2 * K + 1 + 3) / 4 * 4; }
 
-// Row pass.  A CTA takes kRowOut outputs of one row; thread t computes the four
-// consecutive outputs 4t .. 4t+3 with a sliding window stepped four taps at a
-// time: per four taps one float4 weight load (broadcast), four input loads and
-// sixteen FMAs.  The weights are zero-padded to a multiple of four (adding exact
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Row pass.  A CTA takes kRowOut outputs of two adjacent rows; thread t computes
+// the four consecutive outputs 4t .. 4t+3 of both rows, the rows packed into the
+// two lanes of f32x2 registers (FFMA2), with a sliding window stepped four taps
+// at a time: per four taps two float4 loads of duplicated weights (broadcast),
+// four float2 input loads and sixteen FFMA2 = 32 multiply-adds.  Each output
+// takes its taps in the same order as a scalar loop would: the packing changes
+// no result.  The weights are zero-padded to a multiple of four (adding exact
 // zeros).  The staged inputs are stored de-interleaved by index mod 4 (plane
-// e % 4, slot e / 4) so that the lanes' loads of element 4t + k hit 32
-// different banks.
+// e % 4, slot e / 4) so that the lanes' loads of element 4t + k are consecutive.
 __global__ void __launch_bounds__(kThr) k_gauss_rows(const uint32_t *__restrict__ in, int nx, int ny,
                                                      const float *__restrict__ w, int K, float *__restrict__ out)
 {
     extern __shared__ float4 sm4[];
-    float *ws = reinterpret_cast<float *>(sm4);  // Kp weights
     const int Kp = taps_padded(K);
-    const int E = kRowOut + Kp + 3;              // staged inputs
+    float2 *ws = reinterpret_cast<float2 *>(sm4);  // Kp weights, each duplicated (w, w)
+    const int E = kRowOut + Kp + 3;                // staged inputs per row
     const int P = E / 4 + 1;
-    float *xs = ws + Kp;                          // 4 planes of P floats
+    float2 *xs = ws + Kp;                          // 4 planes of P (row j, row j + 1) pairs
     const int tid = threadIdx.x;
-    for (int k = tid; k < Kp; k += kThr) ws[k] = k <= 2 * K ? w[k] : 0.0f;
+    for (int k = tid; k < Kp; k += kThr) {
+        const float v = k <= 2 * K ? w[k] : 0.0f;
+        ws[k] = make_float2(v, v);
+    }
     const int i0 = blockIdx.x * kRowOut;
     const int o = 4 * tid;  // this thread's first output within the tile
-    for (int64_t j = blockIdx.y; j < ny; j += gridDim.y) {
-        const uint32_t *row = in + j * nx;
-        __syncthreads();  // previous row's taps are done
+    for (int64_t j = 2 * (int64_t)blockIdx.y; j < ny; j += 2 * (int64_t)gridDim.y) {
+        const bool two = j + 1 < ny;
+        const uint32_t *row0 = in + j * nx, *row1 = row0 + nx;
+        __syncthreads();  // previous rows' taps are done
         for (int e = tid; e < E; e += kThr) {
             const int i = i0 - K + e;
-            xs[(e & 3) * P + (e >> 2)] = (i >= 0 && i < nx) ? (float)row[i] : 0.0f;
+            const bool inside = i >= 0 && i < nx;
+            xs[(e & 3) * P + (e >> 2)] =
+                make_float2(inside ? (float)row0[i] : 0.0f, inside && two ? (float)row1[i] : 0.0f);
         }
         __syncthreads();
         if (i0 + o < nx) {
             // element 4t + 4m + d sits in plane d & 3, slot t + m + (d >> 2)
-            const float *b = xs + tid;
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-            float x0 = b[0], x1 = b[P], x2 = b[2 * P];
+            const float2 *b = xs + tid;
+            const float4 *wq = sm4;  // (w_2n, w_2n, w_2n+1, w_2n+1)
+            float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
+            float2 x0 = b[0], x1 = b[P], x2 = b[2 * P];
             for (int m = 0; m < Kp / 4; ++m) {
-                const float4 q = sm4[m];
-                const float x3 = b[3 * P + m], x4 = b[m + 1], x5 = b[P + m + 1], x6 = b[2 * P + m + 1];
-                a0 = __fmaf_rn(q.x, x0, a0); a1 = __fmaf_rn(q.x, x1, a1); a2 = __fmaf_rn(q.x, x2, a2); a3 = __fmaf_rn(q.x, x3, a3);
-                a0 = __fmaf_rn(q.y, x1, a0); a1 = __fmaf_rn(q.y, x2, a1); a2 = __fmaf_rn(q.y, x3, a2); a3 = __fmaf_rn(q.y, x4, a3);
-                a0 = __fmaf_rn(q.z, x2, a0); a1 = __fmaf_rn(q.z, x3, a1); a2 = __fmaf_rn(q.z, x4, a2); a3 = __fmaf_rn(q.z, x5, a3);
-                a0 = __fmaf_rn(q.w, x3, a0); a1 = __fmaf_rn(q.w, x4, a1); a2 = __fmaf_rn(q.w, x5, a2); a3 = __fmaf_rn(q.w, x6, a3);
+                const float4 qa = wq[2 * m], qb = wq[2 * m + 1];
+                const float2 w0 = make_float2(qa.x, qa.y), w1 = make_float2(qa.z, qa.w);
+                const float2 w2 = make_float2(qb.x, qb.y), w3 = make_float2(qb.z, qb.w);
+                const float2 x3 = b[3 * P + m], x4 = b[m + 1], x5 = b[P + m + 1], x6 = b[2 * P + m + 1];
+                a0 = ffma2(w0, x0, a0); a1 = ffma2(w0, x1, a1); a2 = ffma2(w0, x2, a2); a3 = ffma2(w0, x3, a3);
+                a0 = ffma2(w1, x1, a0); a1 = ffma2(w1, x2, a1); a2 = ffma2(w1, x3, a2); a3 = ffma2(w1, x4, a3);
+                a0 = ffma2(w2, x2, a0); a1 = ffma2(w2, x3, a1); a2 = ffma2(w2, x4, a2); a3 = ffma2(w2, x5, a3);
+                a0 = ffma2(w3, x3, a0); a1 = ffma2(w3, x4, a1); a2 = ffma2(w3, x5, a2); a3 = ffma2(w3, x6, a3);
                 x0 = x4;
                 x1 = x5;
                 x2 = x6;
             }
-            float *orow = out + j * nx + i0 + o;
             const int n = min(4, nx - (i0 + o));
-            orow[0] = a0;
-            if (n > 1) orow[1] = a1;
-            if (n > 2) orow[2] = a2;
-            if (n > 3) orow[3] = a3;
+            float *orow = out + j * nx + i0 + o;
+            orow[0] = a0.x;
+            if (n > 1) orow[1] = a1.x;
+            if (n > 2) orow[2] = a2.x;
+            if (n > 3) orow[3] = a3.x;
+            if (two) {
+                orow += nx;
+                orow[0] = a0.y;
+                if (n > 1) orow[1] = a1.y;
+                if (n > 2) orow[2] = a2.y;
+                if (n > 3) orow[3] = a3.y;
+            }
         }
     }
 }
 
-// Column pass.  A CTA stages kColY + Kp + 3 rows of 64 columns; thread (c, g)
-// computes rows 32g .. 32g+31 of column c in blocks of four consecutive rows, with
-// the same four-taps-at-a-time window (the lanes of a warp read 32 consecutive
-// columns of one staged row: no bank conflicts).
+// Column pass.  A CTA stages kColY + Kp + 3 rows of 64 columns; thread (p, g)
+// computes rows 16g .. 16g+15 of the adjacent columns 2p and 2p + 1 (packed into
+// f32x2 lanes) in blocks of eight consecutive rows, with the same four-taps-at-a-
+// time window (the lanes of a warp read 32 consecutive column pairs of one staged
+// row).  As in the row pass, every output's taps keep their order.
 __global__ void __launch_bounds__(kThr) k_gauss_cols(const float *__restrict__ in, int nx, int ny,
                                                      const float *__restrict__ w, int K, float scale,
                                                      float *__restrict__ out)
 {
     extern __shared__ float4 sm4[];
-    float *ws = reinterpret_cast<float *>(sm4);  // Kp weights
     const int Kp = taps_padded(K);
-    float *tile = ws + Kp;                        // (kColY + Kp + 3) rows x kColX columns
+    float2 *ws = reinterpret_cast<float2 *>(sm4);        // Kp weights, each duplicated (w, w)
+    float *tile = reinterpret_cast<float *>(ws + Kp);    // (kColY + Kp + 3) rows x kColX columns
     const int tid = threadIdx.x;
-    for (int k = tid; k < Kp; k += kThr) ws[k] = k <= 2 * K ? w[k] : 0.0f;
-    const int c = tid % kColX, g = tid / kColX;  // 4 groups of kColY / 4 rows
-    const int i = blockIdx.x * kColX + c;
+    for (int k = tid; k < Kp; k += kThr) {
+        const float v = k <= 2 * K ? w[k] : 0.0f;
+        ws[k] = make_float2(v, v);
+    }
+    const int lc = tid % kColX, lg = tid / kColX;        // staging: column, row group
+    const int cp = tid % (kColX / 2), g = tid / (kColX / 2);  // compute: column pair, group of kColY / 8 rows
+    const int il = blockIdx.x * kColX + lc;
+    const int i = blockIdx.x * kColX + 2 * cp;           // first column of this thread's pair
     const int rows = kColY + Kp + 3;
     const int tiles_y = (ny + kColY - 1) / kColY;
     for (int ty = blockIdx.y; ty < tiles_y; ty += gridDim.y) {
         const int64_t j0 = (int64_t)ty * kColY;
         __syncthreads();
-        for (int r = g; r < rows; r += kThr / kColX) {
+        for (int r = lg; r < rows; r += kThr / kColX) {
             const int64_t j = j0 - K + r;
-            tile[r * kColX + c] = (i < nx && j >= 0 && j < ny) ? in[j * nx + i] : 0.0f;
+            tile[r * kColX + lc] = (il < nx && j >= 0 && j < ny) ? in[j * nx + il] : 0.0f;
         }
         __syncthreads();
         if (i >= nx) continue;
-        for (int r = g * (kColY / 4); r < (g + 1) * (kColY / 4); r += 8) {
+        const bool two = i + 1 < nx;
+        for (int r = g * (kColY / 8); r < (g + 1) * (kColY / 8); r += 8) {
             if (j0 + r >= ny) break;
-            const float *T = tile + r * kColX + c;
-            float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            float x[11];
+            const float2 *T = reinterpret_cast<const float2 *>(tile + r * kColX + 2 * cp);
+            constexpr int S = kColX / 2;  // float2 per staged row
+            float2 a[8], x[11];
 #pragma unroll
-            for (int q = 0; q < 7; ++q) x[q] = T[q * kColX];
+            for (int q = 0; q < 8; ++q) a[q] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < 7; ++q) x[q] = T[q * S];
             for (int k = 0; k < Kp; k += 4) {
-                const float4 wq = sm4[k >> 2];
+                const float4 qa = sm4[k >> 1], qb = sm4[(k >> 1) + 1];
+                const float2 w0 = make_float2(qa.x, qa.y), w1 = make_float2(qa.z, qa.w);
+                const float2 w2 = make_float2(qb.x, qb.y), w3 = make_float2(qb.z, qb.w);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) x[7 + q] = T[(k + 7 + q) * kColX];
+                for (int q = 0; q < 4; ++q) x[7 + q] = T[(k + 7 + q) * S];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    a[q] = __fmaf_rn(wq.x, x[q], a[q]);
-                    a[q] = __fmaf_rn(wq.y, x[q + 1], a[q]);
-                    a[q] = __fmaf_rn(wq.z, x[q + 2], a[q]);
-                    a[q] = __fmaf_rn(wq.w, x[q + 3], a[q]);
+                    a[q] = ffma2(w0, x[q], a[q]);
+                    a[q] = ffma2(w1, x[q + 1], a[q]);
+                    a[q] = ffma2(w2, x[q + 2], a[q]);
+                    a[q] = ffma2(w3, x[q + 3], a[q]);
                 }
 #pragma unroll
                 for (int q = 0; q < 7; ++q) x[q] = x[q + 4];
             }
 #pragma unroll
             for (int q = 0; q < 8; ++q)
-                if (j0 + r + q < ny) out[(j0 + r + q) * nx + i] = __fmul_rn(a[q], scale);
+                if (j0 + r + q < ny) {
+                    float *dst = out + (j0 + r + q) * nx + i;
+                    dst[0] = __fmul_rn(a[q].x, scale);
+                    if (two) dst[1] = __fmul_rn(a[q].y, scale);
+                }
         }
     }
 }
@@ -399,14 +434,14 @@ int run_convolution(const uint32_t *counts_dev, const mlens_grid *src, int32_t p
         k_gauss_weights<<<1, kThr, 0, s>>>(size, dy, pl.Ky, wy);
         if ((e = cudaGetLastError()) != cudaSuccess) return lc_cuda(e, "weights launch");
         const int kpx = taps_padded(pl.Kx), kpy = taps_padded(pl.Ky);
-        const size_t sm_r = (size_t)(kpx + 4 * ((kRowOut + kpx + 3) / 4 + 1)) * sizeof(float);
-        const size_t sm_c = (size_t)(kpy + (kColY + kpy + 3) * kColX) * sizeof(float);
+        const size_t sm_r = (size_t)(kpx + 4 * ((kRowOut + kpx + 3) / 4 + 1)) * sizeof(float2);
+        const size_t sm_c = (size_t)(2 * kpy + (kColY + kpy + 3) * kColX) * sizeof(float);
         if ((e = cudaFuncSetAttribute(k_gauss_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_r)) !=
                 cudaSuccess ||
             (e = cudaFuncSetAttribute(k_gauss_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c)) !=
                 cudaSuccess)
             return lc_cuda(e, "cudaFuncSetAttribute");
-        const dim3 gr((unsigned)((nx + kRowOut - 1) / kRowOut), (unsigned)std::min<int64_t>(ny, 65535));
+        const dim3 gr((unsigned)((nx + kRowOut - 1) / kRowOut), (unsigned)std::min<int64_t>((ny + 1) / 2, 65535));
         k_gauss_rows<<<gr, kThr, sm_r, s>>>(counts_dev, nx, ny, wx, pl.Kx, t);
         if ((e = cudaGetLastError()) != cudaSuccess) return lc_cuda(e, "row pass launch");
         const int64_t tiles_y = (ny + kColY - 1) / kColY;
