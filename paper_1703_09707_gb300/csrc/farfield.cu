@@ -530,7 +530,7 @@ __device__ __forceinline__ void tc_gemm(uint32_t d, const unsigned char *A, cons
 // and, of each 64-wide accumulator, the columns 32 wg .. 32 wg + 31 (tensor-memory
 // lane s is readable by warp s / 32 of either warpgroup).
 __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S, uint64_t *bar, uint64_t *idle,
-                                           uint32_t tm, uint32_t &phase)
+                                           uint32_t tm, uint32_t &phase, const float (&zv)[16])
 {
     using L = TrainTc;
     float *F = reinterpret_cast<float *>(S);  // byte offsets / 4 below
@@ -542,26 +542,8 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
     const bool expl = A.zin != nullptr;
     float *Slot = F + L::Slots / 4 + warp * 6 * 32;
 
-    // ---- latents: thread (wg, s) takes columns 16 wg .. 16 wg + 15 of z_s
+    // ---- latents (gathered at kernel start): thread (wg, s) has columns 16 wg .. 16 wg + 15 of z_s
     {
-        const int rc = I[L::RC / 4 + s];
-        const bool ok = I[L::OK / 4 + s] != 0;
-        float zv[16];
-        const float *src = (expl ? A.zin + (cbase + s) * kLat : A.z + (int64_t)rc * kLat) + 16 * wg;
-        if (!ok) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) zv[j] = 0.0f;
-        } else if (((uintptr_t)src & 7u) == 0) {  // the latents (after the 6530 parameters) are 8-byte aligned
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float2 v = reinterpret_cast<const float2 *>(src)[j];
-                zv[2 * j] = v.x;
-                zv[2 * j + 1] = v.y;
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) zv[j] = src[j];
-        }
 #pragma unroll
         for (int j = 0; j < 16; ++j) st_bf16(S, L::ZT + tc_off(16 * wg + j, s, kSampC), zv[j]);
 #pragma unroll
@@ -819,6 +801,31 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
         F[L::b2 / 4 + tid] = A.params[ob2 + tid];
     }
     if (tid < 2) F[L::b3 / 4 + tid] = A.params[ob3 + tid];
+    // ---- latents of this thread's sample (columns 16 wg .. 16 wg + 15), loaded first so
+    // that they are in flight during the sample generation: sample i's cell is
+    // (offset + i) mod nrc
+    float zv[16];
+    {
+        const int s = tid & (kSampC - 1), wg = tid >> 7;
+        const int64_t li = (int64_t)blockIdx.x * kSampC + s;
+        const bool ok = li < A.spec.count;
+        const float *src = A.zin ? A.zin + li * kLat : A.z + ((A.spec.offset + li) % A.spec.nrc) * kLat;
+        src += 16 * wg;
+        if (!ok) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) zv[j] = 0.0f;
+        } else if (((uintptr_t)src & 7u) == 0) {  // the latents (after the 6530 parameters) are 8-byte aligned
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float2 v = reinterpret_cast<const float2 *>(src)[j];
+                zv[2 * j] = v.x;
+                zv[2 * j + 1] = v.y;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) zv[j] = src[j];
+        }
+    }
     // ---- samples
     if (tid < kSampC) {
         const int64_t li = (int64_t)blockIdx.x * kSampC + tid;
@@ -854,7 +861,7 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
     umma::fence_after();
     const uint32_t tm = tmem;
     uint32_t phase = 0;
-    if (!train_step(A, tsm, &bar, &idle, tm, phase) && tid == 0) {
+    if (!train_step(A, tsm, &bar, &idle, tm, phase, zv) && tid == 0) {
         // a completion wait gave up: flag it and drain (bounded) before freeing
         // the tensor memory
         if (A.err) atomicExch(A.err, 1);
