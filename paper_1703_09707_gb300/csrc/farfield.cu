@@ -389,13 +389,13 @@ struct TrainTc {
     static constexpr int W2 = W1z + kHid * kLat * 2;     // [64 out][64 in]  layer 2
     static constexpr int W2T = W2 + kHid * kHid * 2;     // [64 in][64 out]  da1 = dh2 W2
     static constexpr int W1zT = W2T + kHid * kHid * 2;   // [32 in][64 out]  dz = dh1 W1z
-    // A operands (M = 128 samples x K)
-    static constexpr int Z = W1zT + kLat * kHid * 2;     // [128][32]
-    static constexpr int A1 = Z + kSampC * kLat * 2;     // [128][64]
-    static constexpr int DH2 = A1 + kSampC * kHid * 2;   // [128][64]
-    static constexpr int DH1 = DH2 + kSampC * kHid * 2;  // [128][64]
+    // A operands (M = 128 samples x K), one region in turn: Z [128][32], then A1,
+    // dH2 and dH1 [128][64]; each is written only after the MMAs reading the
+    // previous one have completed
+    static constexpr int Z = W1zT + kLat * kHid * 2;
+    static constexpr int A1 = Z, DH2 = Z, DH1 = Z;
     // weight gradients: A = [dh2^T; dh1^T] (128 units x 128 samples), B = a1^T, z^T
-    static constexpr int ST = DH1 + kSampC * kHid * 2;   // [128][128]
+    static constexpr int ST = Z + kSampC * kHid * 2;     // [128][128]
     static constexpr int A1T = ST + 128 * kSampC * 2;    // [64][128]
     static constexpr int ZT = A1T + kHid * kSampC * 2;   // [32][128]
     static constexpr int EndOps = ZT + kLat * kSampC * 2;
@@ -414,8 +414,10 @@ struct TrainTc {
     static constexpr int Slots = YP + 2 * kSampC * 2 * 4;  // [8 warps][6][32] column sums over a warp's samples
     static constexpr int WS = Slots + 8 * 6 * 32 * 4;    // [8 warps][4]: sum dy0, sum dy1, loss
     static constexpr int bytes = WS + 8 * 4 * 4;
-    // tensor-memory columns of the six accumulators (all 128 lanes)
-    static constexpr int cH1 = 0, cH2 = 64, cDA1 = 128, cDZ = 192, cDW2 = 256, cDW1z = 320, ncols = 512;
+    // tensor-memory columns (all 128 lanes), reused once read: H1 and H2 first; dA1
+    // over H2 once the dh2 pass has read it; dW2 over H1, dZ and dW1z over dA1 once
+    // the dh1 pass has read both
+    static constexpr int cH1 = 0, cH2 = 64, cDA1 = 64, cDW2 = 0, cDZ = 64, cDW1z = 96, ncols = 128;
 };
 
 // One training / validation sample: a cell and a uniform position in its ray-covered
@@ -457,13 +459,16 @@ __device__ __forceinline__ void sample_of(const TrainArgs &A, int64_t li, int &r
     vp = powf(vr * vr + vi * vi, 0.5f * (float)(A.pe + 1));
 }
 
-// Warp reduce-scatter of 32 per-lane column vectors: afterwards v[0] of lane j
-// holds the sum over the warp's lanes of column j (fixed order: deterministic).
-__device__ __forceinline__ float warp_colsum(float (&v)[32])
+// Column sums of 16 per-lane values over the warp's 32 lanes: afterwards lanes j
+// and j + 16 hold the sum of column j (a fold, then a reduce-scatter; fixed order,
+// so deterministic).
+__device__ __forceinline__ float warp_colsum16(float (&v)[16])
 {
     const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int step = 16; step >= 1; step >>= 1) {
+    for (int i = 0; i < 16; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], 16);
+#pragma unroll
+    for (int step = 8; step >= 1; step >>= 1) {
         const bool up = (lane & step) != 0;
 #pragma unroll
         for (int i = 0; i < step; ++i) {
@@ -503,16 +508,20 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t &phase, uint64_t
     return true;
 }
 
-// 32 accumulator columns c0 .. c0 + 31 of this thread's lane.
-__device__ __forceinline__ void tc_load32(uint32_t taddr, float (&v)[32])
+// 16 accumulator columns of this thread's lane.
+__device__ __forceinline__ void tc_load16(uint32_t taddr, float (&v)[16])
 {
     uint32_t r[16];
     umma::ld16(taddr, r);
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-    umma::ld16(taddr + 16, r);
+}
+
+__device__ __forceinline__ void st_f4x4(float *dst, const float (&v)[16])  // 16-byte aligned
+{
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[16 + j] = __uint_as_float(r[j]);
+    for (int q = 0; q < 4; ++q)
+        reinterpret_cast<float4 *>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 
 // One thread issues D = sum_k A[:, k] B[:, k]^T over K / 16 MMAs of K = 16.
@@ -527,8 +536,10 @@ __device__ __forceinline__ void tc_gemm(uint32_t d, const unsigned char *A, cons
 
 // The step for the CTA's 128 samples; false if a tensor-core wait gave up (the
 // caller drains and reports).  Thread (warpgroup wg, s = tid % 128) owns sample s
-// and, of each 64-wide accumulator, the columns 32 wg .. 32 wg + 31 (tensor-memory
-// lane s is readable by warp s / 32 of either warpgroup).
+// and, of each 64-wide accumulator, the columns 32 wg .. 32 wg + 31, taken in two
+// halves of 16 (tensor-memory lane s is readable by warp s / 32 of either
+// warpgroup).  H1 and H2 are read back from tensor memory when the backward pass
+// needs them rather than held in registers: two CTAs fit per SM.
 __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S, uint64_t *bar, uint64_t *idle,
                                            uint32_t tm, uint32_t &phase, const float (&zv)[16])
 {
@@ -541,6 +552,19 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
     const int64_t cbase = (int64_t)blockIdx.x * kSampC;
     const bool expl = A.zin != nullptr;
     float *Slot = F + L::Slots / 4 + warp * 6 * 32;
+    const float ux = F[L::U / 4 + 2 * s], uy = F[L::U / 4 + 2 * s + 1];
+    // pre-activations of layer 1 / layer 2 for columns c .. c + 15, from tensor memory
+    auto load_h1 = [&](int c, float (&h)[16]) {
+        tc_load16(tm + lane_base + L::cH1 + c, h);
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            h[j] = h[j] + F[L::W1u / 4 + 2 * (c + j)] * ux + F[L::W1u / 4 + 2 * (c + j) + 1] * uy + F[L::b1 / 4 + c + j];
+    };
+    auto load_h2 = [&](int c, float (&h)[16]) {
+        tc_load16(tm + lane_base + L::cH2 + c, h);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) h[j] += F[L::b2 / 4 + c + j];
+    };
 
     // ---- latents (gathered at kernel start): thread (wg, s) has columns 16 wg .. 16 wg + 15 of z_s
     {
@@ -559,24 +583,22 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
         umma::commit(bar);
     }
     if (!tc_wait(bar, phase, A.wait_probe ? idle : nullptr)) return false;
-    const float ux = F[L::U / 4 + 2 * s], uy = F[L::U / 4 + 2 * s + 1];
-    float h1[32];
-    tc_load32(tm + lane_base + L::cH1 + c0, h1);
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const int c = c0 + j;
-        h1[j] = h1[j] + F[L::W1u / 4 + 2 * c] * ux + F[L::W1u / 4 + 2 * c + 1] * uy + F[L::b1 / 4 + c];
-    }
+    for (int hh = 0; hh < 2; ++hh) {  // A1 = silu(H1 + W1u u + b1) over the Z region (its MMAs are done)
+        const int c = c0 + 16 * hh;
+        float h1[16];
+        load_h1(c, h1);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        float a[8];
+        for (int q = 0; q < 2; ++q) {
+            float a[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            a[j] = silu1(h1[8 * q + j]);
-            st_bf16(S, L::A1T + tc_off(c0 + 8 * q + j, s, kSampC), a[j]);
+            for (int j = 0; j < 8; ++j) {
+                a[j] = silu1(h1[8 * q + j]);
+                st_bf16(S, L::A1T + tc_off(c + 8 * q + j, s, kSampC), a[j]);
+            }
+            *reinterpret_cast<uint4 *>(S + L::A1 + tc_off(s, c + 8 * q, kHid)) =
+                make_uint4(pack_bf16(a[0], a[1]), pack_bf16(a[2], a[3]), pack_bf16(a[4], a[5]), pack_bf16(a[6], a[7]));
         }
-        *reinterpret_cast<uint4 *>(S + L::A1 + tc_off(s, c0 + 8 * q, kHid)) =
-            make_uint4(pack_bf16(a[0], a[1]), pack_bf16(a[2], a[3]), pack_bf16(a[4], a[5]), pack_bf16(a[6], a[7]));
     }
     // ---- layer 2: H2 = A1 W2^T (M 128, N 64, K 64); layer 3 in FP32
     tc_publish();
@@ -585,17 +607,19 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
         umma::commit(bar);
     }
     if (!tc_wait(bar, phase)) return false;
-    float h2[32];
-    tc_load32(tm + lane_base + L::cH2 + c0, h2);
     {
         float y0 = 0.0f, y1 = 0.0f;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const int c = c0 + j;
-            h2[j] += F[L::b2 / 4 + c];
-            const float a2 = silu2(h2[j]);
-            y0 += F[L::W3 / 4 + c] * a2;
-            y1 += F[L::W3 / 4 + kHid + c] * a2;
+        for (int hh = 0; hh < 2; ++hh) {
+            const int c = c0 + 16 * hh;
+            float h2[16];
+            load_h2(c, h2);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float a2 = silu2(h2[j]);
+                y0 += F[L::W3 / 4 + c + j] * a2;
+                y1 += F[L::W3 / 4 + kHid + c + j] * a2;
+            }
         }
         F[L::YP / 4 + (wg * kSampC + s) * 2] = y0;
         F[L::YP / 4 + (wg * kSampC + s) * 2 + 1] = y1;
@@ -642,62 +666,77 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
             F[L::WS / 4 + warp * 4 + 2] = lsum;
         }
     }
-    // ---- dh2 = (dy W3) silu'(h2); FP32 column sums for b2 and W3
-    {
-        float v[32], w0[32], w1[32];
+    // ---- dh2 = (dy W3) silu'(h2) over the A1 region (layer 2's MMAs are done); FP32
+    // column sums for b2 and W3
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+    for (int hh = 0; hh < 2; ++hh) {
+        const int c = c0 + 16 * hh;
+        float h2[16];
+        load_h2(c, h2);
+        float v[16], w0[16], w1[16];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
             float d[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const int jj = 8 * q + j, c = c0 + jj;
-                const float da2 = dy0 * F[L::W3 / 4 + c] + dy1 * F[L::W3 / 4 + kHid + c];
+                const int jj = 8 * q + j;
+                const float da2 = dy0 * F[L::W3 / 4 + c + jj] + dy1 * F[L::W3 / 4 + kHid + c + jj];
                 d[j] = da2 * dsilu2(h2[jj]);
                 v[jj] = d[j];
                 const float a2 = silu2(h2[jj]);
                 w0[jj] = dy0 * a2;
                 w1[jj] = dy1 * a2;
-                st_bf16(S, L::ST + tc_off(c, s, kSampC), d[j]);
+                st_bf16(S, L::ST + tc_off(c + jj, s, kSampC), d[j]);
             }
-            *reinterpret_cast<uint4 *>(S + L::DH2 + tc_off(s, c0 + 8 * q, kHid)) =
+            *reinterpret_cast<uint4 *>(S + L::DH2 + tc_off(s, c + 8 * q, kHid)) =
                 make_uint4(pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]), pack_bf16(d[6], d[7]));
         }
-        Slot[0 * 32 + lane] = warp_colsum(v);
-        Slot[1 * 32 + lane] = warp_colsum(w0);
-        Slot[2 * 32 + lane] = warp_colsum(w1);
+        const float r0 = warp_colsum16(v), r1 = warp_colsum16(w0), r2 = warp_colsum16(w1);
+        if (lane < 16) {
+            Slot[0 * 32 + 16 * hh + lane] = r0;
+            Slot[1 * 32 + 16 * hh + lane] = r1;
+            Slot[2 * 32 + 16 * hh + lane] = r2;
+        }
     }
-    // ---- da1 = dh2 W2 (M 128, N 64, K 64); dh1 = da1 silu'(h1); sums for b1 and W1u
+    // ---- da1 = dh2 W2 (M 128, N 64, K 64) over H2's columns; dh1 = da1 silu'(h1) over
+    // the dH2 region; sums for b1 and W1u
     tc_publish();
     if (tid == 0) {
         tc_gemm(tm + L::cDA1, S + L::DH2, S + L::W2T, kHid, umma::idesc_bf16(128, kHid));
         umma::commit(bar);
     }
     if (!tc_wait(bar, phase)) return false;
-    {
-        float da1[32];
-        tc_load32(tm + lane_base + L::cDA1 + c0, da1);
-        float g0[32], g1[32];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+    for (int hh = 0; hh < 2; ++hh) {
+        const int c = c0 + 16 * hh;
+        float h1[16], da1[16];
+        load_h1(c, h1);
+        tc_load16(tm + lane_base + L::cDA1 + c, da1);
+        float g0[16], g1[16];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
             float d[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const int jj = 8 * q + j, c = c0 + jj;
+                const int jj = 8 * q + j;
                 d[j] = da1[jj] * dsilu1(h1[jj]);
                 da1[jj] = d[j];
                 g0[jj] = d[j] * ux;
                 g1[jj] = d[j] * uy;
-                st_bf16(S, L::ST + tc_off(kHid + c, s, kSampC), d[j]);
+                st_bf16(S, L::ST + tc_off(kHid + c + jj, s, kSampC), d[j]);
             }
-            *reinterpret_cast<uint4 *>(S + L::DH1 + tc_off(s, c0 + 8 * q, kHid)) =
+            *reinterpret_cast<uint4 *>(S + L::DH1 + tc_off(s, c + 8 * q, kHid)) =
                 make_uint4(pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]), pack_bf16(d[6], d[7]));
         }
-        Slot[3 * 32 + lane] = warp_colsum(da1);
-        Slot[4 * 32 + lane] = warp_colsum(g0);
-        Slot[5 * 32 + lane] = warp_colsum(g1);
+        const float r3 = warp_colsum16(da1), r4 = warp_colsum16(g0), r5 = warp_colsum16(g1);
+        if (lane < 16) {
+            Slot[3 * 32 + 16 * hh + lane] = r3;
+            Slot[4 * 32 + 16 * hh + lane] = r4;
+            Slot[5 * 32 + 16 * hh + lane] = r5;
+        }
     }
-    // ---- dz = dh1 W1z (N 32, K 64); dW2 = dh2^T a1 and dW1z = dh1^T z from the
-    // stacked [dh2^T; dh1^T] (M 128 units, K 128 samples)
+    // ---- dz = dh1 W1z (N 32, K 64); dW2 = dh2^T a1 and dW1z = dh1^T z from the stacked
+    // [dh2^T; dh1^T] (M 128 units, K 128 samples); over H1's and dA1's columns
     tc_publish();
     if (tid == 0) {
         tc_gemm(tm + L::cDZ, S + L::DH1, S + L::W1zT, kHid, umma::idesc_bf16(128, kLat));
@@ -707,39 +746,32 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
     }
     if (!tc_wait(bar, phase)) return false;
     {
-        uint32_t r[16];
-        umma::ld16(tm + lane_base + L::cDZ + 16 * wg, r);
+        float v[16];
+        tc_load16(tm + lane_base + L::cDZ + 16 * wg, v);
         float *dst = expl ? A.dzout : A.dzs;
         if (valid && dst) {
             dst += (cbase + s) * kLat + 16 * wg;
             if (((uintptr_t)dst & 15u) == 0) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    reinterpret_cast<float4 *>(dst)[q] =
-                        make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
-                                    __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+                st_f4x4(dst, v);
             } else {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) dst[j] = __uint_as_float(r[j]);
+                for (int j = 0; j < 16; ++j) dst[j] = v[j];
             }
         }
     }
     // gradient rows are 16-byte aligned (kGP = 6532 floats; dW2 at 2240, dW1z at 0)
     float *gp = A.gpart + (int64_t)blockIdx.x * kGP;
     if (s < kHid) {  // lanes 0..63: dW2[out = s][in]
-        float v[32];
-        tc_load32(tm + lane_base + L::cDW2 + c0, v);
-        float4 *g4 = reinterpret_cast<float4 *>(gp + oW2 + s * kHid + c0);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) g4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        for (int hh = 0; hh < 2; ++hh) {
+            float v[16];
+            tc_load16(tm + lane_base + L::cDW2 + c0 + 16 * hh, v);
+            st_f4x4(gp + oW2 + s * kHid + c0 + 16 * hh, v);
+        }
     } else {  // lanes 64..127: dW1z[out = s - 64][in]
-        uint32_t r[16];
-        umma::ld16(tm + lane_base + L::cDW1z + 16 * wg, r);
-        float4 *g4 = reinterpret_cast<float4 *>(gp + oW1z + (s - kHid) * kLat + 16 * wg);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            g4[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]), __uint_as_float(r[4 * q + 2]),
-                                __uint_as_float(r[4 * q + 3]));
+        float v[16];
+        tc_load16(tm + lane_base + L::cDW1z + 16 * wg, v);
+        st_f4x4(gp + oW1z + (s - kHid) * kLat + 16 * wg, v);
     }
     __syncthreads();
     // ---- the FP32 column sums: warps 4 wg .. 4 wg + 3 cover all samples of columns 32 wg ..
@@ -759,14 +791,15 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
     return true;
 }
 
-// Training (backward = 1) or validation step over kSampC samples per CTA: the
+// Training (backward = 1) or validation step over kSampC samples per CTA (two CTAs
+// per SM: 126 registers, ~110 KB of shared memory, 128 tensor-memory columns): the
 // layer-1 latent block, layer 2 and the four backward products on the
 // fifth-generation tensor cores (tcgen05.mma, BF16 operands in shared memory,
 // FP32 accumulators in tensor memory, mbarrier completion with bounded waits);
 // position block, biases, layer 3 and all column sums in FP32.
-__global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
+__global__ void __launch_bounds__(256, 2) k_ff_train(TrainArgs A)
 {
-    extern __shared__ __align__(1024) unsigned char tsm[];
+    extern __shared__ __align__(128) unsigned char tsm[];
     __shared__ __align__(8) uint64_t bar, idle;  // MMA completion; a barrier nothing arrives on (probe)
     __shared__ uint32_t tmem;
     using L = TrainTc;
@@ -875,7 +908,11 @@ __global__ void __launch_bounds__(256, 1) k_ff_train(TrainArgs A)
 
 cudaError_t ff_train_step(const TrainArgs &t, int64_t nsamples, cudaStream_t s)
 {
+    // two CTAs of ~110 KB per SM: the largest shared-memory carveout
     cudaError_t e = cudaFuncSetAttribute(k_ff_train, cudaFuncAttributeMaxDynamicSharedMemorySize, TrainTc::bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ff_train, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     if (nsamples <= 0) return cudaSuccess;
     const unsigned nb = (unsigned)((nsamples + kSampC - 1) / kSampC);
