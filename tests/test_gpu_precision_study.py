@@ -4,8 +4,8 @@ gamma = (0.2, 0.1); 16384^2 rays over [-60,60] x [-30,30]; 2048^2 map over
 oracle, compared on a seeded random sample of rays (the oracle costs N_* per ray).
 
 Each FP32 map is also re-binned bit-exactly from its own beta on the CPU.  The
-study's table is written to gpurun-visible output as JSON when MLENS_STUDY_OUT
-is set."""
+study's table is written as JSON to the file named by MLENS_STUDY_OUT when it is
+set."""
 import json
 import os
 
