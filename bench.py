@@ -12,7 +12,7 @@ Prints ONE JSON line (rank 0).  `value` = ray-star interactions per second over 
 timed steps (device time, CUDA events on the launch stream, max over ranks);
 `e2e` = the same metric through the public C ABI from host buffers (star upload,
 shoot, map download, context teardown inside the timed region).
-`--impl reference` times the FP64 CPU oracle (the reference arm of this build) on a
+`--impl reference` times the FP64 CPU oracle (the reference arm) on a
 bounded ray sample of the same workload.
 
 Under torchrun (N > 1) every rank shoots its own independent field of the same size

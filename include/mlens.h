@@ -49,7 +49,7 @@ extern "C" {
 #define MLENS_ERR_CUDA        -2  /* a CUDA runtime call or a launch failed */
 #define MLENS_ERR_NOMEM       -3  /* a device allocation failed */
 #define MLENS_ERR_STATE       -4  /* the call is not valid in the context's current state */
-#define MLENS_ERR_UNSUPPORTED -5  /* no usable sm_103a device, or an option this build lacks */
+#define MLENS_ERR_UNSUPPORTED -5  /* no usable sm_103a device, or an option the library lacks */
 
 /* ------------------------------------------------------ precision variants */
 /* FP32 direct sum with star and ray coordinates re-centred on each ray tile,
