@@ -1059,6 +1059,7 @@ struct LearnSmem {
     float2 l2q[kHid / 2];  // {W3[1][c], W3[1][c+1]}
     float b3[2];
     float coef[kCoefStride];
+    float4 coef2[kPeMax];  // b_q as {Re, Re, Im, Im}: both rays of a pair at once
     float sc;
     int rb[3], re[3];
     int nnear;
@@ -1129,6 +1130,11 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
         ls.sc = L.sc[rc];
     }
     if (tid < kCoefStride) ls.coef[tid] = L.coef[(int64_t)rc * kCoefStride + tid];
+    if (tid < kPeMax) {
+        const float re = L.coef[(int64_t)rc * kCoefStride + 4 + 2 * tid];
+        const float im = L.coef[(int64_t)rc * kCoefStride + 5 + 2 * tid];
+        ls.coef2[tid] = make_float4(re, re, im, im);
+    }
     if (tid < kHid) reinterpret_cast<float *>(&ls.l1p[tid >> 1])[tid & 1] = L.ec ? L.ec[(int64_t)rc * kHid + tid] : 0.0f;
     __syncthreads();
 
@@ -1295,50 +1301,70 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
     }
     __syncthreads();
 
-    // ---- far field and beta per ray
+    // ---- far field and beta per ray, the two rays of each pair (rows 2p and 2p + 1 of
+    // column tx) in the two lanes of f32x2 registers: the same operations per ray as a
+    // scalar loop, x - y as fma(y, -1, x) (one rounding, as a subtraction)
     float bxh[2 * NP], byh[2 * NP], bxl[2 * NP], byl[2 * NP];
-    const float uxr = (float)(2 * (ioff + tx) + 1) * inv_cx - 1.0f;
+    {
+        const float2 m1 = make_float2(-1.0f, -1.0f);
+        auto sub2 = [&](float2 x, float2 y) { return __ffma2_rn(y, m1, x); };
+        auto two_sum2 = [&](float2 a, float2 b, float2 &s, float2 &e) {  // Knuth's TwoSum per lane
+            const float2 x = __fadd2_rn(a, b), bb = sub2(x, a);
+            e = __fadd2_rn(sub2(a, sub2(x, bb)), sub2(b, bb));
+            s = x;
+        };
+        auto dup = [](float x) { return make_float2(x, x); };
+        const float uxr = (float)(2 * (ioff + tx) + 1) * inv_cx - 1.0f;
+        const float2 vx = dup(uxr * 0.70710678f);
+        const float2 tc4 = dup(ts.tc[4]), tc5 = dup(ts.tc[5]), tc6 = dup(ts.tc[6]), tc7 = dup(ts.tc[7]);
+        const float2 nb0x = dup(-ls.coef[0]), b0y = dup(ls.coef[1]), b1x = dup(ls.coef[2]), b1y = dup(ls.coef[3]);
+        const float2 fa11 = dup(a.lens.fa11), fa12 = dup(a.lens.fa12), fa22 = dup(a.lens.fa22);
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int r = 2 * p + h;
-            const int jl = tg * 2 * NP + r;
-            const float uyr = (float)(2 * (joff + jl) + 1) * inv_cy - 1.0f;
-            const float2 v = make_float2(uxr * 0.70710678f, uyr * 0.70710678f);
-            // T = sum_{p=1}^{pe} b_p v^p + v^(pe+1) q, q = s_c (network output) or 0:
-            // Horner with q as the innermost coefficient
-            float2 acc = make_float2(0.f, 0.f);
+        for (int p = 0; p < NP; ++p) {
+            const int jl = tg * 2 * NP + 2 * p;  // the pair's first row in the tile
+            const float uy0 = (float)(2 * (joff + jl) + 1) * inv_cy - 1.0f;
+            const float uy1 = (float)(2 * (joff + jl + 1) + 1) * inv_cy - 1.0f;
+            const float2 vy = make_float2(uy0 * 0.70710678f, uy1 * 0.70710678f);
+            const float2 nvy = make_float2(-vy.x, -vy.y);
+            // T = sum_{q=1}^{pe} b_q v^q + v^(pe+1) q_net, q_net = s_c (network output) or 0:
+            // Horner with q_net as the innermost coefficient; (ar, ai) = T's real and
+            // imaginary parts for the two rays
+            float2 ar = make_float2(0.f, 0.f), ai = make_float2(0.f, 0.f);
             if (L.use_net) {
-                const int ray = jl * kTileX + tx;
-                acc = make_float2(ls.sc * Y[2 * ray], ls.sc * Y[2 * ray + 1]);
+                const int ray0 = jl * kTileX + tx, ray1 = ray0 + kTileX;
+                ar = make_float2(ls.sc * Y[2 * ray0], ls.sc * Y[2 * ray1]);
+                ai = make_float2(ls.sc * Y[2 * ray0 + 1], ls.sc * Y[2 * ray1 + 1]);
             }
-            acc = cmul(acc, v);
+            auto cmul2 = [&]() {  // (ar + i ai) (vx + i vy)
+                const float2 t = __fmul2_rn(ar, vx), u = __fmul2_rn(ar, vy);
+                ar = __ffma2_rn(ai, nvy, t);
+                ai = __ffma2_rn(ai, vx, u);
+            };
+            cmul2();
             for (int q = L.pe; q >= 1; --q) {
-                acc.x += ls.coef[4 + 2 * (q - 1)];
-                acc.y += ls.coef[5 + 2 * (q - 1)];
-                acc = cmul(acc, v);
+                const float4 c = ls.coef2[q - 1];
+                ar = __fadd2_rn(ar, make_float2(c.x, c.y));
+                ai = __fadd2_rn(ai, make_float2(c.z, c.w));
+                cmul2();
             }
-            const float rx_ = 0.f, ry_ = 0.f;
-            const float sx = h ? Sx[p].y : Sx[p].x, sy = h ? Sy[p].y : Sy[p].x;
-            const float ccx = h ? Cx[p].y : Cx[p].x, ccy = h ? Cy[p].y : Cy[p].x;
-            const float dxr = rx.x, dyr = h ? ry[p].y : ry[p].x;
-            const float lx = __fmaf_rn(a.lens.fa11, dxr, __fmul_rn(a.lens.fa12, dyr));
-            const float ly = __fmaf_rn(a.lens.fa12, dxr, __fmul_rn(a.lens.fa22, dyr));
+            const float2 lx = __ffma2_rn(fa11, rx, __fmul2_rn(fa12, ry[p]));
+            const float2 ly = __ffma2_rn(fa12, rx, __fmul2_rn(fa22, ry[p]));
             // alpha_far = (Re F, -Im F) + residual;  F = b0 + T
-            float th, tl, t2;
-            two_sum(ts.tc[4], -sx, th, tl);
-            two_sum(th, -ls.coef[0], th, t2);
-            float small = __fadd_rn(__fadd_rn(ts.tc[6], ccx), lx);
-            small = __fsub_rn(small, __fadd_rn(__fadd_rn(ls.coef[2], acc.x), rx_));
-            tl = __fadd_rn(__fadd_rn(tl, t2), small);
-            two_sum(th, tl, bxh[r], bxl[r]);
-            two_sum(ts.tc[5], -sy, th, tl);
-            two_sum(th, ls.coef[1], th, t2);
-            small = __fadd_rn(__fadd_rn(ts.tc[7], ccy), ly);
-            small = __fadd_rn(small, __fsub_rn(__fadd_rn(ls.coef[3], acc.y), ry_));
-            tl = __fadd_rn(__fadd_rn(tl, t2), small);
-            two_sum(th, tl, byh[r], byl[r]);
+            float2 th, tl, t2, small, h, l;
+            two_sum2(tc4, __fmul2_rn(Sx[p], m1), th, tl);
+            two_sum2(th, nb0x, th, t2);
+            small = __fadd2_rn(__fadd2_rn(tc6, Cx[p]), lx);
+            small = sub2(small, __fadd2_rn(b1x, ar));
+            tl = __fadd2_rn(__fadd2_rn(tl, t2), small);
+            two_sum2(th, tl, h, l);
+            bxh[2 * p] = h.x, bxh[2 * p + 1] = h.y, bxl[2 * p] = l.x, bxl[2 * p + 1] = l.y;
+            two_sum2(tc5, __fmul2_rn(Sy[p], m1), th, tl);
+            two_sum2(th, b0y, th, t2);
+            small = __fadd2_rn(__fadd2_rn(tc7, Cy[p]), ly);
+            small = __fadd2_rn(small, __fadd2_rn(b1y, ai));
+            tl = __fadd2_rn(__fadd2_rn(tl, t2), small);
+            two_sum2(th, tl, h, l);
+            byh[2 * p] = h.x, byh[2 * p + 1] = h.y, byl[2 * p] = l.x, byl[2 * p + 1] = l.y;
         }
     }
 
