@@ -1,8 +1,10 @@
 // farfield.cu -- kernels of the learned-far-field variant (see farfield.h):
-// cell CSR of the stars, FP64 local-expansion coefficients of the far field,
-// network training / validation on BF16 tensor cores, and the persistent
-// shooting kernel that evaluates near field + series + network per ray and
-// falls back to the exact direct sum on flagged cells.
+// cell CSR of the stars, local-expansion coefficients of the far field (direct
+// sums over the far stars, FP64-accurate), network training / validation with
+// every product on the fifth-generation tensor cores (tcgen05, BF16 operands,
+// FP32 accumulators in tensor memory), and the persistent shooting kernel that
+// evaluates near field + series + network per ray (the network's 64 x 64 layer on
+// tcgen05) and falls back to the exact direct sum on flagged cells.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -107,13 +109,14 @@ cudaError_t ff_build_csr(const float4 *stars, int64_t n, const CellGrid &cg, int
     return cudaGetLastError();
 }
 
-// ===================================================== FP64 coefficients
+// ===================================================== series coefficients
 // One warp per ray cell, eight cells per CTA sharing each staged chunk of stars.
 // b_0 (the far field's value at the centre, ~30 theta_E, needed to ~1e-9) is
-// formed entirely in FP64.  For p >= 1 the terms -(m/s) w^(p+1) are formed in
-// FP32 from the FP64 w (relative error ~p 6e-8 per term, far below what the
-// series needs) and accumulated in FP64, so the sums keep FP64 accuracy while
-// the per-term work moves to the FP32 pipe.
+// formed per star in double-float arithmetic (below) and accumulated in FP64 once
+// per stage.  For p >= 1 the terms -(m/s) w^(p+1) are formed in FP32 (relative
+// error ~p 6e-8 per term, far below what the series needs), summed per lane in
+// FP32 over a stage and accumulated in FP64, so the sums keep FP64 accuracy while
+// the per-term work runs on the FP32 pipe.
 // Double-float arithmetic (an unevaluated pair of floats, ~48 significant bits) on
 // the FP32 pipe: Knuth's TwoSum, the FMA form of Dekker's TwoProduct, and one
 // Newton step for the reciprocal.  Used for the order-0 far-field term, which
