@@ -3,8 +3,9 @@
 // an explicitly rounded intrinsic in the order the equations state it, stars
 // visited in input order.  Its beta and its maps therefore equal a plain IEEE
 // FP64 evaluation of the same formulas bit for bit.  On GB300 FP64 runs at a
-// small fraction of the FP32 rate; this path exists for verification, for the
-// precision study and for exact training targets, not for throughput.
+// small fraction of the FP32 rate; this path exists for verification
+// (mlens_trace), for the precision study and for exact per-ray references, not
+// for throughput.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
