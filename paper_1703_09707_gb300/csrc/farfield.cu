@@ -154,7 +154,7 @@ __device__ __forceinline__ DF df_rcp(DF a)
     const float y = __frcp_rn(a.h);           // relative error <= 2^-24
     const DF ay = df_mulf(a, y);              // ~1
     const DF r = df_add({1.0f, 0.0f}, {-ay.h, -ay.l});  // 1 - a y, ~2^-24
-    return df_norm(y, __fmul_rn(y, r.h));     // y (1 + r): error ~2^-47
+    return df_norm(y, __fmul_rn(y, r.h));     // y (1 + r): relative error below 2^-45
 }
 
 __device__ __forceinline__ float2 f2c(float x, float y) { return make_float2(x, y); }
