@@ -281,30 +281,36 @@ int mlens_magnification_scale(const mlens_grid *rays, const mlens_grid *src, dou
 
 /*
  * mlens_shoot_noalloc -- mlens_shoot for callers that must not allocate device
- * memory: code that runs while a CUDA stream is being captured into a graph
- * (cudaMalloc is not allowed there), plugins whose host application owns every
- * device allocation, and real-time loops that may not enter the allocator.  It
- * takes no context: the caller passes the stars already on the device, and the
- * only working memory is a fixed array compiled into the library.
+ * memory: plugins whose host application owns every device allocation (its own
+ * pool, its own accounting), and real-time loops that may not enter the CUDA
+ * allocator (cudaMalloc and cudaFree can synchronise the device and take an
+ * unbounded time).  It takes no context: the caller passes the stars already on
+ * the device, and the only working memory is a fixed array compiled into the
+ * library.
  * The paper has no counterpart; it is a deployment variant of the same FP32
- * kernel (MLENS_PREC_FP32, 8 rays per thread), so it produces the same map as
- * mlens_create + mlens_shoot on the same float32 star values.
+ * kernel (MLENS_PREC_FP32, 8 rays per thread, no star split), so it produces the
+ * same map as mlens_create + mlens_shoot (split 1) on the same float32 stars.
  *   stars_dev  n records float4 {x, y, m, unused} on the current device,
  *              16-byte aligned, caller-owned.  The values are not checked:
  *              non-finite entries give non-finite beta for the rays they touch.
  *   n          0 <= n <= MLENS_NOALLOC_MAX_STARS.
- *   kappa_c, gamma1, gamma2, rays, src, counts_dev, flags, stats_host, stream
+ *   kappa_c, gamma1, gamma2, rays, src, counts_dev, flags, stream
  *              as for mlens_create / mlens_shoot.
+ *   stats_host nullable; when given, the call copies the counters back and
+ *              waits for `stream` before it returns (as mlens_shoot does).
  * Working memory: one file-scope device array of MLENS_NOALLOC_MAX_STARS + 32
- * star records plus three 64-bit counters (about 1 MiB), held on every device
- * that loads the library until the process exits.  Each call copies the stars
- * into it (padding the tail) and clears the counters on `stream` before the
- * kernel runs; the array keeps the last call's contents afterwards.  All calls
- * share that one array, so calls whose GPU work overlaps (different streams,
- * or different host threads) race and corrupt each other's maps: serialise them.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture begins.
+ * star records plus four 64-bit counters (three used; about 1 MiB), held on
+ * every device that loads the library until the process exits.  Each call copies
+ * the stars into it (padding the tail) and clears the counters on `stream` before
+ * the kernel runs; the array keeps the last call's contents afterwards.  All
+ * calls share that one array, so calls whose GPU work overlaps (different
+ * streams, or different host threads) race and corrupt each other's maps:
+ * serialise them.
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life of
+ * the process; make that first call before any stream capture begins.  The
+ * address is not looked up again after cudaDeviceReset, so calls after a reset
+ * of the device in the same process are not supported.
  * Errors: MLENS_ERR_ARG (n above the maximum, bad grid, NULL or misaligned
  * pointer, non-finite lens terms), MLENS_ERR_CUDA.
  */

@@ -1,7 +1,8 @@
 // noalloc.cu -- mlens_shoot_noalloc: the FP32 shooting kernel for callers that
-// cannot allocate device memory (stream capture, host applications that own all
-// device allocations, real-time loops).  Its working memory is one file-scope
-// device array: a padded copy of the caller's stars and the ray counters.
+// cannot allocate device memory (host applications that own all device
+// allocations, real-time loops that must stay out of the allocator).  Its working
+// memory is one file-scope device array: a padded copy of the caller's stars and
+// the ray counters.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,7 +28,9 @@ struct NoAllocScratch {
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
 constexpr int kMaxDevices = 64;
-NoAllocScratch *g_scratch_addr[kMaxDevices];  // device address per device ordinal, set on first use
+// device address per device ordinal, set on the first call on that device and
+// kept for the life of the process (a device reset is not followed)
+NoAllocScratch *g_scratch_addr[kMaxDevices];
 std::mutex g_scratch_mu;
 
 __global__ void k_noalloc_stage(const float4 *in, int64_t n, int64_t npad)

@@ -210,6 +210,27 @@ def _dev_ptr(t) -> C.c_void_p:
     return C.c_void_p(int(t))
 
 
+def _check_tensor(t, what: str, min_elems: int, dtypes):
+    """Check what the C side cannot see in a torch tensor: its element type,
+    contiguity and that it holds at least `min_elems` elements (ValueError).
+    Anything that is not a tensor (an integer address) is not checked."""
+    if not hasattr(t, "data_ptr"):
+        return
+    names = {str(d).replace("torch.", "") for d in dtypes}
+    if str(t.dtype).replace("torch.", "") not in names:
+        raise ValueError(f"{what} must have dtype {' or '.join(sorted(names))}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if t.numel() < min_elems:
+        raise ValueError(f"{what} holds {t.numel()} elements, needs at least {min_elems}")
+
+
+def _counts_buf(counts, src: mlens_grid) -> C.c_void_p:
+    """A source map: int32 or uint32, src.nx * src.ny elements at least, on the device."""
+    _check_tensor(counts, "counts", int(src.nx) * int(src.ny), ("int32", "uint32"))
+    return _dev_ptr(counts)
+
+
 class Ctx:
     """Owns one mlens_ctx*."""
 
@@ -267,7 +288,7 @@ def mlens_star_split_for(ctx: Ctx, rays) -> int:
 def mlens_shoot(ctx: Ctx, rays, src, counts, flags: int = 0, stats: bool = False, stream=None):
     st = mlens_stats()
     g, s = grid(rays), grid(src)
-    _check(load().mlens_shoot(ctx.handle, C.byref(g), C.byref(s), _dev_ptr(counts), int(flags),
+    _check(load().mlens_shoot(ctx.handle, C.byref(g), C.byref(s), _counts_buf(counts, s), int(flags),
                               C.byref(st) if stats else None, _stream_ptr(stream)))
     return st.asdict() if stats else None
 
@@ -275,7 +296,7 @@ def mlens_shoot(ctx: Ctx, rays, src, counts, flags: int = 0, stats: bool = False
 def mlens_shoot_beta(ctx: Ctx, rays, src, counts, beta, flags: int = 0, stats: bool = False, stream=None):
     st = mlens_stats()
     g, s = grid(rays), grid(src)
-    _check(load().mlens_shoot_beta(ctx.handle, C.byref(g), C.byref(s), _dev_ptr(counts), _dev_ptr(beta),
+    _check(load().mlens_shoot_beta(ctx.handle, C.byref(g), C.byref(s), _counts_buf(counts, s), _dev_ptr(beta),
                                    int(flags), C.byref(st) if stats else None, _stream_ptr(stream)))
     return st.asdict() if stats else None
 
@@ -337,11 +358,21 @@ def mlens_magnification_scale(rays, src) -> float:
 
 def mlens_shoot_noalloc(stars, n: int, kappa_c: float, gamma1: float, gamma2: float, rays, src, counts,
                         flags: int = 0, stats: bool = False, stream=None):
-    """stars: CUDA float32 tensor of n records (x, y, m, unused)."""
+    """stars: contiguous CUDA float32 tensor holding n records (x, y, m, unused),
+    shape (n, 4) or flat; it is read on the device, so its type and length are
+    checked here before the call (ValueError)."""
     st = mlens_stats()
     g, s = grid(rays), grid(src)
-    _check(load().mlens_shoot_noalloc(_dev_ptr(stars), int(n), float(kappa_c), float(gamma1), float(gamma2),
-                                      C.byref(g), C.byref(s), _dev_ptr(counts), int(flags),
+    n = int(n)
+    if n < 0:
+        raise ValueError("n must be >= 0")
+    if hasattr(stars, "data_ptr") and stars.dim() > 1 and stars.shape[-1] != 4:
+        raise ValueError(f"stars must be (n, 4) records or flat, got shape {tuple(stars.shape)}")
+    _check_tensor(stars, "stars", 4 * n, ("float32",))
+    _check_tensor(counts, "counts", int(s.nx) * int(s.ny), ("int32", "uint32"))
+    sp, cp = _dev_ptr(stars), _dev_ptr(counts)
+    _check(load().mlens_shoot_noalloc(sp, n, float(kappa_c), float(gamma1), float(gamma2),
+                                      C.byref(g), C.byref(s), cp, int(flags),
                                       C.byref(st) if stats else None, _stream_ptr(stream)))
     return st.asdict() if stats else None
 

@@ -8,6 +8,7 @@ import re
 import numpy as np
 import pytest
 
+import workloads as W
 from paper_1703_09707_gb300 import build as B
 from paper_1703_09707_gb300 import mlens as M
 
@@ -136,3 +137,26 @@ def test_noalloc_size_limit_rejected_without_a_device(lib):
     rc = lib.mlens_shoot_noalloc(C.c_void_p(16), 65537, 0.0, 0.0, 0.0, C.byref(g), C.byref(g), C.c_void_p(16), 0,
                                  None, None)
     assert rc == M.MLENS_ERR_ARG and "65536" in M.mlens_last_error()
+
+
+def test_noalloc_binding_refuses_mismatched_buffers_before_any_call():
+    """mlens_shoot_noalloc reads the caller's star records on the device, so the
+    binding checks a tensor's type, shape and length against n (and the map's length
+    against the source grid) before it reaches the library; CPU tensors show the
+    checks without a GPU."""
+    torch = pytest.importorskip("torch")
+    g = W.Grid(-1.0, 1.0, -1.0, 1.0, 8, 8)
+    counts = torch.zeros(64, dtype=torch.int32)
+    cases = [
+        (torch.zeros((10, 4), dtype=torch.float64), 10, counts, "dtype"),       # float64 records
+        (torch.zeros((9, 4), dtype=torch.float32), 10, counts, "at least 40"),  # too few records for n
+        (torch.zeros(39, dtype=torch.float32), 10, counts, "at least 40"),      # flat, too short
+        (torch.zeros((10, 3), dtype=torch.float32), 10, counts, "shape"),       # not 4-wide
+        (torch.zeros((10, 4), dtype=torch.float32), 10, torch.zeros(63, dtype=torch.int32), "at least 64"),
+        (torch.zeros((10, 4), dtype=torch.float32), 10, torch.zeros(64, dtype=torch.float32), "dtype"),
+        (torch.zeros((10, 4), dtype=torch.float32), 10, counts, "CUDA tensor"),  # right shape, host memory
+        (torch.zeros((10, 4), dtype=torch.float32), -1, counts, "n must"),
+    ]
+    for stars, n, cnt, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            M.mlens_shoot_noalloc(stars, n, 0.0, 0.0, 0.0, g, g, cnt)

@@ -1,10 +1,10 @@
-"""mlens_shoot_noalloc is for callers that cannot allocate device memory: code running
-while a stream is captured into a CUDA graph, plugins whose host application owns all
-device allocations, real-time loops that must stay out of the allocator.  It works out
-of a fixed array inside the library instead of a context.  These tests check that it
-gives exactly the map of the regular entry point (same kernel, same float32 stars),
-twice in a row (the array keeps the previous call's contents, which must not leak into
-the next call), and that it refuses star counts beyond its fixed capacity.
+"""mlens_shoot_noalloc is for callers that cannot allocate device memory: plugins whose
+host application owns all device allocations, and real-time loops that must stay out of
+the CUDA allocator.  It works out of a fixed array inside the library instead of a
+context.  These tests check that it gives exactly the map of the regular entry point
+(same kernel, same float32 stars), twice in a row (the array keeps the previous call's
+contents, which must not leak into the next call), and that it refuses star counts
+beyond its fixed capacity.
 
 This file is collected last on purpose, so that a run stopping at the first failure has
 already run every other test."""
@@ -54,11 +54,16 @@ def test_noalloc_matches_mlens_shoot_on_two_calls_in_a_row():
 
 
 def test_noalloc_rejects_too_many_stars():
+    """The library itself refuses a star count above its fixed capacity (the binding
+    passes a correctly typed buffer of that many records, so the refusal is the C
+    side's)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
     big = 65536 + 1
     g = W.Grid(-1.0, 1.0, -1.0, 1.0, 8, 8)
-    counts = torch.empty(64, dtype=torch.int32, device="cuda") if torch.cuda.is_available() else None
+    counts = torch.empty(64, dtype=torch.int32, device="cuda")
+    stars = torch.zeros((big, 4), dtype=torch.float32, device="cuda")
     with pytest.raises(M.MlensError) as ei:
-        M.mlens_shoot_noalloc(16 if counts is None else counts, big, 0.0, 0.0, 0.0, g, g,
-                              16 if counts is None else counts)
+        M.mlens_shoot_noalloc(stars, big, 0.0, 0.0, 0.0, g, g, counts)
     assert ei.value.code == M.MLENS_ERR_ARG
     assert "65536" in str(ei.value)
