@@ -15,9 +15,11 @@ shoot, map download, context teardown inside the timed region).
 `--impl reference` times the FP64 CPU oracle (the reference arm) on a
 bounded ray sample of the same workload.
 
-Under torchrun (N > 1) every rank shoots its own independent field of the same size
-(weak scaling, no data-path collective; the process group only carries the barrier
-and the max-over-ranks timing).
+Under torchrun (N > 1), by default (--scaling strong) the ranks share one map: rank r
+shoots its band of ray rows (bands on tile boundaries, paper_1703_09707_gb300.partition)
+and the uint32 maps are summed with one NCCL all-reduce per step, inside the timed
+region (Section 2.2's MPI tasks and map reduction).  --scaling weak gives every rank its
+own independent field of the same size instead (no data-path collective).
 """
 from __future__ import annotations
 
@@ -67,9 +69,13 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-fields and learned-far-field measurements that ride along the main line")
     ap.add_argument("--extras", default="batched,binning,lightcurve,split,learned",
-                    help="comma list of extra sections: batched, binning, lightcurve, split, learned")
+                    help="comma list of extra sections: batched, binning, lightcurve, split, learned, fit")
     ap.add_argument("--learned-tol", type=float, default=5e-6, help="per-cell validation bound of the learned field")
     ap.add_argument("--learned-order", type=int, default=10)
+    ap.add_argument("--fit-stars", type=int, default=1_000_000,
+                    help="stars of the field the fit section fits (same density and cell grid as the learned one)")
+    ap.add_argument("--scaling", default="strong", choices=["strong", "weak"],
+                    help="strong: the ranks split one map's ray rows and sum the maps; weak: one field per rank")
     return ap.parse_args()
 
 
@@ -409,54 +415,112 @@ def bench_split(M, torch, flush, peak):
 
 
 # --------------------------------------------------------------- learned
+LEARNED_STRIPS = ((0, 768), (10752, 11520), (16128, 16896), (32000, 32768))
+
+
+def _grid_theta(rays, idx):
+    """Cell-centre image positions of grid rays (linear index j*nx + i), formed with the
+    FP64 kernel's operations: x0 + (i + 1/2) ((x1 - x0) / nx)."""
+    i, j = idx % rays.nx, idx // rays.nx
+    tx = rays.x0 + (i + 0.5) * ((rays.x1 - rays.x0) / rays.nx)
+    ty = rays.y0 + (j + 0.5) * ((rays.y1 - rays.y0) / rays.ny)
+    return np.stack([tx, ty], 1)
+
+
+def _pixel_f64(bx, by, src):
+    """Source pixel of FP64 positions (-1 outside the map)."""
+    ux = np.floor((bx - src.x0) * (src.nx / (src.x1 - src.x0)))
+    uy = np.floor((by - src.y0) * (src.ny / (src.y1 - src.y0)))
+    ok = np.isfinite(ux) & np.isfinite(uy) & (ux >= 0) & (ux < src.nx) & (uy >= 0) & (uy < src.ny)
+    return np.where(ok, uy * src.nx + ux, -1).astype(np.int64)
+
+
+def _errors_vs_fp64(b4, b64, src):
+    """Per-ray error of float-pair beta against FP64 beta: |d beta| in source pixels
+    (mean, p99.99, max), max |d alpha| in theta_E (= max |d beta|), misbinned fraction."""
+    bg = b4[:, :2].astype(np.float64) + b4[:, 2:].astype(np.float64)
+    w = min((src.x1 - src.x0) / src.nx, (src.y1 - src.y0) / src.ny)
+    d = np.linalg.norm(bg - b64, axis=1)
+    fin = np.isfinite(d)
+    pg = _pixel_f64(bg[:, 0], bg[:, 1], src)
+    p6 = _pixel_f64(b64[:, 0], b64[:, 1], src)
+    return {"rays": int(d.size), "dbeta_mean_px": float(d[fin].mean() / w),
+            "dbeta_p9999_px": float(np.quantile(d[fin], 0.9999) / w), "dbeta_max_px": float(d[fin].max() / w),
+            "dalpha_max_theta_e": float(d[fin].max()), "misbinned_frac": float(np.mean(pg != p6))}
+
+
 def bench_learned(M, torch, steps: int, flush, tol: float, order: int):
     """10^6 stars, 32768^2 rays, 4096^2 map: the learned far field (fit on the GPU,
     then one persistent launch per map) against the plain direct sum.  The plain
-    map of the whole grid takes minutes, so both paths are compared on a strip of
-    768 ray rows (two cell rows, 2.5e13 interactions for the plain path): the strip
-    gives the plain path's throughput and the map error of the learned path
-    (relative L1 of the strip maps).  Done with the network, without it at the same
-    exact order, and without it at order 16."""
+    map of the whole grid takes minutes, so both paths are compared on four strips of
+    768 ray rows (the first and last rows of the grid and two interior strips, 1e14
+    interactions for the plain path): the strips give the plain path's throughput and
+    the map error of the learned path (relative L1 over the strips' maps).  Every
+    variant's per-ray error is stated against FP64 on 2e4 rays sampled from the
+    strips: the FP64 kernel (mlens_trace, bit-identical to the FP64 oracle) gives the
+    reference, outside the timed regions.  Variants: with the network, without it at
+    the same exact order, and the exact series alone at higher orders (the fastest of
+    those meeting L1 <= 1e-3 is the best non-learned variant)."""
     wl = W.config("learned")
     f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
     stream = torch.cuda.current_stream()
     ctx = M.mlens_create(f.xy, f.m, f.kappa_c, f.gamma1, f.gamma2, M.MLENS_PREC_FP32)
-    dy = (rays.y1 - rays.y0) / rays.ny
-    j0 = (rays.ny // 2 // 384) * 384
-    j1 = j0 + 768
-    strip = W.Grid(rays.x0, rays.x1, rays.y0 + j0 * dy, rays.y0 + j1 * dy, rays.nx, j1 - j0)
-    cp = torch.empty(src.n, dtype=torch.int32, device="cuda")
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    strip_rays = sum(rays.nx * (j1 - j0) for j0, j1 in LEARNED_STRIPS)
+    plain_maps, plain_ms = [], 0.0
     torch.cuda.synchronize()
-    e0.record(stream)
-    M.mlens_shoot(ctx, strip, src, cp)
-    e1.record(stream)
-    e1.synchronize()
-    plain_strip_ms = e0.elapsed_time(e1)
-    plain_rate = strip.n * f.n / (plain_strip_ms / 1e3)
+    for j0, j1 in LEARNED_STRIPS:
+        cp = torch.empty(src.n, dtype=torch.int32, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        M.mlens_shoot_rows(ctx, rays, (j0, j1), src, cp)
+        e1.record(stream)
+        e1.synchronize()
+        plain_ms += e0.elapsed_time(e1)
+        plain_maps.append(cp.cpu().numpy().view(np.uint32).astype(np.int64))
+    plain_rate = strip_rays * f.n / (plain_ms / 1e3)
     plain_full_s = rays.n * f.n / plain_rate
-    cp_h = cp.cpu().numpy().view(np.uint32).astype(np.int64)
+    # sampled rays and their FP64 beta
+    rng = np.random.default_rng(11)
+    idx = np.concatenate([np.sort(rng.choice(rays.nx * (j1 - j0), 5000, replace=False)) + j0 * rays.nx
+                          for j0, j1 in LEARNED_STRIPS]).astype(np.int64)
+    b64 = M.mlens_trace(ctx, _grid_theta(rays, idx))
+    idx_t = torch.from_numpy(idx).cuda()
+    beta = torch.empty((rays.n, 4), dtype=torch.float32, device="cuda")  # only the strips' rows are written
     out = {"workload": f"learned: {f.n} stars, {rays.nx}^2 rays, {src.nx}^2 map, 256 x 86 cells of 0.46875 theta_E",
            "plain": {"interactions_per_s": plain_rate, "map_s_estimated": plain_full_s,
-                     "measured_on": f"rows [{j0},{j1}) of the grid ({strip.n} rays)"}}
+                     "measured_on": f"ray rows {list(LEARNED_STRIPS)} ({strip_rays} rays)"},
+           "errors_reference": "FP64 kernel (mlens_trace; bit-identical to the FP64 oracle) on 2e4 rays "
+                               "sampled from the strips"}
+    # the plain path's own error on the same rays, for comparison
+    cpb = torch.empty(src.n, dtype=torch.int32, device="cuda")
+    for j0, j1 in LEARNED_STRIPS:
+        M.mlens_shoot_rows(ctx, rays, (j0, j1), src, cpb, beta=beta)
+    out["plain"]["errors_vs_fp64"] = _errors_vs_fp64(beta.index_select(0, idx_t).cpu().numpy(), b64, src)
     # the learned path, the same series without the network (the ablation), and the
-    # exact series at order 16 without a network (the strongest non-learned variant)
-    variants = (("with_network", 1, order), ("series_only", 0, order), ("series_only_order16", 0, 16))
+    # exact series alone at higher orders
+    variants = [("with_network", 1, order), ("series_only", 0, order)]
+    variants += [(f"series_only_order{o}", 0, o) for o in (12, 14, 16) if o > order]
     for key, use_net, o in variants:
         t0 = time.perf_counter()
         rep = M.mlens_fit_far_field(ctx, rays, M.fit_params(cells_x=256, order=o, use_network=use_net,
                                                             tolerance=tol))
         fit_s = time.perf_counter() - t0
         cl = torch.empty(src.n, dtype=torch.int32, device="cuda")
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        M.mlens_shoot_learned(ctx, rays, src, cl, rows=(j0, j1))
-        b.record(stream)
-        b.synchronize()
-        strip_s = a.elapsed_time(b) / 1e3
-        cl_h = cl.cpu().numpy().view(np.uint32).astype(np.int64)
+        strip_s = 0.0
+        num = den = 0
+        for (j0, j1), cp_h in zip(LEARNED_STRIPS, plain_maps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            M.mlens_shoot_learned(ctx, rays, src, cl, beta=beta, rows=(j0, j1))
+            b.record(stream)
+            b.synchronize()
+            strip_s += a.elapsed_time(b) / 1e3
+            cl_h = cl.cpu().numpy().view(np.uint32).astype(np.int64)
+            num += np.abs(cl_h - cp_h).sum()
+            den += cp_h.sum()
+        errs = _errors_vs_fp64(beta.index_select(0, idx_t).cpu().numpy(), b64, src)
         # whole map timed unless its fallback tiles alone would take minutes (then the
-        # strip's time is scaled to the grid)
+        # strips' time is scaled to the grid)
         fallback_s = rep["tiles_fallback"] * 2048 * f.n / plain_rate
         if fallback_s <= 5.0:
             counts = torch.empty(src.n, dtype=torch.int32, device="cuda")
@@ -473,14 +537,15 @@ def bench_learned(M, torch, steps: int, flush, tol: float, order: int):
             learned_s = statistics.mean(ms) / 1e3
             timing = f"whole map, mean of {steps} CUDA-event-timed launches"
         else:
-            learned_s = strip_s * rays.n / strip.n
-            timing = f"estimated from the strip ({strip_s:.3f} s for rows [{j0},{j1}))"
-        l1 = float(np.abs(cl_h - cp_h).sum() / max(cp_h.sum(), 1))
+            learned_s = strip_s * rays.n / strip_rays
+            timing = f"estimated from the strips ({strip_s:.3f} s)"
+        l1 = float(num / max(den, 1))
         out[key] = {
             "map_s": learned_s, "map_s_timing": timing, "maps_per_s": 1.0 / learned_s,
             "effective_interactions_per_s": rays.n * f.n / learned_s,
             "speedup_vs_plain": plain_full_s / learned_s,
             "map_rel_l1_vs_plain": l1, "equal_error": l1 <= 1e-3,
+            "errors_vs_fp64": errs,
             "fallback_cells": rep["cells_fallback"], "cells": rep["cells"],
             "fallback_tiles": rep["tiles_fallback"], "tiles": rep["tiles"],
             "val_mean_err": rep["val_mean_err_net"] if use_net else rep["val_mean_err_series"],
@@ -490,8 +555,45 @@ def bench_learned(M, torch, steps: int, flush, tol: float, order: int):
             "train_steps": rep["train_steps"], "order": o, "tolerance": tol,
         }
     out["network_gain_at_equal_order"] = out["series_only"]["map_s"] / out["with_network"]["map_s"]
+    series = {k: v for k, v in out.items() if k.startswith("series_only") and isinstance(v, dict) and v["equal_error"]}
+    if series:
+        best = min(series, key=lambda k: series[k]["map_s"])
+        out["best_series_variant"] = best
+        # > 1: the trained network is faster than every series-only variant at equal map error
+        out["network_gain_vs_best_series"] = series[best]["map_s"] / out["with_network"]["map_s"]
     ctx.close()
     return out
+
+
+# ------------------------------------------------------------------- fit
+def bench_fit(M, torch, fit_stars: int, tol: float, order: int, peak_fp32_lane_ops: float):
+    """One far-field fit on the learned workload's ray grid (256 x 86 cells of 0.46875
+    theta_E) with `fit_stars` stars at the same density (10^6: the learned section's
+    field): its time split into the series coefficients, the training and the
+    validation, the training step time, and the coefficient kernel's pair rate
+    against its FP32 bound (about 254 FP32 lane operations per (cell, far star)
+    pair)."""
+    wl = W.config("learned")
+    f, rays = wl.fields[0], wl.rays[0]
+    if fit_stars != f.n:
+        f = W.random_field(W.SEED_BASE + 4, fit_stars, f.kappa_star, f.kappa_c, f.gamma1, f.gamma2)
+    ctx = M.mlens_create(f.xy, f.m, f.kappa_c, f.gamma1, f.gamma2, M.MLENS_PREC_FP32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rep = M.mlens_fit_far_field(ctx, rays, M.fit_params(cells_x=256, order=order, use_network=1, tolerance=tol))
+    fit_s = time.perf_counter() - t0
+    ctx.close()
+    pairs = rep["cells"] * f.n  # (cell, star) pairs; the near stars (~1e-5 of them) are counted too
+    coef_s = rep["seconds_coefficients"]
+    lane_ops = 254.0
+    return {"stars": f.n, "cells": rep["cells"], "fit_s": fit_s,
+            "seconds": {"coefficients": coef_s, "train": rep["seconds_train"], "validate": rep["seconds_validate"]},
+            "train_steps": rep["train_steps"], "train_step_us": 1e6 * rep["seconds_train"] / max(rep["train_steps"], 1),
+            "fallback_cells": rep["cells_fallback"], "val_max_err": rep["val_max_err_net"],
+            "coefficients": {"pairs": pairs, "pairs_per_s": pairs / coef_s,
+                             "roofline_frac": pairs * lane_ops / coef_s / peak_fp32_lane_ops,
+                             "peak_basis": "FP32 pipe: 128 lane-ops/SM/clk x SMs x max SM clock; "
+                                           f"{lane_ops:.0f} lane-ops per (cell, star) pair"}}
 
 
 # ------------------------------------------------------------------- main
@@ -526,7 +628,8 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
         "config": workload_config(args.workload, wl, "fp64 (CPU oracle)", "n/a (CPU)"),
         "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
@@ -553,10 +656,16 @@ def run_mine(args):
     M.load()
     prec = M.PRECISIONS[args.precision]
 
+    from paper_1703_09707_gb300 import partition as P
+
     wl = W.config(args.workload, rays_scale=args.rays_scale)
     f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
-    f = rank_field(wl, rank)
-    n_inter = rays.n * f.n
+    strong = args.scaling == "strong"
+    if not strong:
+        f = rank_field(wl, rank)
+    band = P.row_bands(rays.ny, world)[rank] if strong else (0, rays.ny)
+    n_inter = rays.nx * (band[1] - band[0]) * f.n   # this rank's interactions per step
+    n_inter_job = rays.n * f.n * (1 if strong else world)
 
     ctx = M.mlens_create(f.xy, f.m, f.kappa_c, f.gamma1, f.gamma2, prec)
     M.mlens_set_tuning(ctx, args.rays_per_thread, args.star_stage, args.fma_pairs)
@@ -564,11 +673,23 @@ def run_mine(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    st = M.mlens_shoot(ctx, rays, src, counts, stats=True)  # checks the call works; warm the module
-    assert st["rays_binned"] + st["rays_out"] + st["rays_nan"] == rays.n
+    def step(c, counts_buf):
+        """One map: this rank's band, then (N > 1, strong) the sum over ranks."""
+        if band[1] > band[0]:
+            M.mlens_shoot_rows(c, rays, band, src, counts_buf)
+        else:
+            counts_buf.zero_()
+        if strong:
+            P.allreduce_counts(counts_buf)
+
+    st = M.mlens_shoot_rows(ctx, rays, band, src, counts, stats=True)  # checks the call works; warm the module
+    assert st["rays_binned"] + st["rays_out"] + st["rays_nan"] == st["rays_total"]
+    if strong:
+        st = P.shoot_partitioned(ctx, rays, src, counts, stats=True)
+        assert st["rays_total"] == rays.n and st["rays_binned"] + st["rays_out"] + st["rays_nan"] == rays.n
     for _ in range(args.warmup):
         flush.fill_(1.0)
-        M.mlens_shoot(ctx, rays, src, counts)
+        step(ctx, counts)
     torch.cuda.synchronize()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -581,7 +702,7 @@ def run_mine(args):
     for i in range(args.steps):
         flush.fill_(float(i))  # > L2 (129 MB) write between steps, outside the events
         ev[i][0].record(stream)
-        M.mlens_shoot(ctx, rays, src, counts)
+        step(ctx, counts)
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -591,7 +712,7 @@ def run_mine(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     dev_s = sum(step_ms) / 1e3
     dev_s = max_over_ranks(dev_s, device="cuda")
-    value = n_inter * args.steps * world / dev_s
+    value = n_inter_job * args.steps / dev_s
     kernel_ms = statistics.mean(step_ms)
 
     # ------------------------------------------------ end to end through the C ABI
@@ -606,18 +727,20 @@ def run_mine(args):
     for _ in range(e2e_steps):
         c2 = M.mlens_create(f.xy, f.m, f.kappa_c, f.gamma1, f.gamma2, prec)
         M.mlens_set_tuning(c2, args.rays_per_thread, args.star_stage, args.fma_pairs)
-        M.mlens_shoot(c2, rays, src, counts)
+        step(c2, counts)
         host_counts.copy_(counts, non_blocking=True)
         torch.cuda.current_stream().synchronize()
         c2.close()
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_value = n_inter * e2e_steps * world / e2e_s
-    n_pad = (f.n + 255) // 256 * 256
+    e2e_s = max_over_ranks(e2e_s, device="cuda")
+    e2e_value = n_inter_job * e2e_steps / e2e_s
+    n_pad = (f.n + 31) // 32 * 32  # the library pads the stars it uploads to a multiple of 32
     e2e = {"value": e2e_value, "unit": "interactions/s", "h2d_bytes_per_step": int(16 * n_pad),
            "d2h_bytes_per_step": int(4 * src.n), "steps": e2e_steps,
-           "note": "mlens_create from host arrays + mlens_shoot + map download + mlens_destroy, wall clock"}
+           "note": "mlens_create from host arrays + mlens_shoot_rows (+ map all-reduce for N > 1) + map download "
+                   "+ mlens_destroy, wall clock"}
 
     if rank != 0:
         if world > 1:
@@ -643,11 +766,11 @@ def run_mine(args):
     line = {
         "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64",
+        "scaling": args.scaling, "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64",
         "data": "synthetic (seeded star field, paper-shaped)",
         "config": workload_config(args.workload, wl, args.precision,
                                   f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write, outside the events)"),
-        "maps_per_s": args.steps * world / dev_s,
+        "maps_per_s": args.steps * (1 if strong else world) / dev_s,
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": args.steps,
@@ -658,6 +781,10 @@ def run_mine(args):
     line["config"]["rays_per_thread"] = args.rays_per_thread
     line["config"]["fma_pairs"] = args.fma_pairs
     line["config"]["star_stage"] = args.star_stage
+    if world > 1:
+        line["config"]["parallelism"] = (f"ray rows split over {world} ranks ({P.row_bands(rays.ny, world)[0][1]} "
+                                         "rows on rank 0), uint32 maps summed by NCCL all-reduce each step"
+                                         if strong else f"one independent field per rank ({world} ranks)")
     extras = set(x for x in args.extras.split(",") if x)
     if not args.no_extras and world == 1 and args.workload == "paper" and args.rays_scale == 1.0:
         if "batched" in extras:
@@ -676,6 +803,9 @@ def run_mine(args):
         if "learned" in extras:
             line["learned"] = bench_learned(M, torch, max(2, min(args.steps, 3)), flush, args.learned_tol,
                                             args.learned_order)
+        if "fit" in extras:
+            line["fit"] = bench_fit(M, torch, args.fit_stars, args.learned_tol, args.learned_order,
+                                    n_sm * 128 * SM_MAX_MHZ * 1e6)
     if not args.no_cpu_baseline and world == 1:
         v, cores, sample = cpu_oracle_rate(f, rays, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "interactions/s", "cores": cores, "kind": "oracle",

@@ -172,6 +172,29 @@ int mlens_shoot_beta(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid *s
                      void *beta_dev, uint32_t flags, mlens_stats *stats_host, void *stream);
 
 /*
+ * mlens_shoot_rows -- mlens_shoot (or mlens_shoot_beta) restricted to the ray
+ * rows [row_begin, row_end) of the grid `rays`.  Section 2.2 runs the method
+ * with several MPI tasks, each tracing part of the rays into its own map, and
+ * reduces the maps into one; this is one task's part.  Rays keep their
+ * positions in the whole grid, and the launch shape, the star split (chosen for
+ * the whole grid) and therefore every ray's beta are those of the whole-grid
+ * call, so the maps of bands that cover the grid add up to the whole map bit for
+ * bit (uint32 addition; a sum reduction across processes is exact).
+ *   row_begin, row_end  0 <= row_begin <= row_end <= rays.ny, each a multiple
+ *              of MLENS_ROW_ALIGN or row_end = rays.ny; 0, 0 = all rows.
+ *   beta_dev   nullable; as for mlens_shoot_beta (the whole grid's
+ *              rays.nx*rays.ny records), only the band's records are written.
+ *   counts_dev, flags, stats_host, stream  as for mlens_shoot; stats count the
+ *              band's rays (rays_total = rays.nx * (row_end - row_begin)).
+ * Errors: MLENS_ERR_ARG (rows not aligned or out of range, and as mlens_shoot),
+ * MLENS_ERR_CUDA.
+ */
+#define MLENS_ROW_ALIGN 32
+int mlens_shoot_rows(mlens_ctx *ctx, const mlens_grid *rays, int32_t row_begin, int32_t row_end,
+                     const mlens_grid *src, uint32_t *counts_dev, void *beta_dev, uint32_t flags,
+                     mlens_stats *stats_host, void *stream);
+
+/*
  * mlens_trace -- FP64 deflection at arbitrary image positions (Eq. 2-3), for
  * verification and for generating exact targets.  Uses the IEEE FP64 kernel
  * whatever the context's precision.

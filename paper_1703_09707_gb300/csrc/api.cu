@@ -7,6 +7,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <cmath>
 #include <atomic>
 #include <cstdlib>
@@ -118,6 +119,9 @@ int read_stats(unsigned long long *d_stats, uint64_t total, mlens_stats *st, cud
     return MLENS_OK;
 }
 
+// Ray rows per tile of the FP32 kernels (the FP64 kernel's 4-row blocks divide it).
+int tile_rows_of(const mlens_ctx *ctx) { return 8 * ctx->pairs_per_thread; }
+
 // CTAs per tile for the FP32 re-centred kernel: the split star sum runs with the
 // default stage and MUFU reciprocals only.
 int effective_split(const mlens_ctx *ctx, const RayGrid &r)
@@ -127,12 +131,18 @@ int effective_split(const mlens_ctx *ctx, const RayGrid &r)
     return auto_star_split(r, ctx->pairs_per_thread, ctx->n_pad, ctx->nsm);
 }
 
+// Rays rows [row0, row1) of the grid (row1 < 0: all rows).
 int shoot_impl(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid *src, uint32_t *counts, void *beta,
-               uint32_t flags, mlens_stats *stats, void *stream)
+               uint32_t flags, mlens_stats *stats, void *stream, int row0 = 0, int row1 = -1)
 {
     if (!ctx) return fail(MLENS_ERR_ARG, "context is NULL");
     int rc;
     if ((rc = check_rays(rays)) || (rc = check_src(src))) return rc;
+    if (row1 < 0) row1 = rays->ny;
+    if (row0 < 0 || row0 > row1 || row1 > rays->ny || row0 % MLENS_ROW_ALIGN != 0 ||
+        (row1 % MLENS_ROW_ALIGN != 0 && row1 != rays->ny))
+        return fail(MLENS_ERR_ARG, "rows must satisfy 0 <= row_begin <= row_end <= rays.ny, both multiples of "
+                                   "MLENS_ROW_ALIGN (32) or row_end = rays.ny");
     if (!counts) return fail(MLENS_ERR_ARG, "counts_dev is NULL");
     if (((uintptr_t)counts & 3u) != 0) return fail(MLENS_ERR_ARG, "counts_dev must be 4-byte aligned");
     if (beta && ((uintptr_t)beta & 15u) != 0) return fail(MLENS_ERR_ARG, "beta_dev must be 16-byte aligned");
@@ -152,17 +162,22 @@ int shoot_impl(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid *src, ui
     a.counts = counts;
     a.stats = ctx->d_stats;
     a.beta_out = beta;
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
+    // the split follows the whole grid, so a band of rows equals those rows of the
+    // whole map bit for bit
     const int split = effective_split(ctx, a.rays);
-    if (ctx->precision == MLENS_PREC_FP64)
-        e = launch_shoot_fp64(a, s);
-    else if (split > 1)
-        e = launch_shoot_split(a, ctx->pairs_per_thread, split, s);
-    else
-        e = launch_shoot_fp32(a, ctx->pairs_per_thread, ctx->precision == MLENS_PREC_FP32_NAIVE, s, ctx->star_stage,
-                              ctx->fma_pairs);
+    const int th = tile_rows_of(ctx);  // divides MLENS_ROW_ALIGN
+    if (row1 > row0) {
+        if (ctx->precision == MLENS_PREC_FP64)
+            e = launch_shoot_fp64(a, s, row0, row1);
+        else if (split > 1)
+            e = launch_shoot_split(a, ctx->pairs_per_thread, split, s, row0 / th, (row1 + th - 1) / th);
+        else
+            e = launch_shoot_fp32(a, ctx->pairs_per_thread, ctx->precision == MLENS_PREC_FP32_NAIVE, s,
+                                  ctx->star_stage, ctx->fma_pairs, row0 / th, (row1 + th - 1) / th);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "shoot kernel launch");
-    if (stats) return read_stats(ctx->d_stats, (uint64_t)rays->nx * (uint64_t)rays->ny, stats, s);
+    if (stats) return read_stats(ctx->d_stats, (uint64_t)rays->nx * (uint64_t)(row1 - row0), stats, s);
     return MLENS_OK;
 }
 
@@ -243,6 +258,19 @@ BinGrid make_bin_grid(const mlens_grid &g)
     return b;
 }
 
+// The value of the lowest set bit of x's significand (x = m 2^e, m odd: 2^e);
+// +infinity for 0.
+static double low_bit(double x)
+{
+    if (x == 0.0) return INFINITY;
+    int e = 0;
+    const double m = std::frexp(std::fabs(x), &e);  // m in [1/2, 1)
+    const uint64_t M = (uint64_t)std::ldexp(m, 53);
+    int tz = 0;
+    while (((M >> tz) & 1u) == 0) ++tz;
+    return std::ldexp(1.0, e - 53 + tz);
+}
+
 RayGrid make_ray_grid(const mlens_grid &g)
 {
     RayGrid r;
@@ -258,6 +286,20 @@ RayGrid make_ray_grid(const mlens_grid &g)
     r.dxl = (float)(r.dx - (double)r.dxh);
     r.dyh = (float)r.dy;
     r.dyl = (float)(r.dy - (double)r.dyh);
+    r.qx = std::ldexp(1.0, std::ilogb(r.dx));
+    r.qy = std::ldexp(1.0, std::ilogb(r.dy));
+    r.qxinv = 1.0 / r.qx;
+    r.qyinv = 1.0 / r.qy;
+    // Ray offsets from the tile centres are exact floats when every ray position
+    // x0 + (i + 1/2) dx and every centre (0 or a multiple of qx) is a multiple of
+    // one power of two g with all offsets below 2^24 g: g = the lowest set bit of
+    // dx/2, x0 and qx; offsets stay within 6 tile extents.  Then the kernels need
+    // no low parts (the workloads' dyadic grids); otherwise they add them.
+    auto exact_axis = [](double x0, double d, double q, int tile) {
+        const double g = std::min(std::min(low_bit(0.5 * d), low_bit(x0)), q);
+        return 6.0 * tile * d < std::ldexp(g, 24);
+    };
+    r.lo = (exact_axis(g.x0, r.dx, r.qx, 64) && exact_axis(g.y0, r.dy, r.qy, 32)) ? 0 : 1;
     return r;
 }
 
@@ -429,6 +471,14 @@ int mlens_shoot_beta(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid *s
 {
     if (!beta_dev) return fail(MLENS_ERR_ARG, "beta_dev is NULL");
     return shoot_impl(ctx, rays, src, counts_dev, beta_dev, flags, stats_host, stream);
+}
+
+int mlens_shoot_rows(mlens_ctx *ctx, const mlens_grid *rays, int32_t row_begin, int32_t row_end,
+                     const mlens_grid *src, uint32_t *counts_dev, void *beta_dev, uint32_t flags,
+                     mlens_stats *stats_host, void *stream)
+{
+    if (rays && row_begin == 0 && row_end == 0) row_end = rays->ny;
+    return shoot_impl(ctx, rays, src, counts_dev, beta_dev, flags, stats_host, stream, row_begin, row_end);
 }
 
 int mlens_trace(mlens_ctx *ctx, const double *theta, int64_t k, double *beta, void *stream)

@@ -180,6 +180,38 @@ __device__ __forceinline__ FarTerm far_term(float4 q, float zxh, float zxl, floa
     return t;
 }
 
+// Sums over the warp's lanes of the per-lane partials v[p] of orders p + 1 = 1 ..
+// kPtMax, scattered so that lane q receives the sum of order q (lane 0 and lanes
+// beyond kPtMax receive zero): a fold of 32 columns (orders 0 .. 31, the missing
+// ones zero) in five halving steps, the lane's bit deciding which half it keeps.
+// The order of the additions is fixed.
+__device__ __forceinline__ float warp_scatter_orders(float (&v)[kPtMax])
+{
+    static_assert(kPtMax < 32, "orders fit in one warp");
+    const int lane = threadIdx.x & 31;
+    float c[16];
+    {  // step 16: columns 0..15 against 16..31 (column q holds v[q - 1])
+        const bool up = (lane & 16) != 0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const float lo = j == 0 ? 0.0f : v[j - 1];
+            const float hi = j + 15 < kPtMax ? v[j + 15] : 0.0f;
+            const float give = up ? lo : hi, keep = up ? hi : lo;
+            c[j] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+        }
+    }
+#pragma unroll
+    for (int step = 8; step >= 1; step >>= 1) {
+        const bool up = (lane & step) != 0;
+#pragma unroll
+        for (int j = 0; j < step; ++j) {
+            const float give = up ? c[j] : c[j + step], keep = up ? c[j + step] : c[j];
+            c[j] = keep + __shfl_xor_sync(0xffffffffu, give, step);
+        }
+    }
+    return c[0];
+}
+
 // Three CTAs per SM (80 registers; the spills of the partials cost less than the
 // latency the third CTA hides: 0.66 -> 0.61 s for 22016 cells x 1e6 stars).
 __global__ void __launch_bounds__(256, 3) k_coeffs(const float4 *stars, const int *scell, int64_t n, CellGrid g, int pt,
@@ -209,8 +241,11 @@ __global__ void __launch_bounds__(256, 3) k_coeffs(const float4 *stars, const in
     const float zyh = (float)zy, zyl = (float)(zy - (double)zyh);
     const float fscale = (float)scale;
     const float4 pad = make_float4(kPadCoord, kPadCoord, 0.0f, 0.0f);
-    double b0r = 0.0, b0i = 0.0;    // order 0, this lane's stars
-    double accr = 0.0, acci = 0.0;  // lane p (1 <= p <= pt): coefficient p, all stages
+    // running sums in double-float on the FP32 pipe (GB300's FP64 rate is a small
+    // fraction of FP32: FP64 accumulation once per stage had made the FP64 pipe the
+    // kernel's bound)
+    DF b0r = {0.0f, 0.0f}, b0i = {0.0f, 0.0f};    // order 0, this lane's stars
+    DF accr = {0.0f, 0.0f}, acci = {0.0f, 0.0f};  // lane p (1 <= p <= pt): coefficient p, all stages
     for (int64_t s0 = 0; s0 < n; s0 += 256) {
         const int cnt = (int)min((int64_t)256, n - s0);
         __syncthreads();
@@ -254,33 +289,27 @@ __global__ void __launch_bounds__(256, 3) k_coeffs(const float4 *stars, const in
                 pi[p] += __fadd_rn(fi.x, fi.y);
             }
         }
-        b0r += (double)sr.h + (double)sr.l;
-        b0i += (double)si.h + (double)si.l;
-#pragma unroll
-        for (int p = 0; p < kPtMax; ++p) {
-            float r = pr[p], i = pi[p];
-            for (int o = 16; o; o >>= 1) {
-                r += __shfl_xor_sync(0xffffffffu, r, o);
-                i += __shfl_xor_sync(0xffffffffu, i, o);
-            }
-            if (lane == p + 1) {
-                accr += (double)r;
-                acci += (double)i;
-            }
-        }
+        b0r = df_add(b0r, sr);
+        b0i = df_add(b0i, si);
+        // the stage's sums over the warp, scattered: afterwards lane q holds the sum of
+        // order q (q = 1 .. kPtMax) of the stage (reduce-scatter, 31 shuffles per part)
+        const float r = warp_scatter_orders(pr), i = warp_scatter_orders(pi);
+        accr = df_add(accr, {r, 0.0f});
+        acci = df_add(acci, {i, 0.0f});
     }
     if (!ok) return;
+    double c0r = (double)b0r.h + (double)b0r.l, c0i = (double)b0i.h + (double)b0i.l;
     for (int o = 16; o; o >>= 1) {
-        b0r += __shfl_xor_sync(0xffffffffu, b0r, o);
-        b0i += __shfl_xor_sync(0xffffffffu, b0i, o);
+        c0r += __shfl_xor_sync(0xffffffffu, c0r, o);
+        c0i += __shfl_xor_sync(0xffffffffu, c0i, o);
     }
     double *dst = out + (int64_t)rc * (pt + 1) * 2;
     if (lane == 0) {
-        dst[0] = b0r;
-        dst[1] = b0i;
+        dst[0] = c0r;
+        dst[1] = c0i;
     } else if (lane <= pt) {
-        dst[2 * lane] = accr;
-        dst[2 * lane + 1] = acci;
+        dst[2 * lane] = (double)accr.h + (double)accr.l;
+        dst[2 * lane + 1] = (double)acci.h + (double)acci.l;
     }
 }
 
@@ -361,18 +390,14 @@ cudaError_t ff_init_params(float *params, float *z, int nrc, uint64_t seed, cuda
     return cudaGetLastError();
 }
 
-__global__ void k_prep_bf16(const float *p, __nv_bfloat16 *w1zb, __nv_bfloat16 *w2b)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < kHid * kHid) w2b[i] = to_bf16(p[oW2 + i]);
-    if (i < kHid * kLat) w1zb[i] = to_bf16(p[oW1z + i]);
-}
-
-cudaError_t ff_prep_bf16(const float *params, __nv_bfloat16 *w1zb, __nv_bfloat16 *w2b, cudaStream_t s)
-{
-    k_prep_bf16<<<(kHid * kHid + 255) / 256, 256, 0, s>>>(params, w1zb, w2b);
-    return cudaGetLastError();
-}
+// Programmatic dependent launch between the training steps' kernels: a kernel
+// launched with programmatic stream serialisation may begin while the one before
+// it finishes; pdl_wait() returns once that one has completed and its writes are
+// visible, and pdl_launch_next() lets the next kernel begin launching once every
+// CTA of this one has called it.  Both do nothing in a kernel launched without
+// the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // ===================================================== training kernel
 constexpr int kWaitPolls = 1 << 20;  // bound on a tensor-core completion wait
@@ -424,6 +449,52 @@ struct TrainTc {
     // the dh1 pass has read both
     static constexpr int cH1 = 0, cH2 = 64, cDA1 = 64, cDW2 = 0, cDZ = 64, cDW1z = 96, ncols = 128;
 };
+
+// The training kernel's weight operands as they sit in its shared memory (W1z, W2,
+// W2T, W1zT at their TrainTc offsets): written wherever the BF16 weight copies are
+// refreshed, so that a training CTA stages them with 16-byte copies.
+constexpr int kWImgBytes = TrainTc::Z;
+static_assert(kWImgBytes % 16 == 0, "the weight image is copied in 16-byte units");
+
+// Entry i of the flat parameter vector (a W1z or W2 weight), rounded to BF16, into
+// its two places of the image (the operand and its transpose).
+__device__ __forceinline__ void wimg_put(unsigned char *img, int64_t i, __nv_bfloat16 b)
+{
+    using L = TrainTc;
+    if (i >= oW1z && i < oW1z + kHid * kLat) {
+        const int o = (int)(i - oW1z) / kLat, k = (int)(i - oW1z) % kLat;
+        *reinterpret_cast<__nv_bfloat16 *>(img + L::W1z + tc_off(o, k, kLat)) = b;
+        *reinterpret_cast<__nv_bfloat16 *>(img + L::W1zT + tc_off(k, o, kHid)) = b;
+    } else if (i >= oW2 && i < oW2 + kHid * kHid) {
+        const int o = (int)(i - oW2) / kHid, k = (int)(i - oW2) % kHid;
+        *reinterpret_cast<__nv_bfloat16 *>(img + L::W2 + tc_off(o, k, kHid)) = b;
+        *reinterpret_cast<__nv_bfloat16 *>(img + L::W2T + tc_off(k, o, kHid)) = b;
+    }
+}
+
+__global__ void k_prep_bf16(const float *p, __nv_bfloat16 *w1zb, __nv_bfloat16 *w2b, unsigned char *wimg)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kHid * kHid) {
+        const __nv_bfloat16 b = to_bf16(p[oW2 + i]);
+        w2b[i] = b;
+        wimg_put(wimg, oW2 + i, b);
+    }
+    if (i < kHid * kLat) {
+        const __nv_bfloat16 b = to_bf16(p[oW1z + i]);
+        w1zb[i] = b;
+        wimg_put(wimg, oW1z + i, b);
+    }
+}
+
+cudaError_t ff_prep_bf16(const float *params, __nv_bfloat16 *w1zb, __nv_bfloat16 *w2b, unsigned char *wimg,
+                         cudaStream_t s)
+{
+    k_prep_bf16<<<(kHid * kHid + 255) / 256, 256, 0, s>>>(params, w1zb, w2b, wimg);
+    return cudaGetLastError();
+}
+
+int64_t ff_weight_image_bytes() { return kWImgBytes; }
 
 // One training / validation sample: a cell and a uniform position in its ray-covered
 // part; the target is q(v) / s_c with q(v) = sum_{pe < p <= pt} b_p v^(p-pe-1) (so that
@@ -812,36 +883,36 @@ __global__ void __launch_bounds__(256, 2) k_ff_train(TrainArgs A)
     int *I = reinterpret_cast<int *>(tsm);
     const int tid = threadIdx.x;
 
-    // ---- weights: BF16 operands in core-matrix layout, FP32 small parameters
-    // (8 BF16 = one 16-byte core-matrix row per load; the copies are 16-byte aligned)
-    for (int i = tid; i < kHid * kLat / 8; i += 256) {
-        const int o = 8 * i / kLat, k = 8 * i % kLat;
-        const uint4 w = reinterpret_cast<const uint4 *>(A.w1zb)[i];
-        *reinterpret_cast<uint4 *>(tsm + L::W1z + tc_off(o, k, kLat)) = w;
-        const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&w);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) *reinterpret_cast<__nv_bfloat16 *>(tsm + L::W1zT + tc_off(k + j, o, kHid)) = e[j];
+    // ---- samples: generated ones depend only on the fit's fixed tables and run before
+    // the wait on the previous kernel (explicit ones are read after it)
+    const bool gen = A.zin == nullptr;
+    if (gen && tid < kSampC) {
+        const int64_t li = (int64_t)blockIdx.x * kSampC + tid;
+        const bool valid = li < A.spec.count;
+        int rc = 0;
+        float ux = 0.f, uy = 0.f, tx = 0.f, ty = 0.f, scv = 1.0f, vp = 1.0f;
+        if (valid) sample_of(A, li, rc, ux, uy, tx, ty, scv, vp);
+        F[L::U / 4 + 2 * tid] = ux;
+        F[L::U / 4 + 2 * tid + 1] = uy;
+        F[L::T / 4 + 2 * tid] = tx;
+        F[L::T / 4 + 2 * tid + 1] = ty;
+        F[L::SV / 4 + tid] = scv * vp;
+        I[L::RC / 4 + tid] = rc;
+        I[L::OK / 4 + tid] = valid ? 1 : 0;
     }
-    for (int i = tid; i < kHid * kHid / 8; i += 256) {
-        const int o = 8 * i / kHid, k = 8 * i % kHid;
-        const uint4 w = reinterpret_cast<const uint4 *>(A.w2b)[i];
-        *reinterpret_cast<uint4 *>(tsm + L::W2 + tc_off(o, k, kHid)) = w;
-        const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&w);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) *reinterpret_cast<__nv_bfloat16 *>(tsm + L::W2T + tc_off(k + j, o, kHid)) = e[j];
+    if (tid == 0) {
+        umma::mbar_init(&bar, 1);
+        umma::mbar_init(&idle, 1);
+        umma::fence_mbar_init();
     }
-    if (tid < 2 * kHid) {
-        F[L::W1u / 4 + tid] = A.params[oW1u + tid];
-        F[L::W3 / 4 + tid] = A.params[oW3 + tid];
-    }
-    if (tid < kHid) {
-        F[L::b1 / 4 + tid] = A.params[ob1 + tid];
-        F[L::b2 / 4 + tid] = A.params[ob2 + tid];
-    }
-    if (tid < 2) F[L::b3 / 4 + tid] = A.params[ob3 + tid];
-    // ---- latents of this thread's sample (columns 16 wg .. 16 wg + 15), loaded first so
-    // that they are in flight during the sample generation: sample i's cell is
-    // (offset + i) mod nrc
+    if (tid < 32) umma::tmem_alloc(&tmem, L::ncols);
+    // ---- the previous kernel's results: weights, latents.  Only after the wait may the
+    // next kernel (the step's update, which reads what the previous update wrote
+    // before its own wait) begin launching.
+    pdl_wait();
+    pdl_launch_next();
+    // ---- latents of this thread's sample (columns 16 wg .. 16 wg + 15), in flight during
+    // the weight staging: sample i's cell is (offset + i) mod nrc
     float zv[16];
     {
         const int s = tid & (kSampC - 1), wg = tid >> 7;
@@ -864,36 +935,37 @@ __global__ void __launch_bounds__(256, 2) k_ff_train(TrainArgs A)
             for (int j = 0; j < 16; ++j) zv[j] = src[j];
         }
     }
-    // ---- samples
-    if (tid < kSampC) {
+    // ---- weights: the BF16 operands' shared-memory image (16-byte copies), FP32
+    // small parameters
+    for (int i = tid; i < kWImgBytes / 16; i += 256)
+        reinterpret_cast<uint4 *>(tsm)[i] = reinterpret_cast<const uint4 *>(A.wimg)[i];
+    if (tid < 2 * kHid) {
+        F[L::W1u / 4 + tid] = A.params[oW1u + tid];
+        F[L::W3 / 4 + tid] = A.params[oW3 + tid];
+    }
+    if (tid < kHid) {
+        F[L::b1 / 4 + tid] = A.params[ob1 + tid];
+        F[L::b2 / 4 + tid] = A.params[ob2 + tid];
+    }
+    if (tid < 2) F[L::b3 / 4 + tid] = A.params[ob3 + tid];
+    if (!gen && tid < kSampC) {
         const int64_t li = (int64_t)blockIdx.x * kSampC + tid;
         const bool valid = li < A.spec.count;
-        int rc = 0;
-        float ux = 0.f, uy = 0.f, tx = 0.f, ty = 0.f, scv = 1.0f, vp = 1.0f;
+        float ux = 0.f, uy = 0.f, tx = 0.f, ty = 0.f;
         if (valid) {
-            if (A.zin) {
-                ux = A.uin[2 * li];
-                uy = A.uin[2 * li + 1];
-                tx = A.tin ? A.tin[2 * li] : 0.f;
-                ty = A.tin ? A.tin[2 * li + 1] : 0.f;
-            } else {
-                sample_of(A, li, rc, ux, uy, tx, ty, scv, vp);
-            }
+            ux = A.uin[2 * li];
+            uy = A.uin[2 * li + 1];
+            tx = A.tin ? A.tin[2 * li] : 0.f;
+            ty = A.tin ? A.tin[2 * li + 1] : 0.f;
         }
         F[L::U / 4 + 2 * tid] = ux;
         F[L::U / 4 + 2 * tid + 1] = uy;
         F[L::T / 4 + 2 * tid] = tx;
         F[L::T / 4 + 2 * tid + 1] = ty;
-        F[L::SV / 4 + tid] = scv * vp;
-        I[L::RC / 4 + tid] = rc;
+        F[L::SV / 4 + tid] = 1.0f;
+        I[L::RC / 4 + tid] = 0;
         I[L::OK / 4 + tid] = valid ? 1 : 0;
     }
-    if (tid == 0) {
-        umma::mbar_init(&bar, 1);
-        umma::mbar_init(&idle, 1);
-        umma::fence_mbar_init();
-    }
-    if (tid < 32) umma::tmem_alloc(&tmem, L::ncols);
     umma::fence_before();
     __syncthreads();
     umma::fence_after();
@@ -911,7 +983,25 @@ __global__ void __launch_bounds__(256, 2) k_ff_train(TrainArgs A)
     if (tid < 32) umma::tmem_dealloc(tm, L::ncols);
 }
 
-cudaError_t ff_train_step(const TrainArgs &t, int64_t nsamples, cudaStream_t s)
+// Launch with programmatic stream serialisation (PDL): the kernel may begin while
+// the previous one of the stream finishes (see pdl_wait).
+template <class... P, class... A>
+static cudaError_t launch_pdl(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+cudaError_t ff_train_step(const TrainArgs &t, int64_t nsamples, cudaStream_t s, bool pdl)
 {
     // two CTAs of ~110 KB per SM: the largest shared-memory carveout
     cudaError_t e = cudaFuncSetAttribute(k_ff_train, cudaFuncAttributeMaxDynamicSharedMemorySize, TrainTc::bytes);
@@ -921,6 +1011,7 @@ cudaError_t ff_train_step(const TrainArgs &t, int64_t nsamples, cudaStream_t s)
     if (e != cudaSuccess) return e;
     if (nsamples <= 0) return cudaSuccess;
     const unsigned nb = (unsigned)((nsamples + kSampC - 1) / kSampC);
+    if (pdl) return launch_pdl(k_ff_train, dim3(nb), dim3(256), TrainTc::bytes, s, t);
     k_ff_train<<<nb, 256, TrainTc::bytes, s>>>(t);
     return cudaGetLastError();
 }
@@ -960,60 +1051,100 @@ __global__ void __launch_bounds__(kRedCols * kRedGroups) k_reduce_grads(const fl
     }
 }
 
-// dz[c][k] = sum of the step's samples of cell c in sample order: sample li of
-// the step is sample offset + li of the sequence, whose cell is its index mod nrc.
-__global__ void k_reduce_latents(const float *__restrict__ dzs, int64_t count, int64_t offset, int nrc,
-                                 float *__restrict__ dz)
-{
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)nrc * kLat) return;
-    const int c = (int)(e / kLat), k = (int)(e % kLat);
-    int64_t li = ((int64_t)c - offset % nrc + nrc) % nrc;
-    float acc = 0.0f;
-    for (; li < count; li += nrc) acc += dzs[li * kLat + k];
-    dz[e] = acc;
-}
-
 cudaError_t ff_reduce_grads(const float *gpart, int64_t nblk, float *grads, float *loss, cudaStream_t s)
 {
     k_reduce_grads<<<(kParams + 1 + kRedCols - 1) / kRedCols, kRedCols * kRedGroups, 0, s>>>(gpart, nblk, grads, loss);
     return cudaGetLastError();
 }
 
-cudaError_t ff_reduce_latents(const float *dzs, int64_t count, int64_t offset, int nrc, float *dz, cudaStream_t s)
+
+
+// The rest of a training step in one launch: the weight gradients summed over the
+// step's CTA rows (as k_reduce_grads: 32 columns per CTA, eight row groups in row
+// order, then in group order), each latent's gradient over the step's samples of
+// its cell in sample order (sample li of the step is sample offset + li of the
+// sequence, whose cell is its index mod nrc), and the Adam update (Kingma & Ba
+// 2015) of every parameter with its sum, refreshing the BF16 weight copies and the
+// training kernel's operand image.  The summation orders are fixed, so training is
+// bit-reproducible.
+__global__ void __launch_bounds__(kRedCols * kRedGroups) k_step_update(StepUpdate U)
 {
-    const int64_t n = (int64_t)nrc * kLat;
-    k_reduce_latents<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dzs, count, offset, nrc, dz);
-    return cudaGetLastError();
+    constexpr int kWBlocks = (kParams + 1 + kRedCols - 1) / kRedCols;
+    // the next training step may begin launching; this thread's parameter and Adam
+    // moments (last written two kernels back) are read before the wait for the
+    // step's gradients
+    pdl_launch_next();
+    int64_t mine = -1;
+    if (blockIdx.x < kWBlocks) {
+        const int p = blockIdx.x * kRedCols + threadIdx.x % kRedCols;
+        if (threadIdx.x / kRedCols == 0 && p < kParams) mine = p;
+    } else {
+        const int64_t e = (int64_t)(blockIdx.x - kWBlocks) * blockDim.x + threadIdx.x;
+        if (e < (int64_t)U.nrc * kLat) mine = kParams + e;
+    }
+    float m0 = 0.f, v0 = 0.f, p0 = 0.f;
+    if (mine >= 0) {
+        m0 = U.m[mine];
+        v0 = U.v[mine];
+        p0 = U.p[mine];
+    }
+    pdl_wait();
+    auto adam_one = [&](int64_t i, float gi) {
+        const float mi = U.b1 * m0 + (1.0f - U.b1) * gi;
+        const float vi = U.b2 * v0 + (1.0f - U.b2) * gi * gi;
+        U.m[i] = mi;
+        U.v[i] = vi;
+        const float lr = i < kParams ? U.lr_w : U.lr_z;
+        const float pn = p0 - lr * (mi / U.bc1) / (sqrtf(vi / U.bc2) + U.eps);
+        U.p[i] = pn;
+        if (i >= oW1z && i < oW1z + kHid * kLat) {
+            U.w1zb[i - oW1z] = to_bf16(pn);
+            wimg_put(U.wimg, i, to_bf16(pn));
+        }
+        if (i >= oW2 && i < oW2 + kHid * kHid) {
+            U.w2b[i - oW2] = to_bf16(pn);
+            wimg_put(U.wimg, i, to_bf16(pn));
+        }
+    };
+    if (blockIdx.x < kWBlocks) {
+        __shared__ float part[kRedGroups][kRedCols];
+        const int c = threadIdx.x % kRedCols, g = threadIdx.x / kRedCols;
+        const int p = blockIdx.x * kRedCols + c;  // parameter index; kParams is the loss
+        const int64_t per = (U.nblk + kRedGroups - 1) / kRedGroups;
+        const int64_t b0 = g * per, b1 = min(U.nblk, b0 + per);
+        float acc = 0.0f;
+        if (p <= kParams) {
+#pragma unroll 16
+            for (int64_t b = b0; b < b1; ++b) acc += U.gpart[b * kGP + p];
+        }
+        part[g][c] = acc;
+        __syncthreads();
+        if (g == 0 && p <= kParams) {
+            float t = part[0][c];
+#pragma unroll
+            for (int q = 1; q < kRedGroups; ++q) t += part[q][c];
+            if (p < kParams)
+                adam_one(p, t);
+            else if (U.loss)
+                *U.loss = t;
+        }
+        return;
+    }
+    const int64_t e = (int64_t)(blockIdx.x - kWBlocks) * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)U.nrc * kLat) return;
+    const int c = (int)(e / kLat), k = (int)(e % kLat);
+    int64_t li = ((int64_t)c - U.offset % U.nrc + U.nrc) % U.nrc;
+    float acc = 0.0f;
+    for (; li < U.count; li += U.nrc) acc += U.dzs[li * kLat + k];
+    adam_one(kParams + e, acc);
 }
 
-// One Adam step over the weights (the first nw entries, rate lr_w) and the latents
-// (rate lr_z); the updated W1z and W2 are also written as the BF16 copies the next
-// training step reads.
-__global__ void k_adam(float *p, float *m, float *v, const float *g, int64_t n, int64_t nw, float lr_w, float lr_z,
-                       float b1, float b2, float eps, float bc1, float bc2, __nv_bfloat16 *w1zb, __nv_bfloat16 *w2b)
+cudaError_t ff_step_update(const StepUpdate &u, cudaStream_t s)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.0f - b1) * gi;
-    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    const float lr = i < nw ? lr_w : lr_z;
-    const float pn = p[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
-    p[i] = pn;
-    if (i >= oW1z && i < oW1z + kHid * kLat) w1zb[i - oW1z] = to_bf16(pn);
-    if (i >= oW2 && i < oW2 + kHid * kHid) w2b[i - oW2] = to_bf16(pn);
-}
-
-cudaError_t ff_adam(float *p, float *m, float *v, const float *g, int64_t n, int64_t nw, float lr_w, float lr_z,
-                    float b1, float b2, float eps, float bc1, float bc2, __nv_bfloat16 *w1zb, __nv_bfloat16 *w2b,
-                    cudaStream_t s)
-{
-    if (n <= 0) return cudaSuccess;
-    k_adam<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, m, v, g, n, nw, lr_w, lr_z, b1, b2, eps, bc1, bc2, w1zb, w2b);
-    return cudaGetLastError();
+    constexpr int kWBlocks = (kParams + 1 + kRedCols - 1) / kRedCols;
+    const int64_t nlat = (int64_t)u.nrc * kLat;
+    const unsigned grid = (unsigned)(kWBlocks + (nlat + kRedCols * kRedGroups - 1) / (kRedCols * kRedGroups));
+    return launch_pdl(k_step_update, dim3(grid), dim3(kRedCols * kRedGroups), 0, s, u);
 }
 
 // e_c = bf16(W1z) bf16(z_c) + b1 (FP32 accumulation): layer 1 without the position block
@@ -1093,7 +1224,10 @@ constexpr int kTcChunk = 128;                            // rays per tensor-core
 constexpr int kTcABytes = kTcChunk * kHid * 2;           // one warpgroup's A operand (16 KB)
 constexpr int kTcSmem = 2 * kTcABytes;                   // dynamic shared memory of the learned kernel
 
-template <bool NET>
+// LO: the ray offsets carry low parts (grids whose offsets are not exact floats,
+// RayGrid lo); a separate instance so that the exact-offset tiles keep their
+// registers.
+template <bool NET, bool LO>
 __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int by, ShootSmem<256> &sm, TileShared &ts,
                                              LearnSmem &ls, unsigned char *abuf_all, uint32_t &phase)
 {
@@ -1108,7 +1242,8 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
     if (tid == 0) {
         double cxd = R.x0 + ((double)i0 + 0.5 * kTileX) * R.dx;
         double cyd = R.y0 + ((double)j0 + 0.5 * kTileY) * R.dy;
-        float fcx = (float)cxd, fcy = (float)cyd;
+        float fcx = tile_centre(cxd, kTileX * R.dx, R.qx, R.qxinv);
+        float fcy = tile_centre(cyd, kTileY * R.dy, R.qy, R.qyinv);
         double ex = (R.x0 + ((double)i0 + 0.5) * R.dx) - (double)fcx;
         double ey = (R.y0 + ((double)j0 + 0.5) * R.dy) - (double)fcy;
         double bxd = a.lens.a11 * (double)fcx + a.lens.a12 * (double)fcy;
@@ -1122,6 +1257,8 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
         ts.tc[5] = byh;
         ts.tc[6] = (float)(bxd - (double)bxh);
         ts.tc[7] = (float)(byd - (double)byh);
+        ts.tc[8] = (float)(ex - (double)ts.tc[2]);
+        ts.tc[9] = (float)(ey - (double)ts.tc[3]);
         ts.sred[0] = ts.sred[1] = ts.sred[2] = 0u;
         const int ecx = cx + 1, ecy = cy + 1;
         int tot = 0;
@@ -1143,17 +1280,30 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
     if (tid < kHid) reinterpret_cast<float *>(&ls.l1p[tid >> 1])[tid & 1] = L.ec ? L.ec[(int64_t)rc * kHid + tid] : 0.0f;
     __syncthreads();
 
+    // ray offsets from the tile centre: the high parts here, the low parts (LO) formed
+    // inside the near-field loop
     float2 rx, ry[NP], px[NP], py[NP], Sx[NP], Sy[NP], Cx[NP], Cy[NP];
     const float cxf = ts.tc[0], cyf = ts.tc[1];
-    {
+    if (LO) {
+        float h, l, h1, l1;
+        ray_offset((float)tx, ts.tc[2], ts.tc[8], R.dxh, R.dxl, h, l);
+        rx = f2(h, h);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            float k0 = (float)(tg * 2 * NP + 2 * p), k1 = k0 + 1.0f;
+            ray_offset(k0, ts.tc[3], ts.tc[9], R.dyh, R.dyl, h, l);
+            ray_offset(k1, ts.tc[3], ts.tc[9], R.dyh, R.dyl, h1, l1);
+            ry[p] = f2(h, h1);
+            px[p] = py[p] = Sx[p] = Sy[p] = Cx[p] = Cy[p] = f2(0.f, 0.f);
+        }
+    } else {  // exact float offsets: e + k d with every step exact
         const float kx = (float)tx;
-        const float dxr = __fmaf_rn(kx, R.dxh, __fmaf_rn(kx, R.dxl, ts.tc[2]));
+        const float dxr = __fmaf_rn(kx, R.dxh, ts.tc[2]);
         rx = f2(dxr, dxr);
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
             float k0 = (float)(tg * 2 * NP + 2 * p), k1 = k0 + 1.0f;
-            ry[p] = f2(__fmaf_rn(k0, R.dyh, __fmaf_rn(k0, R.dyl, ts.tc[3])),
-                       __fmaf_rn(k1, R.dyh, __fmaf_rn(k1, R.dyl, ts.tc[3])));
+            ry[p] = f2(__fmaf_rn(k0, R.dyh, ts.tc[3]), __fmaf_rn(k1, R.dyh, ts.tc[3]));
             px[p] = py[p] = Sx[p] = Sy[p] = Cx[p] = Cy[p] = f2(0.f, 0.f);
         }
     }
@@ -1180,29 +1330,46 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
         __syncthreads();
         const float4 *Q = sm.st.q[0];
         const float2 *M = sm.st.mm[0];
-        for (int k0 = 0; k0 < cntp; k0 += C) {
+        {
+            float2 rxl = f2(0.f, 0.f), ryl[NP];
 #pragma unroll
-            for (int k = k0; k < k0 + C; ++k) {
-                const float4 q = Q[k];
-                const float2 m2 = M[k];
-                const float2 dx = __fadd2_rn(rx, f2(q.x, q.y));
-                const float2 dx2 = __fmul2_rn(dx, dx);
-                const float2 nyv = f2(q.z, q.w);
+            for (int p = 0; p < NP; ++p) ryl[p] = f2(0.f, 0.f);
+            if (LO) {
+                float h, l, h1, l1;
+                ray_offset((float)tx, ts.tc[2], ts.tc[8], R.dxh, R.dxl, h, l);
+                rxl = f2(l, l);
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
-                    const float2 dy = __fadd2_rn(ry[p], nyv);
-                    const float2 r2 = __ffma2_rn(dy, dy, dx2);
-                    const float2 inv = f2(rcp_approx(r2.x), rcp_approx(r2.y));
-                    const float2 f = __fmul2_rn(m2, inv);
-                    px[p] = __ffma2_rn(f, dx, px[p]);
-                    py[p] = __ffma2_rn(f, dy, py[p]);
+                    float k0 = (float)(tg * 2 * NP + 2 * p), k1 = k0 + 1.0f;
+                    ray_offset(k0, ts.tc[3], ts.tc[9], R.dyh, R.dyl, h, l);
+                    ray_offset(k1, ts.tc[3], ts.tc[9], R.dyh, R.dyl, h1, l1);
+                    ryl[p] = f2(l, l1);
                 }
             }
+            for (int k0 = 0; k0 < cntp; k0 += C) {
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                kahan2(Sx[p], Cx[p], px[p]);
-                kahan2(Sy[p], Cy[p], py[p]);
-                px[p] = py[p] = f2(0.f, 0.f);
+                for (int k = k0; k < k0 + C; ++k) {
+                    const float4 q = Q[k];
+                    const float2 m2 = M[k];
+                    const float2 dx = LO ? __fadd2_rn(__fadd2_rn(rx, f2(q.x, q.y)), rxl) : __fadd2_rn(rx, f2(q.x, q.y));
+                    const float2 dx2 = __fmul2_rn(dx, dx);
+                    const float2 nyv = f2(q.z, q.w);
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        const float2 dy = LO ? __fadd2_rn(__fadd2_rn(ry[p], nyv), ryl[p]) : __fadd2_rn(ry[p], nyv);
+                        const float2 r2 = __ffma2_rn(dy, dy, dx2);
+                        const float2 inv = f2(rcp_approx(r2.x), rcp_approx(r2.y));
+                        const float2 f = __fmul2_rn(m2, inv);
+                        px[p] = __ffma2_rn(f, dx, px[p]);
+                        py[p] = __ffma2_rn(f, dy, py[p]);
+                    }
+                }
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    kahan2(Sx[p], Cx[p], px[p]);
+                    kahan2(Sy[p], Cy[p], py[p]);
+                    px[p] = py[p] = f2(0.f, 0.f);
+                }
             }
         }
     }
@@ -1352,6 +1519,8 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
                 ai = __fadd2_rn(ai, make_float2(c.z, c.w));
                 cmul2();
             }
+            // A delta from the offsets' high parts: the low parts (2^-24 of an offset)
+            // matter only inside the near-field sum, next to a star
             const float2 lx = __ffma2_rn(fa11, rx, __fmul2_rn(fa12, ry[p]));
             const float2 ly = __ffma2_rn(fa12, rx, __fmul2_rn(fa22, ry[p]));
             // alpha_far = (Re F, -Im F) + residual;  F = b0 + T
@@ -1415,7 +1584,7 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
 // NET: the network on the tensor cores (tcgen05; tensor memory and kTcSmem bytes
 // of dynamic shared memory); without it (the series alone) the kernel carries no
 // tensor-core code and no dynamic shared memory.
-template <int NRP, bool NET>
+template <int NRP, bool NET, bool LO>
 // Three CTAs per SM (80 registers, ~100 bytes of spills per thread): six warps per
 // scheduler hide the latency of the 128 hardware tanh per ray better than four
 // (0.060 s -> 0.056 s per 32768^2-ray map at two CTAs per SM and 128 registers).
@@ -1464,9 +1633,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_shoot_learned(LearnedArgs L)
         const int bx = tile % ntx, by = tile / ntx;
         const int rc = (by / L.cg.kty) * L.cg.ncx + bx / L.cg.ktx;
         if (L.flags[rc])
-            shoot_tile<4, 256, false, NRP>(L.plain, bx, by, sm, ts);
+            shoot_tile<4, 256, false, NRP, 1, LO ? 2 : 1>(L.plain, bx, by, sm, ts);
         else
-            learned_tile<NET>(L, bx, by, sm, ts, ls, tc_abuf, phase);
+            learned_tile<NET, LO>(L, bx, by, sm, ts, ls, tc_abuf, phase);
     }
     if (NET) {
         // a warpgroup that gave up on a wait drains its MMAs (again bounded) before
@@ -1499,9 +1668,9 @@ cudaError_t ff_learned_grid(int *grid)
     // by registers, 3 by shared memory), though the occupancy query reports one
     // for it; CTAs beyond those resident only find the shared work queue empty.
     int per_sm = 0, per_sm1 = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shoot_learned<0, false>, kThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shoot_learned<0, false, false>, kThreads, 0);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, k_shoot_learned<1, false>, kThreads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, k_shoot_learned<1, false, false>, kThreads, 0);
     if (e != cudaSuccess) return e;
     per_sm = per_sm < per_sm1 ? per_sm : per_sm1;
     int dev = 0, nsm = 0;
@@ -1511,17 +1680,23 @@ cudaError_t ff_learned_grid(int *grid)
     return cudaSuccess;
 }
 
+template <int NRP, bool LO>
+static cudaError_t launch_learned_t(const LearnedArgs &L, unsigned g, cudaStream_t s)
+{
+    if (L.use_net) {
+        cudaError_t e = learned_attributes(k_shoot_learned<NRP, true, LO>);
+        if (e != cudaSuccess) return e;
+        k_shoot_learned<NRP, true, LO><<<g, kThreads, kTcSmem, s>>>(L);
+    } else {
+        k_shoot_learned<NRP, false, LO><<<g, kThreads, 0, s>>>(L);
+    }
+    return cudaGetLastError();
+}
+
 template <int NRP>
 static cudaError_t launch_learned(const LearnedArgs &L, unsigned g, cudaStream_t s)
 {
-    if (L.use_net) {
-        cudaError_t e = learned_attributes(k_shoot_learned<NRP, true>);
-        if (e != cudaSuccess) return e;
-        k_shoot_learned<NRP, true><<<g, kThreads, kTcSmem, s>>>(L);
-    } else {
-        k_shoot_learned<NRP, false><<<g, kThreads, 0, s>>>(L);
-    }
-    return cudaGetLastError();
+    return L.plain.rays.lo ? launch_learned_t<NRP, true>(L, g, s) : launch_learned_t<NRP, false>(L, g, s);
 }
 
 cudaError_t ff_shoot_learned(const LearnedArgs &L, int grid, int fma_pairs, cudaStream_t s)

@@ -73,12 +73,13 @@ struct TrainArgs {
     // network
     float *params;                     // FP32 master (read)
     const __nv_bfloat16 *w1zb, *w2b;   // BF16 copies of W1z [64][32] and W2 [64][64]
+    const unsigned char *wimg;         // the same as the training kernel's shared-memory operands (16-byte aligned)
     float *grads;                      // host-side bookkeeping: the reduced gradients (flat layout)
     float *loss;                       // validation / forward-only: accumulated loss (sum of squared errors / B)
     // backward: each CTA writes its weight gradients and loss to row blockIdx.x of
     // gpart (ff_gpart_stride floats per row) and each sample its latent gradient
-    // to dzs[sample][32]; ff_reduce_grads / ff_reduce_latents sum them in a fixed
-    // order (deterministic training)
+    // to dzs[sample][32]; ff_step_update (training) or ff_reduce_grads sums them in
+    // a fixed order (deterministic training)
     float *gpart;
     float *dzs;
     // generated samples (training / validation)
@@ -110,17 +111,32 @@ cudaError_t ff_coefficients(const float4 *stars, const int *scell, int64_t n, co
 cudaError_t ff_convert(const double *coef64, const CellGrid &cg, int pe, int pt, float *coef, float *tail, float *sc,
                        cudaStream_t s);
 cudaError_t ff_init_params(float *params, float *z, int nrc, uint64_t seed, cudaStream_t s);
-cudaError_t ff_prep_bf16(const float *params, __nv_bfloat16 *w1zb, __nv_bfloat16 *w2b, cudaStream_t s);
-cudaError_t ff_train_step(const TrainArgs &t, int64_t nsamples, cudaStream_t s);
-// Adam over weights (first nw entries, rate lr_w) and latents (rate lr_z); also
-// refreshes the BF16 copies of W1z and W2.
-cudaError_t ff_adam(float *p, float *m, float *v, const float *g, int64_t n, int64_t nw, float lr_w, float lr_z,
-                    float b1, float b2, float eps, float bc1, float bc2, __nv_bfloat16 *w1zb, __nv_bfloat16 *w2b,
-                    cudaStream_t s);
+// BF16 copies of W1z and W2, and the training kernel's image of its weight
+// operands (ff_weight_image_bytes bytes, 16-byte aligned)
+cudaError_t ff_prep_bf16(const float *params, __nv_bfloat16 *w1zb, __nv_bfloat16 *w2b, unsigned char *wimg,
+                         cudaStream_t s);
+int64_t ff_weight_image_bytes();
+// pdl: launched with programmatic stream serialisation (the training loop: the
+// sample generation overlaps the previous kernel's end)
+cudaError_t ff_train_step(const TrainArgs &t, int64_t nsamples, cudaStream_t s, bool pdl = false);
+// The rest of one training step in one launch: the fixed-order sums of the step's
+// weight and latent gradients, then the Adam update.
+struct StepUpdate {
+    float *p, *m, *v;                  // parameters (weights, then latents), Adam moments
+    const float *gpart;                // the step's CTA gradient rows
+    int64_t nblk;                      // rows
+    const float *dzs;                  // the step's per-sample latent gradients
+    int64_t count, offset;             // samples of the step and the first one's index
+    int nrc;                           // cells (latents)
+    float *loss;                       // receives the step's loss (nullable)
+    float lr_w, lr_z, b1, b2, eps, bc1, bc2;
+    __nv_bfloat16 *w1zb, *w2b;         // BF16 copies of W1z and W2, refreshed
+    unsigned char *wimg;               // and the training kernel's operand image
+};
+cudaError_t ff_step_update(const StepUpdate &u, cudaStream_t s);
 int64_t ff_gpart_stride();                 // floats per CTA row of gpart
 int64_t ff_train_blocks(int64_t nsamples);  // CTAs of one ff_train_step
 cudaError_t ff_reduce_grads(const float *gpart, int64_t nblk, float *grads, float *loss, cudaStream_t s);
-cudaError_t ff_reduce_latents(const float *dzs, int64_t count, int64_t offset, int nrc, float *dz, cudaStream_t s);
 cudaError_t ff_embed(const float *params, const float *z, int nrc, float *ec, cudaStream_t s);
 cudaError_t ff_flags(const unsigned *maxerr, int nrc, float tol, int *flags, cudaStream_t s);
 // fallback tiles use the plain tile function with the context's fma_pairs setting

@@ -35,6 +35,7 @@ struct FarState {
     float *gpart = nullptr, *dzs = nullptr;  // per-CTA gradient rows and per-sample latent gradients of a step
     int64_t gpart_rows = 0, dzs_samples = 0;
     __nv_bfloat16 *w1zb = nullptr, *w2b = nullptr;
+    unsigned char *wimg = nullptr;  // the training kernel's weight operands, as in its shared memory
     float *ec = nullptr;
     int *flags = nullptr;
     unsigned *vmax_net = nullptr, *vmax_series = nullptr;
@@ -82,7 +83,7 @@ void free_state(FarState *f)
     ffree(f->scell), ffree(f->count), ffree(f->start), ffree(f->fill), ffree(f->perm), ffree(f->cstars);
     ffree(f->coef64), ffree(f->coef), ffree(f->tail), ffree(f->sc);
     ffree(f->params), ffree(f->m), ffree(f->v), ffree(f->grads), ffree(f->loss);
-    ffree(f->w1zb), ffree(f->w2b), ffree(f->ec), ffree(f->flags);
+    ffree(f->w1zb), ffree(f->w2b), ffree(f->wimg), ffree(f->ec), ffree(f->flags);
     ffree(f->vmax_net), ffree(f->vmax_series), ffree(f->vsum), ffree(f->items), ffree(f->counter);
     ffree(f->sub_items);
     ffree(f->gpart), ffree(f->dzs), ffree(f->d_err);
@@ -146,6 +147,7 @@ int alloc_state(FarState *f, int64_t nstars)
     FCUDA(dmalloc(&f->loss, sizeof(float) * 2), "cudaMalloc");
     FCUDA(dmalloc(&f->w1zb, sizeof(__nv_bfloat16) * mlp::kHid * mlp::kLat), "cudaMalloc");
     FCUDA(dmalloc(&f->w2b, sizeof(__nv_bfloat16) * mlp::kHid * mlp::kHid), "cudaMalloc");
+    FCUDA(dmalloc(&f->wimg, (size_t)ff_weight_image_bytes()), "cudaMalloc");
     FCUDA(dmalloc(&f->ec, sizeof(float) * (size_t)nrc * mlp::kHid), "cudaMalloc");
     FCUDA(dmalloc(&f->flags, sizeof(int) * nrc), "cudaMalloc");
     FCUDA(dmalloc(&f->vmax_net, sizeof(unsigned) * nrc), "cudaMalloc");
@@ -166,6 +168,7 @@ TrainArgs train_args(FarState *f)
     t.params = f->params;
     t.w1zb = f->w1zb;
     t.w2b = f->w2b;
+    t.wimg = f->wimg;
     t.grads = f->grads;
     t.loss = f->loss;
     t.gpart = f->gpart;
@@ -190,7 +193,7 @@ int validate(FarState *f, int64_t per_cell, uint64_t seed, cudaStream_t s, doubl
     FCUDA(cudaMemsetAsync(f->vmax_net, 0, sizeof(unsigned) * f->nrc, s), "memset");
     FCUDA(cudaMemsetAsync(f->vmax_series, 0, sizeof(unsigned) * f->nrc, s), "memset");
     FCUDA(cudaMemsetAsync(f->vsum, 0, sizeof(double) * 2, s), "memset");
-    FCUDA(ff_prep_bf16(f->params, f->w1zb, f->w2b, s), "prep");
+    FCUDA(ff_prep_bf16(f->params, f->w1zb, f->w2b, f->wimg, s), "prep");
     TrainArgs t = train_args(f);
     t.backward = 0;
     t.loss = nullptr;
@@ -260,7 +263,7 @@ int schedule(FarState *f, cudaStream_t s)
 
 int finish_inference_tables(FarState *f, cudaStream_t s)
 {
-    FCUDA(ff_prep_bf16(f->params, f->w1zb, f->w2b, s), "prep");
+    FCUDA(ff_prep_bf16(f->params, f->w1zb, f->w2b, f->wimg, s), "prep");
     FCUDA(ff_embed(f->params, f->params + mlp::kParams, f->nrc, f->ec, s), "embed");
     return MLENS_OK;
 }
@@ -366,27 +369,42 @@ int mlens_fit_far_field(mlens_ctx *ctx, const mlens_grid *rays, const mlens_fit_
         }
         TrainArgs t = train_args(f);
         t.spec.seed = p.seed * 0x9E3779B97F4A7C15ull + 17;
-        FCUDA(ff_prep_bf16(f->params, f->w1zb, f->w2b, s), "prep");
+        FCUDA(ff_prep_bf16(f->params, f->w1zb, f->w2b, f->wimg, s), "prep");
         for (int64_t k = 0; k < total; ++k) {
             const int64_t j = k % per_epoch;
             const int64_t cnt = std::min<int64_t>(p.batch, p.train_samples - j * p.batch);
             t.spec.offset = j * p.batch;
             t.spec.count = cnt;
             t.inv_batch = 1.0f / (float)cnt;
-            FCUDA(ff_train_step(t, cnt, s), "train step");
-            // gradients summed in a fixed order: training is bit-reproducible
-            FCUDA(ff_reduce_grads(f->gpart, ff_train_blocks(cnt), f->grads, f->loss, s), "gradient reduction");
-            FCUDA(ff_reduce_latents(f->dzs, cnt, t.spec.offset, f->nrc, f->grads + mlp::kParams, s),
-                  "latent gradient reduction");
-            // cosine decay to 5% of the initial rates; the update also refreshes the
-            // BF16 weight copies of the next step
+            FCUDA(ff_train_step(t, cnt, s, true), "train step");
+            // gradients summed in a fixed order (training is bit-reproducible), then
+            // Adam with a cosine decay to 5% of the initial rates; the update also
+            // refreshes the BF16 weight copies of the next step
             const double fr = (double)k / (double)std::max<int64_t>(total - 1, 1);
             const double sc = 0.05 + 0.95 * 0.5 * (1.0 + std::cos(3.14159265358979323846 * fr));
             const double st = (double)(k + 1);
-            const float bc1 = (float)(1.0 - std::pow(0.9, st)), bc2 = (float)(1.0 - std::pow(0.999, st));
-            FCUDA(ff_adam(f->params, f->m, f->v, f->grads, np, mlp::kParams, (float)(p.lr_weights * sc),
-                          (float)(p.lr_latents * sc), 0.9f, 0.999f, 1e-8f, bc1, bc2, f->w1zb, f->w2b, s),
-                  "adam");
+            StepUpdate u{};
+            u.p = f->params;
+            u.m = f->m;
+            u.v = f->v;
+            u.gpart = f->gpart;
+            u.nblk = ff_train_blocks(cnt);
+            u.dzs = f->dzs;
+            u.count = cnt;
+            u.offset = t.spec.offset;
+            u.nrc = f->nrc;
+            u.loss = f->loss;
+            u.lr_w = (float)(p.lr_weights * sc);
+            u.lr_z = (float)(p.lr_latents * sc);
+            u.b1 = 0.9f;
+            u.b2 = 0.999f;
+            u.eps = 1e-8f;
+            u.bc1 = (float)(1.0 - std::pow(0.9, st));
+            u.bc2 = (float)(1.0 - std::pow(0.999, st));
+            u.w1zb = f->w1zb;
+            u.w2b = f->w2b;
+            u.wimg = f->wimg;
+            FCUDA(ff_step_update(u, s), "gradient sums and Adam");
             if (k + 1 == total) FCUDA(cudaMemcpyAsync(&last_loss, f->loss, sizeof(float), cudaMemcpyDeviceToHost, s),
                                       "memcpy(loss)");
             ++steps;
@@ -673,19 +691,23 @@ int mlens_ff_eval(const float *params_dev, const float *z_dev, const float *u_de
     cudaStream_t s = (cudaStream_t)stream;
     __nv_bfloat16 *w = nullptr;
     float *dl = nullptr;
-    FCUDA(dmalloc(&w, sizeof(__nv_bfloat16) * (mlp::kHid * mlp::kLat + mlp::kHid * mlp::kHid)), "cudaMalloc");
+    // BF16 copies of W1z and W2, then the training kernel's operand image (16-byte aligned)
+    const size_t wb = sizeof(__nv_bfloat16) * (mlp::kHid * mlp::kLat + mlp::kHid * mlp::kHid);
+    FCUDA(dmalloc(&w, wb + (size_t)ff_weight_image_bytes()), "cudaMalloc");
     cudaError_t e = dmalloc(&dl, 2 * sizeof(float));  // the loss, then the kernel's error flag
     __nv_bfloat16 *w1zb = w, *w2b = w + mlp::kHid * mlp::kLat;
+    unsigned char *wimg = reinterpret_cast<unsigned char *>(w) + wb;
     float *gpart = nullptr;
     const int64_t nblk = ff_train_blocks(nsamples);
     if (e == cudaSuccess && grads_dev) e = dmalloc(&gpart, sizeof(float) * nblk * ff_gpart_stride());
     if (e == cudaSuccess) e = cudaMemsetAsync(dl, 0, 2 * sizeof(float), s);
-    if (e == cudaSuccess) e = ff_prep_bf16(params_dev, w1zb, w2b, s);
+    if (e == cudaSuccess) e = ff_prep_bf16(params_dev, w1zb, w2b, wimg, s);
     if (e == cudaSuccess) {
         TrainArgs t{};
         t.params = const_cast<float *>(params_dev);
         t.w1zb = w1zb;
         t.w2b = w2b;
+        t.wimg = wimg;
         t.grads = grads_dev;
         t.loss = dl;
         t.gpart = gpart;

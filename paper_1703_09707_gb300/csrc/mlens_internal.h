@@ -38,6 +38,8 @@ struct RayGrid {
     int nx, ny;
     double dx, dy;          // (x1-x0)/nx, (y1-y0)/ny
     float dxh, dxl, dyh, dyl;
+    double qx, qy, qxinv, qyinv;  // largest powers of two <= dx, dy (tile-centre quantum) and inverses
+    int lo;                 // 1: ray offsets from the tile centres need a low part (see make_ray_grid)
 };
 
 // Smooth + shear part of Eq. (1): beta = A theta - star sum, A = I - M,
@@ -83,13 +85,16 @@ struct BatchLaunch {
 // launchers (defined in the .cu files)
 // pairs_per_thread in {2, 4} (4 or 8 rays per thread); stage in {128, 256, 512} stars
 // fma_pairs in {0, 1}: ray pairs per thread whose reciprocal runs on the FMA pipe
+// [ty0, ty1): the tile rows to shoot (tile_rows(pairs_per_thread) ray rows each;
+// ty1 < 0 = through the last)
 cudaError_t launch_shoot_fp32(const ShootArgs &a, int pairs_per_thread, bool naive, cudaStream_t s,
-                              int stage = 256, int fma_pairs = 0);
+                              int stage = 256, int fma_pairs = 0, int ty0 = 0, int ty1 = -1);
 cudaError_t launch_shoot_batch(const BatchLaunch &b, int pairs_per_thread, int stage, cudaStream_t s,
                                int fma_pairs = 0);
 cudaError_t batch_grid_size(int pairs_per_thread, int stage, int *grid, int fma_pairs = 0);
 int64_t tiles_of(const RayGrid &r, int pairs_per_thread);
-cudaError_t launch_shoot_fp64(const ShootArgs &a, cudaStream_t s);
+// ray rows [row0, row1) (row0 a multiple of 4; row1 < 0 = through the last)
+cudaError_t launch_shoot_fp64(const ShootArgs &a, cudaStream_t s, int row0 = 0, int row1 = -1);
 cudaError_t launch_trace_fp64(const float4 *stars, int64_t nstars, const LensTerms &lens, const double2 *theta,
                               double2 *beta, int64_t k, cudaStream_t s);
 // Split star sum (re-centred FP32, 256-star stages, MUFU reciprocals): clusters
@@ -97,7 +102,8 @@ cudaError_t launch_trace_fp64(const float4 *stars, int64_t nstars, const LensTer
 // grid (1 = none) from the wave efficiency on `nsm` SMs.
 constexpr int kSplitStage = 256;
 constexpr int64_t kMinSplitStars = 2048;
-cudaError_t launch_shoot_split(const ShootArgs &a, int pairs_per_thread, int split, cudaStream_t s);
+cudaError_t launch_shoot_split(const ShootArgs &a, int pairs_per_thread, int split, cudaStream_t s, int ty0 = 0,
+                               int ty1 = -1);
 int auto_star_split(const RayGrid &r, int pairs_per_thread, int64_t nstars, int nsm);
 // Tiles of a list (tile = by * tiles_x + bx; 8 rays per thread), one cluster of
 // `split` CTAs per tile; fallback_star_split is the split used for the learned

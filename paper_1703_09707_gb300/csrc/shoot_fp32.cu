@@ -83,12 +83,19 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
 }
 
+// Tile rows [ty0, ty1) of the grid; ty1 < 0 means through the last tile row.
+static inline int tile_row_end(const ShootArgs &a, int np, int ty1)
+{
+    const int ty = (a.rays.ny + tile_rows(np) - 1) / tile_rows(np);
+    return ty1 < 0 || ty1 > ty ? ty : ty1;
+}
+
 template <int NP, int SC, bool NAIVE, int NRP>
-static cudaError_t launch_t(const ShootArgs &a, cudaStream_t s)
+static cudaError_t launch_t(const ShootArgs &a, cudaStream_t s, int ty0, int ty1)
 {
     // tile rows in launches of at most 65535 (the grid's y limit)
-    const int tx = (a.rays.nx + kTileX - 1) / kTileX, ty = (a.rays.ny + tile_rows(NP) - 1) / tile_rows(NP);
-    for (int by0 = 0; by0 < ty; by0 += 65535) {
+    const int tx = (a.rays.nx + kTileX - 1) / kTileX, ty = tile_row_end(a, NP, ty1);
+    for (int by0 = ty0; by0 < ty; by0 += 65535) {
         const dim3 grid((unsigned)tx, (unsigned)min(65535, ty - by0));
         k_shoot_fp32<NP, SC, NAIVE, NRP><<<grid, kThreads, 0, s>>>(a, by0);
         const cudaError_t e = cudaGetLastError();
@@ -98,30 +105,30 @@ static cudaError_t launch_t(const ShootArgs &a, cudaStream_t s)
 }
 
 template <bool NAIVE, int NRP>
-static cudaError_t launch_sel(const ShootArgs &a, int np, int sc, cudaStream_t s)
+static cudaError_t launch_sel(const ShootArgs &a, int np, int sc, cudaStream_t s, int ty0, int ty1)
 {
     if (np == 2) {
-        if (sc == 128) return launch_t<2, 128, NAIVE, NRP>(a, s);
-        if (sc == 512) return launch_t<2, 512, NAIVE, NRP>(a, s);
-        return launch_t<2, 256, NAIVE, NRP>(a, s);
+        if (sc == 128) return launch_t<2, 128, NAIVE, NRP>(a, s, ty0, ty1);
+        if (sc == 512) return launch_t<2, 512, NAIVE, NRP>(a, s, ty0, ty1);
+        return launch_t<2, 256, NAIVE, NRP>(a, s, ty0, ty1);
     }
-    if (sc == 128) return launch_t<4, 128, NAIVE, NRP>(a, s);
-    if (sc == 512) return launch_t<4, 512, NAIVE, NRP>(a, s);
-    return launch_t<4, 256, NAIVE, NRP>(a, s);
+    if (sc == 128) return launch_t<4, 128, NAIVE, NRP>(a, s, ty0, ty1);
+    if (sc == 512) return launch_t<4, 512, NAIVE, NRP>(a, s, ty0, ty1);
+    return launch_t<4, 256, NAIVE, NRP>(a, s, ty0, ty1);
 }
 
 cudaError_t launch_shoot_fp32(const ShootArgs &a, int pairs_per_thread, bool naive, cudaStream_t s, int stage,
-                              int fma_pairs)
+                              int fma_pairs, int ty0, int ty1)
 {
-    if (naive) return launch_sel<true, 0>(a, pairs_per_thread, stage, s);
-    return fma_pairs ? launch_sel<false, 1>(a, pairs_per_thread, stage, s)
-                     : launch_sel<false, 0>(a, pairs_per_thread, stage, s);
+    if (naive) return launch_sel<true, 0>(a, pairs_per_thread, stage, s, ty0, ty1);
+    return fma_pairs ? launch_sel<false, 1>(a, pairs_per_thread, stage, s, ty0, ty1)
+                     : launch_sel<false, 0>(a, pairs_per_thread, stage, s, ty0, ty1);
 }
 
 template <int NP, int SPLIT>
-static cudaError_t launch_split_t(const ShootArgs &a, cudaStream_t s)
+static cudaError_t launch_split_t(const ShootArgs &a, cudaStream_t s, int ty0, int ty1)
 {
-    const int tx = (a.rays.nx + kTileX - 1) / kTileX, ty = (a.rays.ny + tile_rows(NP) - 1) / tile_rows(NP);
+    const int tx = (a.rays.nx + kTileX - 1) / kTileX, ty = tile_row_end(a, NP, ty1);
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = SPLIT;
@@ -142,7 +149,7 @@ static cudaError_t launch_split_t(const ShootArgs &a, cudaStream_t s)
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    for (int by0 = 0; by0 < ty; by0 += 65535) {
+    for (int by0 = ty0; by0 < ty; by0 += 65535) {
         cfg.gridDim = dim3((unsigned)(tx * SPLIT), (unsigned)min(65535, ty - by0));
         const cudaError_t e = cudaLaunchKernelEx(&cfg, k_shoot_split<NP, SPLIT>, a, by0);
         if (e != cudaSuccess) return e;
@@ -204,16 +211,16 @@ int fallback_star_split(int64_t nstars)
     return 1;
 }
 
-cudaError_t launch_shoot_split(const ShootArgs &a, int pairs_per_thread, int split, cudaStream_t s)
+cudaError_t launch_shoot_split(const ShootArgs &a, int pairs_per_thread, int split, cudaStream_t s, int ty0, int ty1)
 {
     if (pairs_per_thread == 2) {
-        if (split == 2) return launch_split_t<2, 2>(a, s);
-        if (split == 4) return launch_split_t<2, 4>(a, s);
-        if (split == 8) return launch_split_t<2, 8>(a, s);
+        if (split == 2) return launch_split_t<2, 2>(a, s, ty0, ty1);
+        if (split == 4) return launch_split_t<2, 4>(a, s, ty0, ty1);
+        if (split == 8) return launch_split_t<2, 8>(a, s, ty0, ty1);
     } else {
-        if (split == 2) return launch_split_t<4, 2>(a, s);
-        if (split == 4) return launch_split_t<4, 4>(a, s);
-        if (split == 8) return launch_split_t<4, 8>(a, s);
+        if (split == 2) return launch_split_t<4, 2>(a, s, ty0, ty1);
+        if (split == 4) return launch_split_t<4, 4>(a, s, ty0, ty1);
+        if (split == 8) return launch_split_t<4, 8>(a, s, ty0, ty1);
     }
     return cudaErrorInvalidValue;
 }

@@ -101,10 +101,13 @@ __global__ void __launch_bounds__(kT64) k_fp64(ShootArgs a, const double2 *theta
     stats_add_block(nb, no, nn, sred, a.stats);
 }
 
-cudaError_t launch_shoot_fp64(const ShootArgs &a, cudaStream_t s)
+cudaError_t launch_shoot_fp64(const ShootArgs &a, cudaStream_t s, int row0, int row1)
 {
-    const int tx = (a.rays.nx + 31) / 32, ty = (a.rays.ny + 3) / 4;
-    for (int by0 = 0; by0 < ty; by0 += 65535) {
+    // blocks of 32 x 4 rays: rows [row0, row1) in block rows (row0 a multiple of 4)
+    const int tx = (a.rays.nx + 31) / 32;
+    const int r1 = row1 < 0 || row1 > a.rays.ny ? a.rays.ny : row1;
+    const int ty = (r1 + 3) / 4;
+    for (int by0 = row0 / 4; by0 < ty; by0 += 65535) {
         const dim3 grid((unsigned)tx, (unsigned)min(65535, ty - by0));
         k_fp64<true><<<grid, kT64, 0, s>>>(a, nullptr, nullptr, 0, by0);
         const cudaError_t e = cudaGetLastError();

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "mlens_dev.cuh"
 
 namespace mlens {
@@ -34,7 +36,7 @@ union ShootSmem {
 };
 
 struct TileShared {
-    float tc[8];       // cx, cy, ex, ey, B0h.x, B0h.y, B0l.x, B0l.y
+    float tc[10];      // cx, cy, ex, ey, B0h.x, B0h.y, B0l.x, B0l.y, exl, eyl
     int win[2];
     unsigned sred[3];
 };
@@ -43,6 +45,43 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 
 // v - c for packed pairs, with one rounding (fma with -1 is exact in the product)
 __device__ __forceinline__ float2 sub2(float2 v, float2 c) { return __ffma2_rn(c, f2(-1.0f, -1.0f), v); }
+
+// The tile centre on one axis, chosen so that the offset of every star near the
+// tile from it is exact in float32: 0 when the tile lies within 4 tile extents of
+// the axis' zero (a star offset is then the star's own coordinate), else the
+// middle of the tile rounded to a multiple of q, the largest power of two not
+// above the ray spacing (RayGrid qx, qy).  A float star coordinate s and a centre
+// c that are both multiples of ulp(s), or both of q, differ by a float whenever
+// |s - c| < |s| (or |s - c| < 2^24 q), which holds for the stars within an extent
+// of the tile (|s| >= 2.5 extents > |s - c|).  Farther stars round as before,
+// with errors small against their distance.
+__device__ __forceinline__ float tile_centre(double mid, double extent, double q, double qinv)
+{
+    if (fabs(mid) < 4.0 * extent) return 0.0f;
+    const double c = rint(mid * qinv) * q;
+    return (float)c == c ? (float)c : (float)mid;
+}
+
+// Offset of ray k of the tile from the tile centre, e + k d with the first ray's
+// offset e = eh + el and the ray spacing d = dh + dl, as a float pair (hi, lo):
+// TwoProduct for k dh (exact with the FMA), TwoSum with eh, the small terms
+// added to the error and the pair renormalised; about 2^-44 relative.  The
+// star loop adds lo after the subtraction of the star's offset, which is exact
+// for the stars close to the ray (tile_centre): there the deflection m/r would
+// magnify the rounding of a float32 offset.  On grids whose ray offsets are
+// exact floats (a dyadic spacing and origin, RayGrid lo = 0) lo is zero and the
+// loop skips the addition, which then changes nothing.
+__device__ __forceinline__ void ray_offset(float k, float eh, float el, float dh, float dl, float &hi, float &lo)
+{
+    const float p = __fmul_rn(k, dh);
+    const float pe = __fmaf_rn(k, dh, -p);
+    const float s = __fadd_rn(eh, p);
+    const float bb = __fsub_rn(s, eh);
+    const float se = __fadd_rn(__fsub_rn(eh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    const float t = __fadd_rn(__fadd_rn(se, pe), __fmaf_rn(k, dl, el));
+    hi = __fadd_rn(s, t);
+    lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
 
 // Kahan step on packed pairs: S + v with compensation C (true sum ~ S - C).
 __device__ __forceinline__ void kahan2(float2 &S, float2 &C, float2 v)
@@ -88,7 +127,10 @@ __device__ __forceinline__ float2 rcp_nr2(float2 x)
 // per thread, in their own shared memory); rank 0 reads them through
 // distributed shared memory in rank order, folds each in with two Kahan steps
 // (S_r, then -C_r) and alone goes on to beta and binning.
-template <int NP, int SC, bool NAIVE, int NRP = 0, int SPLIT = 1>
+// LOM: how the tile learns whether the ray offsets need low parts: 0 = from the grid
+// at run time (RayGrid lo, both loops compiled), 1 = never, 2 = always (callers
+// that have chosen already).
+template <int NP, int SC, bool NAIVE, int NRP = 0, int SPLIT = 1, int LOM = 0>
 __device__ __forceinline__ void shoot_tile(const ShootArgs &a, int bx, int by, ShootSmem<SC> &sm, TileShared &ts,
                                            float4 *part = nullptr)
 {
@@ -104,11 +146,11 @@ __device__ __forceinline__ void shoot_tile(const ShootArgs &a, int bx, int by, S
 
     if (tid == 0) {
         if (!NAIVE) {
-            // tile centre (any float near the middle), offsets of the first ray and
-            // A c in FP64, split into float pairs
+            // tile centre (tile_centre: star offsets near the tile exact), offsets of
+            // the first ray and A c in FP64, split into float pairs
             double cxd = R.x0 + ((double)i0 + 0.5 * kTileX) * R.dx;
             double cyd = R.y0 + ((double)j0 + 0.5 * kTileY) * R.dy;
-            float cx = (float)cxd, cy = (float)cyd;
+            float cx = tile_centre(cxd, kTileX * R.dx, R.qx, R.qxinv), cy = tile_centre(cyd, kTileY * R.dy, R.qy, R.qyinv);
             double ex = (R.x0 + ((double)i0 + 0.5) * R.dx) - (double)cx;
             double ey = (R.y0 + ((double)j0 + 0.5) * R.dy) - (double)cy;
             double bxd = a.lens.a11 * (double)cx + a.lens.a12 * (double)cy;
@@ -122,6 +164,8 @@ __device__ __forceinline__ void shoot_tile(const ShootArgs &a, int bx, int by, S
             ts.tc[5] = byh;
             ts.tc[6] = (float)(bxd - (double)bxh);
             ts.tc[7] = (float)(byd - (double)byh);
+            ts.tc[8] = (float)(ex - (double)ts.tc[2]);
+            ts.tc[9] = (float)(ey - (double)ts.tc[3]);
         }
         ts.sred[0] = ts.sred[1] = ts.sred[2] = 0u;
     }
@@ -130,32 +174,55 @@ __device__ __forceinline__ void shoot_tile(const ShootArgs &a, int bx, int by, S
     // ------------------------------------------------------- this thread's rays
     float2 rx;       // packed (x, x): both rays of a pair share the column
     float2 ry[NP];   // packed (y_2p, y_2p+1)
+    float2 rxl, ryl[NP];               // low parts of the offsets (re-centred variants)
     float2 px[NP], py[NP];             // partial sums (NAIVE: the whole running sum)
     float2 Sx[NP], Sy[NP], Cx[NP], Cy[NP];
     const float kx = (float)tx;
     float cx = 0.f, cy = 0.f;
+    const bool lo = !NAIVE && (LOM == 2 || (LOM == 0 && R.lo));
     if (!NAIVE) {
         cx = ts.tc[0];
         cy = ts.tc[1];
-        float dxr = __fmaf_rn(kx, R.dxh, __fmaf_rn(kx, R.dxl, ts.tc[2]));
-        rx = f2(dxr, dxr);
+        if (lo) {
+            float h, l;
+            ray_offset(kx, ts.tc[2], ts.tc[8], R.dxh, R.dxl, h, l);
+            rx = f2(h, h);
+            rxl = f2(l, l);
 #pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            float k0 = (float)(tg * 2 * NP + 2 * p), k1 = k0 + 1.0f;
-            ry[p] = f2(__fmaf_rn(k0, R.dyh, __fmaf_rn(k0, R.dyl, ts.tc[3])),
-                       __fmaf_rn(k1, R.dyh, __fmaf_rn(k1, R.dyl, ts.tc[3])));
-            px[p] = py[p] = Sx[p] = Sy[p] = Cx[p] = Cy[p] = f2(0.f, 0.f);
+            for (int p = 0; p < NP; ++p) {
+                float k0 = (float)(tg * 2 * NP + 2 * p), k1 = k0 + 1.0f;
+                float h1, l1;
+                ray_offset(k0, ts.tc[3], ts.tc[9], R.dyh, R.dyl, h, l);
+                ray_offset(k1, ts.tc[3], ts.tc[9], R.dyh, R.dyl, h1, l1);
+                ry[p] = f2(h, h1);
+                ryl[p] = f2(l, l1);
+            }
+        } else {
+            // exact float offsets (RayGrid lo = 0): e + k d with every step exact
+            const float dxr = __fmaf_rn(kx, R.dxh, ts.tc[2]);
+            rx = f2(dxr, dxr);
+            rxl = f2(0.f, 0.f);
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                float k0 = (float)(tg * 2 * NP + 2 * p), k1 = k0 + 1.0f;
+                ry[p] = f2(__fmaf_rn(k0, R.dyh, ts.tc[3]), __fmaf_rn(k1, R.dyh, ts.tc[3]));
+                ryl[p] = f2(0.f, 0.f);
+            }
         }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) px[p] = py[p] = Sx[p] = Sy[p] = Cx[p] = Cy[p] = f2(0.f, 0.f);
     } else {
         const float x0f = (float)R.x0, y0f = (float)R.y0;
         const float dxf = (float)R.dx, dyf = (float)R.dy;
         float thx = x0f + ((float)(i0 + tx) + 0.5f) * dxf;
         rx = f2(thx, thx);
+        rxl = f2(0.f, 0.f);
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
             float y0 = y0f + ((float)(j0 + tg * 2 * NP + 2 * p) + 0.5f) * dyf;
             float y1 = y0f + ((float)(j0 + tg * 2 * NP + 2 * p + 1) + 0.5f) * dyf;
             ry[p] = f2(y0, y1);
+            ryl[p] = f2(0.f, 0.f);
             // alpha_0 first (Algorithm 1), then every star is added to it
             px[p] = f2(a.lens.fm11 * thx + a.lens.fm12 * y0, a.lens.fm11 * thx + a.lens.fm12 * y1);
             py[p] = f2(a.lens.fm12 * thx + a.lens.fm22 * y0, a.lens.fm12 * thx + a.lens.fm22 * y1);
@@ -207,34 +274,47 @@ __device__ __forceinline__ void shoot_tile(const ShootArgs &a, int bx, int by, S
         if (s + 1 < nstage) stage_load(s + 1);
         const float4 *Q = sm.st.q[buf];
         const float2 *M = sm.st.mm[buf];
+        // the chunks of the stage; LO: the offsets' low parts are added after the
+        // subtraction (grids whose ray offsets are not exact floats, RayGrid lo)
+        auto chunks = [&](auto lo_tag) {
+            constexpr bool LO = decltype(lo_tag)::value && !NAIVE;
 #pragma unroll 1
-        for (int k0 = 0; k0 < cnt; k0 += kKahan) {
+            for (int k0 = 0; k0 < cnt; k0 += kKahan) {
 #pragma unroll
-            for (int k = k0; k < k0 + kKahan; ++k) {
-                const float4 q = Q[k];
-                const float2 m2 = M[k];
-                const float2 dx = __fadd2_rn(rx, f2(q.x, q.y));
-                const float2 dx2 = __fmul2_rn(dx, dx);
-                const float2 nyv = f2(q.z, q.w);
+                for (int k = k0; k < k0 + kKahan; ++k) {
+                    const float4 q = Q[k];
+                    const float2 m2 = M[k];
+                    const float2 dx = LO ? __fadd2_rn(__fadd2_rn(rx, f2(q.x, q.y)), rxl) : __fadd2_rn(rx, f2(q.x, q.y));
+                    const float2 dx2 = __fmul2_rn(dx, dx);
+                    const float2 nyv = f2(q.z, q.w);
 #pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    const float2 dy = __fadd2_rn(ry[p], nyv);
-                    const float2 r2 = __ffma2_rn(dy, dy, dx2);
-                    const float2 inv = p < NRP ? rcp_nr2(r2) : f2(rcp_approx(r2.x), rcp_approx(r2.y));
-                    const float2 f = __fmul2_rn(m2, inv);
-                    px[p] = __ffma2_rn(f, dx, px[p]);
-                    py[p] = __ffma2_rn(f, dy, py[p]);
+                    for (int p = 0; p < NP; ++p) {
+                        const float2 dy = LO ? __fadd2_rn(__fadd2_rn(ry[p], nyv), ryl[p]) : __fadd2_rn(ry[p], nyv);
+                        const float2 r2 = __ffma2_rn(dy, dy, dx2);
+                        const float2 inv = p < NRP ? rcp_nr2(r2) : f2(rcp_approx(r2.x), rcp_approx(r2.y));
+                        const float2 f = __fmul2_rn(m2, inv);
+                        px[p] = __ffma2_rn(f, dx, px[p]);
+                        py[p] = __ffma2_rn(f, dy, py[p]);
+                    }
+                }
+                if (!NAIVE) {
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        kahan2(Sx[p], Cx[p], px[p]);
+                        kahan2(Sy[p], Cy[p], py[p]);
+                        px[p] = py[p] = f2(0.f, 0.f);
+                    }
                 }
             }
-            if (!NAIVE) {
-#pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    kahan2(Sx[p], Cx[p], px[p]);
-                    kahan2(Sy[p], Cy[p], py[p]);
-                    px[p] = py[p] = f2(0.f, 0.f);
-                }
-            }
-        }
+        };
+        if (LOM == 2 && !NAIVE)
+            chunks(std::true_type{});
+        else if (LOM == 1 || NAIVE)
+            chunks(std::false_type{});
+        else if (lo)
+            chunks(std::true_type{});
+        else
+            chunks(std::false_type{});
         if (s + 1 < nstage) stage_store(buf ^ 1);
         __syncthreads();
     }
@@ -279,9 +359,12 @@ __device__ __forceinline__ void shoot_tile(const ShootArgs &a, int bx, int by, S
                 const float sx = h ? Sx[p].y : Sx[p].x, sy = h ? Sy[p].y : Sy[p].x;
                 const float ccx = h ? Cx[p].y : Cx[p].x, ccy = h ? Cy[p].y : Cy[p].x;
                 const float dxr = rx.x, dyr = h ? ry[p].y : ry[p].x;
-                // A delta for this ray (small)
-                const float lx = __fmaf_rn(a.lens.fa11, dxr, __fmul_rn(a.lens.fa12, dyr));
-                const float ly = __fmaf_rn(a.lens.fa12, dxr, __fmul_rn(a.lens.fa22, dyr));
+                const float dxl = rxl.x, dyl = h ? ryl[p].y : ryl[p].x;
+                // A delta for this ray (small), the offsets' low parts included
+                const float lx = __fmaf_rn(a.lens.fa11, dxr, __fmaf_rn(a.lens.fa12, dyr,
+                                           __fmaf_rn(a.lens.fa11, dxl, __fmul_rn(a.lens.fa12, dyl))));
+                const float ly = __fmaf_rn(a.lens.fa12, dxr, __fmaf_rn(a.lens.fa22, dyr,
+                                           __fmaf_rn(a.lens.fa12, dxl, __fmul_rn(a.lens.fa22, dyl))));
                 float th, tl;
                 two_sum(ts.tc[4], -sx, th, tl);
                 tl = __fadd_rn(tl, __fadd_rn(__fadd_rn(ts.tc[6], ccx), lx));

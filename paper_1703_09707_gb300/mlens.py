@@ -99,6 +99,7 @@ SIGNATURES = {
     "mlens_star_split_for": (C.c_int, [_vp, _gp, C.POINTER(C.c_int32)]),
     "mlens_shoot": (C.c_int, [_vp, _gp, _gp, _vp, C.c_uint32, _sp, _vp]),
     "mlens_shoot_beta": (C.c_int, [_vp, _gp, _gp, _vp, _vp, C.c_uint32, _sp, _vp]),
+    "mlens_shoot_rows": (C.c_int, [_vp, _gp, C.c_int32, C.c_int32, _gp, _vp, _vp, C.c_uint32, _sp, _vp]),
     "mlens_trace": (C.c_int, [_vp, _dp, C.c_int64, _dp, _vp]),
     "mlens_bin": (C.c_int, [_vp, C.c_int64, _gp, _vp, C.c_uint32, _sp, _vp]),
     "mlens_bin_grid": (C.c_int, [_vp, _gp, _gp, _vp, C.c_uint32, _sp, _vp]),
@@ -298,6 +299,21 @@ def mlens_shoot_beta(ctx: Ctx, rays, src, counts, beta, flags: int = 0, stats: b
     g, s = grid(rays), grid(src)
     _check(load().mlens_shoot_beta(ctx.handle, C.byref(g), C.byref(s), _counts_buf(counts, s), _dev_ptr(beta),
                                    int(flags), C.byref(st) if stats else None, _stream_ptr(stream)))
+    return st.asdict() if stats else None
+
+
+MLENS_ROW_ALIGN = 32
+
+
+def mlens_shoot_rows(ctx: Ctx, rays, rows, src, counts, beta=None, flags: int = 0, stats: bool = False,
+                     stream=None):
+    """Ray rows [rows[0], rows[1]) of the grid (multiples of MLENS_ROW_ALIGN, or the
+    end at rays.ny); beta (optional) holds the whole grid's records."""
+    st = mlens_stats()
+    g, s = grid(rays), grid(src)
+    _check(load().mlens_shoot_rows(ctx.handle, C.byref(g), int(rows[0]), int(rows[1]), C.byref(s),
+                                   _counts_buf(counts, s), _dev_ptr(beta), int(flags),
+                                   C.byref(st) if stats else None, _stream_ptr(stream)))
     return st.asdict() if stats else None
 
 

@@ -15,7 +15,8 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 import workloads as W  # noqa: E402
-from gpu_util import compare_to_oracle, make_ctx, shoot_gpu  # noqa: E402
+from gpu_util import (beta_pair_to_f64, compare_to_oracle, make_ctx, oracle_reference,  # noqa: E402
+                      position_rounding, shoot_gpu)
 from oracle import mlp  # noqa: E402
 from paper_1703_09707_gb300 import mlens as M  # noqa: E402
 
@@ -108,13 +109,14 @@ def _unflat_grad(g):
 
 @pytest.mark.parametrize("B", [128, 1000])
 def test_network_forward_and_backward_match_the_oracle(B):
-    """The GPU training kernel (BF16 tensor cores, FP32 accumulation) on explicit
-    inputs against the FP64 reference with the same BF16 rounding points.  Bound:
-    2e-3 relative (Frobenius) per gradient block and for the outputs, from one BF16
-    half-ulp (2^-9) of a rounded operand flipping where the GPU's and the FP64
-    pre-rounding values differ (FP32 arithmetic, and the hardware tanh of the
-    activations, relative error <= 2^-11); no output may be off by more than 1e-3
-    of the largest output."""
+    """The GPU training kernel (BF16 tensor cores, FP32 accumulation, hardware tanh)
+    on explicit inputs against the FP64 reference with the same BF16 rounding points,
+    element by element: every output, every parameter gradient and every latent
+    gradient within the bound of oracle/mlp.error_bounds (a worst-case running error
+    analysis of BF16 operands at those points, FP32 sums and a tanh within 2^-10.9,
+    exact where a BF16 rounding cannot flip).  The relative (Frobenius) errors per
+    block, and those against the network evaluated exactly in FP64 without BF16
+    rounding, are printed."""
     rng = np.random.default_rng(10 + B)
     p = mlp.init_params(rng)
     for k in p:
@@ -130,20 +132,26 @@ def test_network_forward_and_backward_match_the_oracle(B):
     g = torch.empty(flat.shape[0], dtype=torch.float32, device="cuda")
     dz = torch.empty((B, 32), dtype=torch.float32, device="cuda")
     loss = M.mlens_ff_eval(dev(flat), dev(z), dev(u), dev(t), y=y, grads=g, dz=dz)
-    lref, gref, yref = mlp.loss_and_grads(p32, z.astype(np.float64), u.astype(np.float64), t.astype(np.float64),
-                                          bf16=True)
+    z64, u64, t64 = z.astype(np.float64), u.astype(np.float64), t.astype(np.float64)
+    lref, gref, yref, bound = mlp.error_bounds(p32, z64, u64, t64)
+    got = _unflat_grad(g.cpu().numpy().astype(np.float64))
+    got["z"] = dz.cpu().numpy().astype(np.float64)
     yg = y.cpu().numpy().astype(np.float64)
-    assert np.linalg.norm(yg - yref) <= 2e-3 * np.linalg.norm(yref)
-    assert np.max(np.abs(yg - yref)) <= 1e-3 * np.max(np.abs(yref))
-    assert abs(loss - lref) <= 2e-3 * abs(lref)
-    gg = _unflat_grad(g.cpu().numpy().astype(np.float64))
+    assert abs(loss - lref) <= bound["loss"], (loss, lref, bound["loss"])
+    over = np.abs(yg - yref) / bound["y"]
+    assert over.max() <= 1.0, ("y", float(over.max()), np.unravel_index(over.argmax(), over.shape))
     for k in gref:
-        if k == "z":
-            continue
-        err = np.linalg.norm(gg[k] - gref[k]) / max(np.linalg.norm(gref[k]), 1e-30)
-        assert err < 2e-3, (k, err)
-    err = np.linalg.norm(dz.cpu().numpy() - gref["z"]) / np.linalg.norm(gref["z"])
-    assert err < 2e-3, ("z", err)
+        over = np.abs(got[k] - gref[k]) / np.maximum(bound[k], 1e-300)
+        assert over.max() <= 1.0, (k, float(over.max()), np.unravel_index(over.argmax(), over.shape))
+    # reported: block errors against this reference and against the exact FP64 network
+    _, gex, yex = mlp.loss_and_grads(p32, z64, u64, t64, bf16=False)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))  # noqa: E731
+    rep = {k: (rel(got[k], gref[k]), rel(got[k], gex[k])) for k in gref}
+    rep["y"] = (rel(yg, yref), rel(yg, yex))
+    print("network block errors (vs BF16-point reference, vs exact FP64):",
+          {k: (f"{a:.1e}", f"{b:.1e}") for k, (a, b) in rep.items()})
+    for k, (a, _) in rep.items():
+        assert a < 2e-3, (k, a)
 
 
 def test_series_only_far_field_matches_the_plain_path(field):
@@ -228,37 +236,77 @@ def test_row_restricted_calls_add_up_to_the_full_map(field):
     ctx.close()
 
 
+LEARNED_STRIPS = ((0, 768), (10752, 11520), (16128, 16896), (32000, 32768))
+
+
+def near_scale(f, th, radius):
+    """sum_k m_k / |theta - theta_k| over the stars within `radius` of each theta."""
+    from scipy.spatial import cKDTree
+    tree = cKDTree(f.xy)
+    out = np.zeros(th.shape[0])
+    for i, ks in enumerate(tree.query_ball_point(th, radius)):
+        if ks:
+            d = np.linalg.norm(f.xy[ks] - th[i], axis=1)
+            out[i] = np.sum(f.m[ks] / d)
+    return out
+
+
 def test_learned_full_size_workload_against_the_oracle():
     """The bench's learned workload itself (1e6 stars, 32768^2 rays, 4096^2 map, the
-    default fit): beta of a 768-row strip from the learned kernel, 2e4 sampled rays
-    against the FP64 oracle (misbinning and the deflection bound), and the strip map
-    against the plain kernel's (relative L1 <= 1e-3)."""
+    default fit) on four strips of 768 ray rows: the first and last rows of the grid
+    (the cells next to the extra ring) and two interior strips.  Per strip: the map
+    against the plain kernel's map of the same rays (relative L1 <= 1e-3), and 2e4
+    sampled rays against the FP64 oracle: misbinned fraction <= 1e-4 and every ray's
+    deflection error within
+        2 tol + 1e-5 (|alpha_0| + sum_near m/r) + ||d alpha/d theta|| sqrt(2) eps_pos,
+    tol the fit's validation bound on the far field (2 tol: the bound is validated on
+    held-out samples, not at every position), the second term the plain path's 1e-5
+    error bar applied to the exactly summed near stars (those within 2 sqrt(2) cell
+    widths: a superset of the 3x3 block), the third its position rounding."""
     wl = W.config("learned")
     f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
+    tol = 5e-6
     ctx = make_ctx(f)
-    rep = M.mlens_fit_far_field(ctx, rays, M.fit_params(cells_x=256, tolerance=5e-6))
+    rep = M.mlens_fit_far_field(ctx, rays, M.fit_params(cells_x=256, tolerance=tol))
     assert rep["cells"] == 256 * 86
-    j0, j1 = 16128, 16896
-    beta = torch.empty((rays.n, 4), dtype=torch.float32, device="cuda")  # rows outside the strip stay unset
-    cl = torch.empty(src.n, dtype=torch.int32, device="cuda")
-    st = M.mlens_shoot_learned(ctx, rays, src, cl, beta=beta, rows=(j0, j1), stats=True)
-    torch.cuda.synchronize()
-    assert st["rays_total"] == rays.nx * (j1 - j0)
+    info = M.mlens_far_field_export(ctx)["info"]
+    beta = torch.empty((rays.n, 4), dtype=torch.float32, device="cuda")  # rows outside the strips stay unset
     rng = np.random.default_rng(5)
-    idx = np.sort(rng.choice(rays.nx * (j1 - j0), 20000, replace=False)) + j0 * rays.nx
-    b4 = beta.index_select(0, torch.from_numpy(idx).cuda()).cpu().numpy()
-    e = compare_to_oracle(f, rays, src, b4, idx, presampled=True)
-    print("learned full size", e)
-    assert e["misbinned_frac"] <= 1e-4, e
-    dy = (rays.y1 - rays.y0) / rays.ny
-    strip = W.Grid(rays.x0, rays.x1, rays.y0 + j0 * dy, rays.y0 + j1 * dy, rays.nx, j1 - j0)
-    cp = torch.empty(src.n, dtype=torch.int32, device="cuda")
-    M.mlens_shoot(ctx, strip, src, cp)
-    torch.cuda.synchronize()
-    a = cl.cpu().numpy().view(np.uint32).astype(np.int64)
-    b = cp.cpu().numpy().view(np.uint32).astype(np.int64)
-    l1 = np.abs(a - b).sum() / b.sum()
-    assert l1 <= 1e-3, l1
+    l1_num = l1_den = 0
+    worst = {}
+    for j0, j1 in LEARNED_STRIPS:
+        cl = torch.empty(src.n, dtype=torch.int32, device="cuda")
+        st = M.mlens_shoot_learned(ctx, rays, src, cl, beta=beta, rows=(j0, j1), stats=True)
+        cp = torch.empty(src.n, dtype=torch.int32, device="cuda")
+        stp = M.mlens_shoot_rows(ctx, rays, (j0, j1), src, cp, stats=True)
+        torch.cuda.synchronize()
+        assert st["rays_total"] == stp["rays_total"] == rays.nx * (j1 - j0)
+        a = cl.cpu().numpy().view(np.uint32).astype(np.int64)
+        b = cp.cpu().numpy().view(np.uint32).astype(np.int64)
+        l1 = np.abs(a - b).sum() / b.sum()
+        l1_num += np.abs(a - b).sum()
+        l1_den += b.sum()
+        idx = np.sort(rng.choice(rays.nx * (j1 - j0), 20000, replace=False)) + j0 * rays.nx
+        b4 = beta.index_select(0, torch.from_numpy(idx).cuda()).cpu().numpy()
+        ref = oracle_reference(f, rays, idx)
+        e = compare_to_oracle(f, rays, src, b4, idx, presampled=True, ref=ref)
+        th = ref["th"]
+        dal = np.linalg.norm((th - beta_pair_to_f64(b4)) - (th - ref["b64"]), axis=1)
+        ac = np.abs(np.array([[f.kappa_c + f.gamma1, f.gamma2], [f.gamma2, f.kappa_c - f.gamma1]]))
+        a0 = np.linalg.norm(th @ ac.T, axis=1)
+        J = ref["J"]
+        jn = np.sqrt(J[:, 0] ** 2 + 2 * J[:, 1] ** 2 + J[:, 2] ** 2)
+        allow = 2 * tol + 1e-5 * (a0 + near_scale(f, th, 2 * np.sqrt(2) * info.cell_width)) + \
+            jn * np.sqrt(2.0) * position_rounding(rays)
+        ratio = float(np.max(dal / allow))
+        print(f"learned strip [{j0},{j1}): L1 {l1:.2e}, misbinned {e['misbinned_frac']:.1e}, "
+              f"|d alpha| mean {dal.mean():.2e} max {dal.max():.2e} theta_E, "
+              f"|d beta| mean {e['dbeta_mean_px']:.2e} max {e['dbeta_max_px']:.2e} px, bound ratio {ratio:.3f}")
+        assert l1 <= 1e-3, (j0, l1)
+        assert e["misbinned_frac"] <= 1e-4, (j0, e)
+        assert ratio <= 1.0, (j0, ratio)
+        worst[j0] = ratio
+    assert l1_num / l1_den <= 1e-3
     ctx.close()
 
 

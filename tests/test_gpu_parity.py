@@ -4,13 +4,15 @@ Criteria (spec bar):
   - bit-exact: the GPU map equals a CPU re-binning of the GPU's own beta with the
     float32 pair rule, and the GPU's ray bookkeeping equals the re-binning's;
   - misbinned fraction (GPU pixel != oracle FP64 pixel) <= 1e-4;
-  - per-ray deflection error within 1e-5 relative: |alpha_gpu - alpha_64| <=
+  - per-ray relative deflection error |alpha_gpu - alpha_64| / |alpha_64| <= 1e-5
+    over the rays with |alpha_64| >= 1e-3 median |alpha_64| (rel_max);
+  - per-ray deflection error within its 1e-5 error bound: |alpha_gpu - alpha_64| <=
     1e-5 (|alpha_0| + sum_k m_k/r_k) + ||d alpha/d theta|| sqrt(2) eps_pos, where
     the first term is a 1e-5 relative error of the summed terms (where alpha itself
     nearly cancels no float32 evaluation can be small relative to |alpha|) and the
     second the unavoidable effect of holding ray and star offsets from the tile
     centre in float32 (eps_pos = 2^-22 tile extent; it matters only within ~1e-3
-    of a star).  The plain |dalpha|/|alpha| is reported as quantiles;
+    of a star);
   - the FP64 variant equals the oracle bit for bit (beta and map).
 """
 import math
@@ -59,6 +61,10 @@ def test_tiny_fp32_full_parity(scale):
     print("tiny", scale, e)
     assert e["misbinned_frac"] <= MISBIN_MAX, e
     assert e["bound_ratio"] <= 1.0, e
+    # kappa_c = gamma = 0: the star terms cancel near the disk centre, so the relative
+    # bar is asserted where alpha keeps 1e-2 of its terms' magnitude (every ray stays
+    # within the term-scale bound above)
+    assert e["rel_max_conditioned"] <= REL_MAX, e
     c64, st64 = oracle.shoot(rays, src, f)
     assert st["rays_total"] == st64["rays_total"]
 
@@ -74,6 +80,7 @@ def test_paper_shaped_reduced_grid_parity():
     print("paper 1024^2", e)
     assert e["misbinned_frac"] <= MISBIN_MAX, e
     assert e["bound_ratio"] <= 1.0, e
+    assert e["rel_max"] <= REL_MAX, e
 
 
 def test_paper_full_size_bench_configuration():
@@ -90,6 +97,7 @@ def test_paper_full_size_bench_configuration():
     print("paper full", e)
     assert e["misbinned_frac"] <= MISBIN_MAX, e
     assert e["bound_ratio"] <= 1.0, e
+    assert e["rel_max"] <= REL_MAX, e
 
 
 def test_fp64_equals_oracle_bit_for_bit():
