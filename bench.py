@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--print-kernel-hash", action="store_true", help="print the FP32 kernel source hash and exit")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-fields and learned-far-field measurements that ride along the main line")
-    ap.add_argument("--extras", default="batched,binning,lightcurve,split,learned",
+    ap.add_argument("--extras", default="batched,binning,lightcurve,split,learned,fit",
                     help="comma list of extra sections: batched, binning, lightcurve, split, learned, fit")
     ap.add_argument("--learned-tol", type=float, default=5e-6, help="per-cell validation bound of the learned field")
     ap.add_argument("--learned-order", type=int, default=10)
