@@ -424,9 +424,9 @@ typedef struct {
     int32_t target_order;         /* order of the far-field expansion the network learns up to, order < . <= 24 (24) */
     int32_t use_network;          /* 1: learn the remainder (default); 0: series only */
     int64_t train_samples;        /* distinct training samples (2^24) */
-    int32_t epochs;               /* passes over them (64) */
-    int32_t batch;                /* samples per optimiser step, >= 128 (65536) */
-    float lr_weights, lr_latents; /* Adam learning rates, cosine-decayed to 5 % (3e-3, 5e-2) */
+    int32_t epochs;               /* passes over them (48) */
+    int32_t batch;                /* samples per optimiser step, >= 128 (77824) */
+    float lr_weights, lr_latents; /* Adam learning rates, cosine-decayed to 5 % (3.9e-3, 6.5e-2) */
     int32_t val_samples_per_cell; /* held-out samples per cell for validation (64) */
     double tolerance;             /* max validation error allowed per cell, theta_E (1e-6) */
     uint64_t seed;                /* seed of the counter-based sample and weight generators */

@@ -186,7 +186,8 @@ def test_trained_network_reduces_the_far_field_error(field):
     """Order-6 series + network (trained on the GPU) against order-6 series alone, on
     held-out samples; then the map of the learned path against the plain map."""
     ctx = make_ctx(field)
-    prm = M.fit_params(cells_x=CELLS_X, use_network=1, order=6, train_samples=1 << 20, epochs=128, tolerance=1e-6)
+    prm = M.fit_params(cells_x=CELLS_X, use_network=1, order=6, train_samples=1 << 20, epochs=128, tolerance=1e-6,
+                       batch=65536)
     rep = M.mlens_fit_far_field(ctx, RAYS, prm)
     print("fit", rep)
     assert rep["train_steps"] == 128 * 16
