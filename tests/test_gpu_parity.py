@@ -188,6 +188,31 @@ def test_ray_exactly_on_a_star_is_nan():
         assert c.sum() == 0
 
 
+def test_ray_on_a_star_leaves_its_neighbours_exact():
+    """One ray of a 4 x 4 grid sits exactly on a star; the rays around it, among them
+    the one that shares its reciprocal in the FP32 kernel (the next row of the same
+    column), must come out as if the star were anywhere else: every other beta equals
+    the oracle's within the error bound, and the bookkeeping counts one NaN ray."""
+    f = W.Field(xy=np.array([[0.375, 0.375], [3.0, 1.0], [-0.6, 0.7]]), m=np.array([1.0, 0.5, 0.3]),
+                kappa_c=0.1, gamma1=0.05, gamma2=0.0)
+    rays = W.Grid(0.0, 1.0, 0.0, 1.0, 4, 4)  # cell centres 0.125, 0.375, ...: ray (1, 1) is on the first star
+    src = W.Grid(-8.0, 8.0, -8.0, 8.0, 64, 64)
+    for prec in (M.MLENS_PREC_FP32, M.MLENS_PREC_FP32_NAIVE, M.MLENS_PREC_FP64):
+        c, st, b = shoot_gpu(f, rays, src, prec=prec)
+        assert st["rays_nan"] == 1 and st["rays_binned"] + st["rays_out"] == 15, (prec, st)
+        b64 = oracle.beta_rays(rays, np.arange(16, dtype=np.int64), f)
+        on = 1 * 4 + 1
+        bg = b if prec == M.MLENS_PREC_FP64 else b[:, :2].astype(np.float64) + b[:, 2:].astype(np.float64)
+        assert not np.all(np.isfinite(bg[on]))
+        keep = np.arange(16) != on
+        assert np.all(np.isfinite(bg[keep])), prec
+        assert np.max(np.abs(bg[keep] - b64[keep])) < 1e-4, (prec, np.max(np.abs(bg[keep] - b64[keep])))
+        if prec == M.MLENS_PREC_FP32:
+            assert_rebin_exact(c, st, b, src)
+            e = compare_to_oracle(f, rays, src, b[keep], np.nonzero(keep)[0].astype(np.int64), presampled=True)
+            assert e["bound_ratio"] <= 1.0 and e["misbinned"] == 0, e
+
+
 def test_accumulate_and_determinism():
     wl = W.config("paper", rays_scale=1 / 16)
     f, rays, src = wl.fields[0], wl.rays[0], wl.srcs[0]
