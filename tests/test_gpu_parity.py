@@ -190,9 +190,10 @@ def test_ray_exactly_on_a_star_is_nan():
 
 def test_ray_on_a_star_leaves_its_neighbours_exact():
     """One ray of a 4 x 4 grid sits exactly on a star; the rays around it, among them
-    the one that shares its reciprocal in the FP32 kernel (the next row of the same
-    column), must come out as if the star were anywhere else: every other beta equals
-    the oracle's within the error bound, and the bookkeeping counts one NaN ray."""
+    the one processed in the same packed pair of the FP32 kernel (the next row of the
+    same column), must come out as if the star were anywhere else: every other beta
+    equals the oracle's within the error bound, and the bookkeeping counts one NaN
+    ray."""
     f = W.Field(xy=np.array([[0.375, 0.375], [3.0, 1.0], [-0.6, 0.7]]), m=np.array([1.0, 0.5, 0.3]),
                 kappa_c=0.1, gamma1=0.05, gamma2=0.0)
     rays = W.Grid(0.0, 1.0, 0.0, 1.0, 4, 4)  # cell centres 0.125, 0.375, ...: ray (1, 1) is on the first star
