@@ -72,6 +72,8 @@ def parse():
                     help="comma list of extra sections: batched, binning, lightcurve, split, learned, fit")
     ap.add_argument("--learned-tol", type=float, default=5e-6, help="per-cell validation bound of the learned field")
     ap.add_argument("--learned-order", type=int, default=10)
+    ap.add_argument("--learned-errors", type=int, default=1, choices=[0, 1],
+                    help="state the learned variants' per-ray errors against FP64 (0: skip, no 17 GB beta buffer)")
     ap.add_argument("--fit-stars", type=int, default=1_000_000,
                     help="stars of the field the fit section fits (same density and cell grid as the learned one)")
     ap.add_argument("--scaling", default="strong", choices=["strong", "weak"],
@@ -449,7 +451,7 @@ def _errors_vs_fp64(b4, b64, src):
             "dalpha_max_theta_e": float(d[fin].max()), "misbinned_frac": float(np.mean(pg != p6))}
 
 
-def bench_learned(M, torch, steps: int, flush, tol: float, order: int):
+def bench_learned(M, torch, steps: int, flush, tol: float, order: int, errors: bool = True):
     """10^6 stars, 32768^2 rays, 4096^2 map: the learned far field (fit on the GPU,
     then one persistent launch per map) against the plain direct sum.  The plain
     map of the whole grid takes minutes, so both paths are compared on four strips of
@@ -483,19 +485,21 @@ def bench_learned(M, torch, steps: int, flush, tol: float, order: int):
     rng = np.random.default_rng(11)
     idx = np.concatenate([np.sort(rng.choice(rays.nx * (j1 - j0), 5000, replace=False)) + j0 * rays.nx
                           for j0, j1 in LEARNED_STRIPS]).astype(np.int64)
-    b64 = M.mlens_trace(ctx, _grid_theta(rays, idx))
+    b64 = M.mlens_trace(ctx, _grid_theta(rays, idx)) if errors else None
     idx_t = torch.from_numpy(idx).cuda()
-    beta = torch.empty((rays.n, 4), dtype=torch.float32, device="cuda")  # only the strips' rows are written
+    # only the strips' rows are written
+    beta = torch.empty((rays.n, 4), dtype=torch.float32, device="cuda") if errors else None
     out = {"workload": f"learned: {f.n} stars, {rays.nx}^2 rays, {src.nx}^2 map, 256 x 86 cells of 0.46875 theta_E",
            "plain": {"interactions_per_s": plain_rate, "map_s_estimated": plain_full_s,
                      "measured_on": f"ray rows {list(LEARNED_STRIPS)} ({strip_rays} rays)"},
            "errors_reference": "FP64 kernel (mlens_trace; bit-identical to the FP64 oracle) on 2e4 rays "
                                "sampled from the strips"}
     # the plain path's own error on the same rays, for comparison
-    cpb = torch.empty(src.n, dtype=torch.int32, device="cuda")
-    for j0, j1 in LEARNED_STRIPS:
-        M.mlens_shoot_rows(ctx, rays, (j0, j1), src, cpb, beta=beta)
-    out["plain"]["errors_vs_fp64"] = _errors_vs_fp64(beta.index_select(0, idx_t).cpu().numpy(), b64, src)
+    if errors:
+        cpb = torch.empty(src.n, dtype=torch.int32, device="cuda")
+        for j0, j1 in LEARNED_STRIPS:
+            M.mlens_shoot_rows(ctx, rays, (j0, j1), src, cpb, beta=beta)
+        out["plain"]["errors_vs_fp64"] = _errors_vs_fp64(beta.index_select(0, idx_t).cpu().numpy(), b64, src)
     # the learned path, the same series without the network (the ablation), and the
     # exact series alone at higher orders
     variants = [("with_network", 1, order), ("series_only", 0, order)]
@@ -518,7 +522,7 @@ def bench_learned(M, torch, steps: int, flush, tol: float, order: int):
             cl_h = cl.cpu().numpy().view(np.uint32).astype(np.int64)
             num += np.abs(cl_h - cp_h).sum()
             den += cp_h.sum()
-        errs = _errors_vs_fp64(beta.index_select(0, idx_t).cpu().numpy(), b64, src)
+        errs = _errors_vs_fp64(beta.index_select(0, idx_t).cpu().numpy(), b64, src) if errors else None
         # whole map timed unless its fallback tiles alone would take minutes (then the
         # strips' time is scaled to the grid)
         fallback_s = rep["tiles_fallback"] * 2048 * f.n / plain_rate
@@ -545,7 +549,7 @@ def bench_learned(M, torch, steps: int, flush, tol: float, order: int):
             "effective_interactions_per_s": rays.n * f.n / learned_s,
             "speedup_vs_plain": plain_full_s / learned_s,
             "map_rel_l1_vs_plain": l1, "equal_error": l1 <= 1e-3,
-            "errors_vs_fp64": errs,
+            **({"errors_vs_fp64": errs} if errors else {}),
             "fallback_cells": rep["cells_fallback"], "cells": rep["cells"],
             "fallback_tiles": rep["tiles_fallback"], "tiles": rep["tiles"],
             "val_mean_err": rep["val_mean_err_net"] if use_net else rep["val_mean_err_series"],
@@ -802,7 +806,7 @@ def run_mine(args):
             line["split"] = bench_split(M, torch, flush, peak)
         if "learned" in extras:
             line["learned"] = bench_learned(M, torch, max(2, min(args.steps, 3)), flush, args.learned_tol,
-                                            args.learned_order)
+                                            args.learned_order, bool(args.learned_errors))
         if "fit" in extras:
             line["fit"] = bench_fit(M, torch, args.fit_stars, args.learned_tol, args.learned_order,
                                     n_sm * 128 * SM_MAX_MHZ * 1e6)
