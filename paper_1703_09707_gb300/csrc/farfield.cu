@@ -212,9 +212,11 @@ __device__ __forceinline__ float warp_scatter_orders(float (&v)[kPtMax])
     return c[0];
 }
 
-// Three CTAs per SM (80 registers; the spills of the partials cost less than the
-// latency the third CTA hides: 0.66 -> 0.61 s for 22016 cells x 1e6 stars).
-__global__ void __launch_bounds__(256, 3) k_coeffs(const float4 *stars, const int *scell, int64_t n, CellGrid g, int pt,
+// Two CTAs per SM.  While the stage sums were accumulated in FP64 a third CTA (80
+// registers, with spills) hid more latency than the spills cost; with the FP32-pipe
+// accumulation the kernel is bound by the FMA pipe and two CTAs without spills are
+// faster (0.245 -> 0.232 s for 22016 cells x 1e6 stars).
+__global__ void __launch_bounds__(256, 2) k_coeffs(const float4 *stars, const int *scell, int64_t n, CellGrid g, int pt,
                                                 double scale, double *out)
 {
     // One warp per ray cell.  Per far star: the order-0 term -m / (z_k - z_c) in
