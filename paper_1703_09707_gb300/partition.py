@@ -63,6 +63,26 @@ def allreduce_stats(st: dict, device=None, group=None) -> dict:
     return {k: int(v) for k, v in zip(keys, t.tolist())}
 
 
+def shoot_learned_partitioned(ctx, rays, src, counts, group=None, stats: bool = False, stream=None):
+    """As shoot_partitioned, with the learned far field fitted on `ctx` (every rank
+    fits the same field with the same parameters, or loads the same saved fit):
+    this rank's band through mlens_shoot_learned, then the sum over the group.  The
+    learned kernel's row restriction keeps whole 32-row tiles, so the bands add up to
+    the one-process learned map bit for bit."""
+    rank, world = _group_rank_world(group)
+    g = M.grid(rays)
+    r0, r1 = row_bands(int(g.ny), world)[rank]
+    if r1 > r0:
+        st = M.mlens_shoot_learned(ctx, rays, src, counts, rows=(r0, r1), stats=stats, stream=stream)
+    else:
+        counts.zero_()
+        st = dict(rays_total=0, rays_binned=0, rays_out=0, rays_nan=0)
+    allreduce_counts(counts, group)
+    if stats:
+        return allreduce_stats(st, device=counts.device, group=group)
+    return None
+
+
 def shoot_partitioned(ctx, rays, src, counts, group=None, stats: bool = False, stream=None):
     """This rank's band of the grid into `counts` (overwritten), then the sum over the
     group: afterwards every rank holds the whole map.  Returns the summed stats when

@@ -98,3 +98,34 @@ def test_rows_are_checked():
         assert ei.value.code == M.MLENS_ERR_ARG, rows
     M.mlens_shoot_rows(ctx, rays, (320, 333), src, c)  # the ragged end is allowed
     ctx.close()
+
+
+def test_learned_bands_add_up_to_the_whole_learned_map():
+    """The learned far field's map split into bands of ray rows (one per rank of a
+    partitioned run) sums to the one-process learned map bit for bit, fallback
+    cells included."""
+    f = W.random_field(W.SEED_BASE + 40, 20000, 0.45, 0.05, 0.25, 0.0)
+    rays = W.Grid(-7.5, 7.5, -2.5, 2.5, 2048, 2048)
+    src = W.Grid(-2.0, 2.0, -2.0, 2.0, 512, 512)
+    ctx = make_ctx(f)
+    # order 6 with a strict tolerance: some cells fall back to the plain sum
+    rep = M.mlens_fit_far_field(ctx, rays, M.fit_params(cells_x=32, use_network=1, order=6, train_samples=1 << 18,
+                                                        epochs=8, tolerance=2e-7))
+    assert rep["cells_fallback"] > 0, rep
+    full = torch.empty(src.n, dtype=torch.int32, device="cuda")
+    st_full = M.mlens_shoot_learned(ctx, rays, src, full, stats=True)
+    acc = torch.zeros(src.n, dtype=torch.int32, device="cuda")
+    tot = dict(rays_total=0, rays_binned=0, rays_out=0, rays_nan=0)
+    for r0, r1 in P.row_bands(rays.ny, 3):
+        part = torch.empty(src.n, dtype=torch.int32, device="cuda")
+        st = M.mlens_shoot_learned(ctx, rays, src, part, rows=(r0, r1), stats=True)
+        for k in tot:
+            tot[k] += st[k]
+        acc += part
+    torch.cuda.synchronize()
+    assert torch.equal(acc, full) and tot == st_full
+    got = torch.empty(src.n, dtype=torch.int32, device="cuda")
+    st = P.shoot_learned_partitioned(ctx, rays, src, got, stats=True)  # one process: the whole map
+    torch.cuda.synchronize()
+    assert torch.equal(got, full) and st == st_full
+    ctx.close()
