@@ -404,7 +404,9 @@ __device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol
 // ===================================================== training kernel
 constexpr int kWaitPolls = 1 << 20;  // bound on a tensor-core completion wait
 constexpr int kProbePolls = 1024;    // bound on a probe wait (an mbarrier nothing arrives on)
-constexpr int kSampC = 128;          // samples per CTA = tensor-memory lanes of one accumulator
+constexpr int kSampC = 128;          // samples per chunk = tensor-memory lanes of one accumulator
+constexpr int kChunks = 2;           // chunks per CTA, one after the other
+constexpr int kSampCTA = kChunks * kSampC;
 constexpr int kGP = kParams + 2;     // gpart row: the parameters' gradients, then the loss
 
 // Shared memory of the training kernel (byte offsets).  Every tensor-core
@@ -437,20 +439,26 @@ struct TrainTc {
     static constexpr int b2 = b1 + kHid * 4;
     static constexpr int W3 = b2 + kHid * 4;             // [2][64]
     static constexpr int b3 = W3 + 2 * kHid * 4;         // [2], padded
-    static constexpr int U = b3 + 16;                    // [128][2] positions
-    static constexpr int T = U + 2 * kSampC * 4;         // [128][2] targets
-    static constexpr int SV = T + 2 * kSampC * 4;        // [128] s_c |v|^(pe+1)
-    static constexpr int RC = SV + kSampC * 4;           // [128] int cell
-    static constexpr int OK = RC + kSampC * 4;           // [128] int valid
-    static constexpr int YP = OK + kSampC * 4;           // [2 warpgroups][128][2] layer-3 partial sums
+    // the CTA's samples, both chunks (sample i of chunk c at index c * 128 + i)
+    static constexpr int U = b3 + 16;                    // [256][2] positions
+    static constexpr int T = U + 2 * kSampCTA * 4;       // [256][2] targets
+    static constexpr int SV = T + 2 * kSampCTA * 4;      // [256] s_c |v|^(pe+1)
+    static constexpr int RC = SV + kSampCTA * 4;         // [256] int cell
+    static constexpr int OK = RC + kSampCTA * 4;         // [256] int valid
+    static constexpr int YP = OK + kSampCTA * 4;         // [2 warpgroups][128][2] layer-3 partial sums
     static constexpr int Slots = YP + 2 * kSampC * 2 * 4;  // [8 warps][6][32] column sums over a warp's samples
     static constexpr int WS = Slots + 8 * 6 * 32 * 4;    // [8 warps][4]: sum dy0, sum dy1, loss
     static constexpr int bytes = WS + 8 * 4 * 4;
-    // tensor-memory columns (all 128 lanes), reused once read: H1 and H2 first; dA1
-    // over H2 once the dh2 pass has read it; dW2 over H1, dZ and dW1z over dA1 once
-    // the dh1 pass has read both
-    static constexpr int cH1 = 0, cH2 = 64, cDA1 = 64, cDW2 = 0, cDZ = 64, cDW1z = 96, ncols = 128;
+    // tensor-memory columns (all 128 lanes).  A chunk's own accumulators are reused
+    // once read: H1 and H2 first; dA1 over H2 once the dh2 pass has read it; dZ over
+    // dA1 once the dh1 pass has read it.  dW2 and dW1z have columns of their own:
+    // both chunks accumulate into them.
+    static constexpr int cH1 = 0, cH2 = 64, cDA1 = 64, cDZ = 64, cDW2 = 128, cDW1z = 192, ncols = 256;
 };
+// two CTAs per SM: their dynamic and static shared memory within the SM's 228 KB
+// less 1 KB per CTA, and their tensor memory within the SM's 512 columns
+static_assert(TrainTc::bytes + 128 <= (228 * 1024) / 2 - 1024, "two training CTAs per SM");
+static_assert(2 * TrainTc::ncols <= 512, "two training CTAs per SM");
 
 // The training kernel's weight operands as they sit in its shared memory (W1z, W2,
 // W2T, W1zT at their TrainTc offsets): written wherever the BF16 weight copies are
@@ -602,24 +610,52 @@ __device__ __forceinline__ void st_f4x4(float *dst, const float (&v)[16])  // 16
         reinterpret_cast<float4 *>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 
-// One thread issues D = sum_k A[:, k] B[:, k]^T over K / 16 MMAs of K = 16.
+// One thread issues D = sum_k A[:, k] B[:, k]^T over K / 16 MMAs of K = 16 (acc:
+// D += instead).
 __device__ __forceinline__ void tc_gemm(uint32_t d, const unsigned char *A, const unsigned char *B, int K,
-                                        uint32_t idesc)
+                                        uint32_t idesc, bool acc = false)
 {
     const uint32_t a = umma::smem_addr(A), b = umma::smem_addr(B), sbo = (uint32_t)(K * 16);
     for (int ks = 0; ks < K / 16; ++ks)
         umma::mma_bf16(d, umma::desc(a + ks * 256, 128, sbo), umma::desc(b + ks * 256, 128, sbo), idesc,
-                       ks > 0 ? 1u : 0u);
+                       acc || ks > 0 ? 1u : 0u);
 }
 
-// The step for the CTA's 128 samples; false if a tensor-core wait gave up (the
-// caller drains and reports).  Thread (warpgroup wg, s = tid % 128) owns sample s
-// and, of each 64-wide accumulator, the columns 32 wg .. 32 wg + 31, taken in two
-// halves of 16 (tensor-memory lane s is readable by warp s / 32 of either
-// warpgroup).  H1 and H2 are read back from tensor memory when the backward pass
-// needs them rather than held in registers: two CTAs fit per SM.
+// 16 latent columns (16 wg .. 16 wg + 15) of sample li of the launch, zero past its
+// end: explicit latents, or those of the sample's cell (offset + li) mod nrc.
+__device__ __forceinline__ void load_latents(const TrainArgs &A, int64_t li, int wg, float (&zv)[16])
+{
+    const bool ok = li < A.spec.count;
+    const float *src = A.zin ? A.zin + li * kLat : A.z + ((A.spec.offset + li) % A.spec.nrc) * kLat;
+    src += 16 * wg;
+    if (!ok) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) zv[j] = 0.0f;
+    } else if (((uintptr_t)src & 7u) == 0) {  // the latents (after the 6530 parameters) are 8-byte aligned
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float2 v = reinterpret_cast<const float2 *>(src)[j];
+            zv[2 * j] = v.x;
+            zv[2 * j + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) zv[j] = src[j];
+    }
+}
+
+// The step for chunk `chunk` of the CTA's samples (128 of them); false if a
+// tensor-core wait gave up (the caller drains and reports).  Thread (warpgroup wg,
+// s = tid % 128) owns sample s and, of each 64-wide accumulator, the columns
+// 32 wg .. 32 wg + 31, taken in two halves of 16 (tensor-memory lane s is readable
+// by warp s / 32 of either warpgroup).  H1 and H2 are read back from tensor memory
+// when the backward pass needs them rather than held in registers: two CTAs fit
+// per SM.  zv holds the chunk's latents on entry and, after a backward chunk
+// followed by another, the next chunk's (loaded while the last MMAs run).  The
+// weight gradients and FP32 column sums accumulate over the chunks; the last one
+// writes the CTA's gradient row.
 __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S, uint64_t *bar, uint64_t *idle,
-                                           uint32_t tm, uint32_t &phase, const float (&zv)[16])
+                                           uint32_t tm, uint32_t &phase, float (&zv)[16], int chunk)
 {
     using L = TrainTc;
     float *F = reinterpret_cast<float *>(S);  // byte offsets / 4 below
@@ -627,10 +663,13 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, wg = warp >> 2, s = tid & 127;
     const int c0 = 32 * wg;  // this thread's first column of a 64-wide accumulator
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-    const int64_t cbase = (int64_t)blockIdx.x * kSampC;
-    const bool expl = A.zin != nullptr;
+    const int64_t cbase = (int64_t)blockIdx.x * kSampCTA + chunk * kSampC;
+    const int si = chunk * kSampC + s;  // the sample's index in the CTA's sample regions
+    const bool expl = A.zin != nullptr, first = chunk == 0, last = chunk == kChunks - 1;
     float *Slot = F + L::Slots / 4 + warp * 6 * 32;
-    const float ux = F[L::U / 4 + 2 * s], uy = F[L::U / 4 + 2 * s + 1];
+    // this warp's column sums so far plus r (the first chunk starts them)
+    auto slot_add = [&](int i, float r) { Slot[i] = first ? r : Slot[i] + r; };
+    const float ux = F[L::U / 4 + 2 * si], uy = F[L::U / 4 + 2 * si + 1];
     // pre-activations of layer 1 / layer 2 for columns c .. c + 15, from tensor memory
     auto load_h1 = [&](int c, float (&h)[16]) {
         tc_load16(tm + lane_base + L::cH1 + c, h);
@@ -660,7 +699,7 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
         tc_gemm(tm + L::cH1, S + L::Z, S + L::W1z, kLat, umma::idesc_bf16(128, kHid));
         umma::commit(bar);
     }
-    if (!tc_wait(bar, phase, A.wait_probe ? idle : nullptr)) return false;
+    if (!tc_wait(bar, phase, A.wait_probe && first ? idle : nullptr)) return false;
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh) {  // A1 = silu(H1 + W1u u + b1) over the Z region (its MMAs are done)
         const int c = c0 + 16 * hh;
@@ -704,10 +743,10 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
     }
     __syncthreads();
     // ---- outputs, loss, validation (both warpgroups form the same y and dy)
-    const bool valid = I[L::OK / 4 + s] != 0;
+    const bool valid = I[L::OK / 4 + si] != 0;
     const float yv0 = F[L::YP / 4 + 2 * s] + F[L::YP / 4 + (kSampC + s) * 2] + F[L::b3 / 4];
     const float yv1 = F[L::YP / 4 + 2 * s + 1] + F[L::YP / 4 + (kSampC + s) * 2 + 1] + F[L::b3 / 4 + 1];
-    const float ex = yv0 - F[L::T / 4 + 2 * s], ey = yv1 - F[L::T / 4 + 2 * s + 1];
+    const float ex = yv0 - F[L::T / 4 + 2 * si], ey = yv1 - F[L::T / 4 + 2 * si + 1];
     const float dy0 = valid ? 2.0f * ex * A.inv_batch : 0.0f, dy1 = valid ? 2.0f * ey * A.inv_batch : 0.0f;
     float lsum = valid && wg == 0 ? ex * ex + ey * ey : 0.0f;
     if (valid && wg == 0) {
@@ -716,11 +755,11 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
             A.yout[2 * (cbase + s) + 1] = yv1;
         }
         if (!A.backward && A.val_max_net) {
-            const float scv = F[L::SV / 4 + s];
+            const float scv = F[L::SV / 4 + si];
             const float en = scv * sqrtf(ex * ex + ey * ey);
-            const float tx = F[L::T / 4 + 2 * s], ty = F[L::T / 4 + 2 * s + 1];
+            const float tx = F[L::T / 4 + 2 * si], ty = F[L::T / 4 + 2 * si + 1];
             const float es = scv * sqrtf(tx * tx + ty * ty);
-            const int rc = I[L::RC / 4 + s];
+            const int rc = I[L::RC / 4 + si];
             atomicMax(&A.val_max_net[rc], __float_as_uint(en));
             atomicMax(&A.val_max_series[rc], __float_as_uint(es));
             atomicAdd(&A.val_sum[0], (double)en);
@@ -739,9 +778,10 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
             d1 += __shfl_xor_sync(0xffffffffu, d1, o);
         }
         if (lane == 0) {
-            F[L::WS / 4 + warp * 4] = d0;
-            F[L::WS / 4 + warp * 4 + 1] = d1;
-            F[L::WS / 4 + warp * 4 + 2] = lsum;
+            float *ws = F + L::WS / 4 + warp * 4;
+            ws[0] = first ? d0 : ws[0] + d0;
+            ws[1] = first ? d1 : ws[1] + d1;
+            ws[2] = first ? lsum : ws[2] + lsum;
         }
     }
     // ---- dh2 = (dy W3) silu'(h2) over the A1 region (layer 2's MMAs are done); FP32
@@ -771,9 +811,9 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
         }
         const float r0 = warp_colsum16(v), r1 = warp_colsum16(w0), r2 = warp_colsum16(w1);
         if (lane < 16) {
-            Slot[0 * 32 + 16 * hh + lane] = r0;
-            Slot[1 * 32 + 16 * hh + lane] = r1;
-            Slot[2 * 32 + 16 * hh + lane] = r2;
+            slot_add(0 * 32 + 16 * hh + lane, r0);
+            slot_add(1 * 32 + 16 * hh + lane, r1);
+            slot_add(2 * 32 + 16 * hh + lane, r2);
         }
     }
     // ---- da1 = dh2 W2 (M 128, N 64, K 64) over H2's columns; dh1 = da1 silu'(h1) over
@@ -808,20 +848,21 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
         }
         const float r3 = warp_colsum16(da1), r4 = warp_colsum16(g0), r5 = warp_colsum16(g1);
         if (lane < 16) {
-            Slot[3 * 32 + 16 * hh + lane] = r3;
-            Slot[4 * 32 + 16 * hh + lane] = r4;
-            Slot[5 * 32 + 16 * hh + lane] = r5;
+            slot_add(3 * 32 + 16 * hh + lane, r3);
+            slot_add(4 * 32 + 16 * hh + lane, r4);
+            slot_add(5 * 32 + 16 * hh + lane, r5);
         }
     }
-    // ---- dz = dh1 W1z (N 32, K 64); dW2 = dh2^T a1 and dW1z = dh1^T z from the stacked
-    // [dh2^T; dh1^T] (M 128 units, K 128 samples); over H1's and dA1's columns
+    // ---- dz = dh1 W1z (N 32, K 64) over dA1's columns; dW2 += dh2^T a1 and dW1z +=
+    // dh1^T z from the stacked [dh2^T; dh1^T] (M 128 units, K 128 samples)
     tc_publish();
     if (tid == 0) {
         tc_gemm(tm + L::cDZ, S + L::DH1, S + L::W1zT, kHid, umma::idesc_bf16(128, kLat));
-        tc_gemm(tm + L::cDW2, S + L::ST, S + L::A1T, kSampC, umma::idesc_bf16(128, kHid));
-        tc_gemm(tm + L::cDW1z, S + L::ST, S + L::ZT, kSampC, umma::idesc_bf16(128, kLat));
+        tc_gemm(tm + L::cDW2, S + L::ST, S + L::A1T, kSampC, umma::idesc_bf16(128, kHid), !first);
+        tc_gemm(tm + L::cDW1z, S + L::ST, S + L::ZT, kSampC, umma::idesc_bf16(128, kLat), !first);
         umma::commit(bar);
     }
+    if (!last) load_latents(A, cbase + kSampC + s, wg, zv);  // the next chunk's, in flight during the MMAs
     if (!tc_wait(bar, phase)) return false;
     {
         float v[16];
@@ -837,6 +878,7 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
             }
         }
     }
+    if (!last) return true;
     // gradient rows are 16-byte aligned (kGP = 6532 floats; dW2 at 2240, dW1z at 0)
     float *gp = A.gpart + (int64_t)blockIdx.x * kGP;
     if (s < kHid) {  // lanes 0..63: dW2[out = s][in]
@@ -869,12 +911,14 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
     return true;
 }
 
-// Training (backward = 1) or validation step over kSampC samples per CTA (two CTAs
-// per SM: 126 registers, ~110 KB of shared memory, 128 tensor-memory columns): the
-// layer-1 latent block, layer 2 and the four backward products on the
-// fifth-generation tensor cores (tcgen05.mma, BF16 operands in shared memory,
-// FP32 accumulators in tensor memory, mbarrier completion with bounded waits);
-// position block, biases, layer 3 and all column sums in FP32.
+// Training (backward = 1) or validation step over 256 samples per CTA in two
+// chunks of 128 (two CTAs per SM: ~113 KB of shared memory, 256 tensor-memory
+// columns each): the layer-1 latent block, layer 2 and the four backward products
+// on the fifth-generation tensor cores (tcgen05.mma, BF16 operands in shared
+// memory, FP32 accumulators in tensor memory, mbarrier completion with bounded
+// waits); position block, biases, layer 3 and all column sums in FP32.  One CTA row
+// of weight gradients per 256 samples: half the rows, and half the per-CTA set-up,
+// of a CTA per chunk.
 __global__ void __launch_bounds__(256, 2) k_ff_train(TrainArgs A)
 {
     extern __shared__ __align__(128) unsigned char tsm[];
@@ -885,11 +929,12 @@ __global__ void __launch_bounds__(256, 2) k_ff_train(TrainArgs A)
     int *I = reinterpret_cast<int *>(tsm);
     const int tid = threadIdx.x;
 
-    // ---- samples: generated ones depend only on the fit's fixed tables and run before
-    // the wait on the previous kernel (explicit ones are read after it)
+    // ---- samples, one per thread (both chunks): generated ones depend only on the
+    // fit's fixed tables and run before the wait on the previous kernel (explicit ones
+    // are read after it)
     const bool gen = A.zin == nullptr;
-    if (gen && tid < kSampC) {
-        const int64_t li = (int64_t)blockIdx.x * kSampC + tid;
+    if (gen) {
+        const int64_t li = (int64_t)blockIdx.x * kSampCTA + tid;
         const bool valid = li < A.spec.count;
         int rc = 0;
         float ux = 0.f, uy = 0.f, tx = 0.f, ty = 0.f, scv = 1.0f, vp = 1.0f;
@@ -913,30 +958,10 @@ __global__ void __launch_bounds__(256, 2) k_ff_train(TrainArgs A)
     // before its own wait) begin launching.
     pdl_wait();
     pdl_launch_next();
-    // ---- latents of this thread's sample (columns 16 wg .. 16 wg + 15), in flight during
-    // the weight staging: sample i's cell is (offset + i) mod nrc
+    // ---- latents of this thread's sample of the first chunk (columns 16 wg .. 16 wg + 15),
+    // in flight during the weight staging
     float zv[16];
-    {
-        const int s = tid & (kSampC - 1), wg = tid >> 7;
-        const int64_t li = (int64_t)blockIdx.x * kSampC + s;
-        const bool ok = li < A.spec.count;
-        const float *src = A.zin ? A.zin + li * kLat : A.z + ((A.spec.offset + li) % A.spec.nrc) * kLat;
-        src += 16 * wg;
-        if (!ok) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) zv[j] = 0.0f;
-        } else if (((uintptr_t)src & 7u) == 0) {  // the latents (after the 6530 parameters) are 8-byte aligned
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float2 v = reinterpret_cast<const float2 *>(src)[j];
-                zv[2 * j] = v.x;
-                zv[2 * j + 1] = v.y;
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) zv[j] = src[j];
-        }
-    }
+    load_latents(A, (int64_t)blockIdx.x * kSampCTA + (tid & (kSampC - 1)), tid >> 7, zv);
     // ---- weights: the BF16 operands' shared-memory image (16-byte copies), FP32
     // small parameters
     for (int i = tid; i < kWImgBytes / 16; i += 256)
@@ -950,8 +975,8 @@ __global__ void __launch_bounds__(256, 2) k_ff_train(TrainArgs A)
         F[L::b2 / 4 + tid] = A.params[ob2 + tid];
     }
     if (tid < 2) F[L::b3 / 4 + tid] = A.params[ob3 + tid];
-    if (!gen && tid < kSampC) {
-        const int64_t li = (int64_t)blockIdx.x * kSampC + tid;
+    if (!gen) {
+        const int64_t li = (int64_t)blockIdx.x * kSampCTA + tid;
         const bool valid = li < A.spec.count;
         float ux = 0.f, uy = 0.f, tx = 0.f, ty = 0.f;
         if (valid) {
@@ -973,11 +998,20 @@ __global__ void __launch_bounds__(256, 2) k_ff_train(TrainArgs A)
     umma::fence_after();
     const uint32_t tm = tmem;
     uint32_t phase = 0;
-    if (!train_step(A, tsm, &bar, &idle, tm, phase, zv) && tid == 0) {
-        // a completion wait gave up: flag it and drain (bounded) before freeing
-        // the tensor memory
-        if (A.err) atomicExch(A.err, 1);
-        umma::mbar_wait(&bar, phase, kWaitPolls);
+#pragma unroll 1
+    for (int chunk = 0; chunk < kChunks; ++chunk) {
+        // (a backward chunk loads the next one's latents itself)
+        if (chunk > 0 && !A.backward)
+            load_latents(A, (int64_t)blockIdx.x * kSampCTA + chunk * kSampC + (tid & (kSampC - 1)), tid >> 7, zv);
+        if (!train_step(A, tsm, &bar, &idle, tm, phase, zv, chunk)) {
+            // a completion wait gave up: flag it and drain (bounded) before freeing
+            // the tensor memory
+            if (tid == 0) {
+                if (A.err) atomicExch(A.err, 1);
+                umma::mbar_wait(&bar, phase, kWaitPolls);
+            }
+            break;
+        }
     }
     umma::fence_before();
     __syncthreads();
@@ -1005,21 +1039,21 @@ static cudaError_t launch_pdl(void (*k)(P...), dim3 grid, dim3 block, size_t sme
 
 cudaError_t ff_train_step(const TrainArgs &t, int64_t nsamples, cudaStream_t s, bool pdl)
 {
-    // two CTAs of ~110 KB per SM: the largest shared-memory carveout
+    // two CTAs of ~113 KB per SM: the largest shared-memory carveout
     cudaError_t e = cudaFuncSetAttribute(k_ff_train, cudaFuncAttributeMaxDynamicSharedMemorySize, TrainTc::bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_ff_train, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     if (nsamples <= 0) return cudaSuccess;
-    const unsigned nb = (unsigned)((nsamples + kSampC - 1) / kSampC);
+    const unsigned nb = (unsigned)((nsamples + kSampCTA - 1) / kSampCTA);
     if (pdl) return launch_pdl(k_ff_train, dim3(nb), dim3(256), TrainTc::bytes, s, t);
     k_ff_train<<<nb, 256, TrainTc::bytes, s>>>(t);
     return cudaGetLastError();
 }
 
 int64_t ff_gpart_stride() { return kGP; }
-int64_t ff_train_blocks(int64_t nsamples) { return (nsamples + kSampC - 1) / kSampC; }
+int64_t ff_train_blocks(int64_t nsamples) { return (nsamples + kSampCTA - 1) / kSampCTA; }
 
 // grads[p] = sum over the CTA rows of gpart: a CTA takes 32 columns; its 8 row
 // groups each sum a contiguous eighth of the rows in row order (loads in flight
