@@ -410,29 +410,29 @@ constexpr int kSampCTA = kChunks * kSampC;
 constexpr int kGP = kParams + 2;     // gpart row: the parameters' gradients, then the loss
 
 // Shared memory of the training kernel (byte offsets).  Every tensor-core
-// operand is K-major BF16 in 8-row x 16-byte core matrices: element (r, k) of an
-// operand with K columns at tc_off(r, k, K); descriptors take 128 bytes between
-// K-adjacent core matrices and 16 K bytes between 8-row groups.
+// operand is a row-major BF16 block [R][C] of 8-row x 16-byte core matrices:
+// element (r, c) at tc_off(r, c, C), 128 bytes between core matrices along a row
+// and 16 C bytes between 8-row groups.  A product whose K runs along the rows
+// (over the columns c) reads the block K-major; one whose K runs down the columns
+// (over the rows r: the weight gradients' sums over samples, the backward
+// products' sums over output units) reads the same block MN-major.  Every block is
+// written once, in its natural row order, with 16-byte stores.
 __host__ __device__ constexpr int tc_off(int r, int k, int K)
 {
     return (r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 struct TrainTc {
-    // B operands (N x K): the weights
+    // the weights [out][in]: B operands K-major for the forward products, MN-major for
+    // the backward ones (dA1 = dH2 W2, dZ = dH1 W1z)
     static constexpr int W1z = 0;                        // [64 out][32 in]  layer 1, latent block
     static constexpr int W2 = W1z + kHid * kLat * 2;     // [64 out][64 in]  layer 2
-    static constexpr int W2T = W2 + kHid * kHid * 2;     // [64 in][64 out]  da1 = dh2 W2
-    static constexpr int W1zT = W2T + kHid * kHid * 2;   // [32 in][64 out]  dz = dh1 W1z
-    // A operands (M = 128 samples x K), one region in turn: Z [128][32], then A1,
-    // dH2 and dH1 [128][64]; each is written only after the MMAs reading the
-    // previous one have completed
-    static constexpr int Z = W1zT + kLat * kHid * 2;
-    static constexpr int A1 = Z, DH2 = Z, DH1 = Z;
-    // weight gradients: A = [dh2^T; dh1^T] (128 units x 128 samples), B = a1^T, z^T
-    static constexpr int ST = Z + kSampC * kHid * 2;     // [128][128]
-    static constexpr int A1T = ST + 128 * kSampC * 2;    // [64][128]
-    static constexpr int ZT = A1T + kHid * kSampC * 2;   // [32][128]
-    static constexpr int EndOps = ZT + kLat * kSampC * 2;
+    // per-sample blocks [128 samples][units]: A operands K-major for the per-sample
+    // products; MN-major, over their samples, for the weight gradients: dW2 = dH2^T A1
+    // and dW1z = dH1^T Z from the stacked [dH2 | dH1] (M = 128 units) against A1 and Z
+    static constexpr int Z = W2 + kHid * kHid * 2;       // [128][32]
+    static constexpr int A1 = Z + kSampC * kLat * 2;     // [128][64]
+    static constexpr int DH = A1 + kSampC * kHid * 2;    // [128][128]: dh2 in units 0..63, dh1 in 64..127
+    static constexpr int EndOps = DH + kSampC * 2 * kHid * 2;
     // FP32 / int region
     static constexpr int W1u = EndOps;                   // [64][2]
     static constexpr int b1 = W1u + 2 * kHid * 4;
@@ -456,29 +456,28 @@ struct TrainTc {
     static constexpr int cH1 = 0, cH2 = 64, cDA1 = 64, cDZ = 64, cDW2 = 128, cDW1z = 192, ncols = 256;
 };
 // two CTAs per SM: their dynamic and static shared memory within the SM's 228 KB
-// less 1 KB per CTA, and their tensor memory within the SM's 512 columns
+// less 1 KB per CTA, and their tensor memory within the SM's 512 columns (tensor
+// memory allows no more than two)
 static_assert(TrainTc::bytes + 128 <= (228 * 1024) / 2 - 1024, "two training CTAs per SM");
 static_assert(2 * TrainTc::ncols <= 512, "two training CTAs per SM");
 
-// The training kernel's weight operands as they sit in its shared memory (W1z, W2,
-// W2T, W1zT at their TrainTc offsets): written wherever the BF16 weight copies are
+// The training kernel's weight operands as they sit in its shared memory (W1z and
+// W2 at their TrainTc offsets): written wherever the BF16 weight copies are
 // refreshed, so that a training CTA stages them with 16-byte copies.
 constexpr int kWImgBytes = TrainTc::Z;
 static_assert(kWImgBytes % 16 == 0, "the weight image is copied in 16-byte units");
 
 // Entry i of the flat parameter vector (a W1z or W2 weight), rounded to BF16, into
-// its two places of the image (the operand and its transpose).
+// its place in the image.
 __device__ __forceinline__ void wimg_put(unsigned char *img, int64_t i, __nv_bfloat16 b)
 {
     using L = TrainTc;
     if (i >= oW1z && i < oW1z + kHid * kLat) {
         const int o = (int)(i - oW1z) / kLat, k = (int)(i - oW1z) % kLat;
         *reinterpret_cast<__nv_bfloat16 *>(img + L::W1z + tc_off(o, k, kLat)) = b;
-        *reinterpret_cast<__nv_bfloat16 *>(img + L::W1zT + tc_off(k, o, kHid)) = b;
     } else if (i >= oW2 && i < oW2 + kHid * kHid) {
         const int o = (int)(i - oW2) / kHid, k = (int)(i - oW2) % kHid;
         *reinterpret_cast<__nv_bfloat16 *>(img + L::W2 + tc_off(o, k, kHid)) = b;
-        *reinterpret_cast<__nv_bfloat16 *>(img + L::W2T + tc_off(k, o, kHid)) = b;
     }
 }
 
@@ -566,11 +565,6 @@ __device__ __forceinline__ float warp_colsum16(float (&v)[16])
     return v[0];
 }
 
-__device__ __forceinline__ void st_bf16(unsigned char *S, int off, float v)
-{
-    *reinterpret_cast<__nv_bfloat16 *>(S + off) = to_bf16(v);
-}
-
 // Make this thread's shared-memory operand writes visible to the tensor cores and
 // wait for the whole CTA.
 __device__ __forceinline__ void tc_publish()
@@ -610,15 +604,28 @@ __device__ __forceinline__ void st_f4x4(float *dst, const float (&v)[16])  // 16
         reinterpret_cast<float4 *>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 
+// An operand of a product: a block of tc_off core matrices with `cols` columns,
+// starting at byte `off` of shared memory, read K-major (K along its columns) or
+// MN-major (K down its rows).
+struct TcOp {
+    int off, cols;
+    bool mn;
+    // descriptor strides: along K, along M/N, and the advance per K = 16 step
+    __device__ __forceinline__ uint32_t lbo() const { return mn ? (uint32_t)(cols * 16) : 128u; }
+    __device__ __forceinline__ uint32_t sbo() const { return mn ? 128u : (uint32_t)(cols * 16); }
+    __device__ __forceinline__ uint32_t step() const { return mn ? (uint32_t)(cols * 32) : 256u; }
+};
+
 // One thread issues D = sum_k A[:, k] B[:, k]^T over K / 16 MMAs of K = 16 (acc:
-// D += instead).
-__device__ __forceinline__ void tc_gemm(uint32_t d, const unsigned char *A, const unsigned char *B, int K,
-                                        uint32_t idesc, bool acc = false)
+// D += instead); M = 128.
+__device__ __forceinline__ void tc_gemm(uint32_t d, const unsigned char *S, TcOp A, TcOp B, int N, int K,
+                                        bool acc = false)
 {
-    const uint32_t a = umma::smem_addr(A), b = umma::smem_addr(B), sbo = (uint32_t)(K * 16);
+    const uint32_t a = umma::smem_addr(S + A.off), b = umma::smem_addr(S + B.off);
+    const uint32_t idesc = umma::idesc_bf16(128, N, A.mn, B.mn);
     for (int ks = 0; ks < K / 16; ++ks)
-        umma::mma_bf16(d, umma::desc(a + ks * 256, 128, sbo), umma::desc(b + ks * 256, 128, sbo), idesc,
-                       acc || ks > 0 ? 1u : 0u);
+        umma::mma_bf16(d, umma::desc(a + ks * A.step(), A.lbo(), A.sbo()),
+                       umma::desc(b + ks * B.step(), B.lbo(), B.sbo()), idesc, acc || ks > 0 ? 1u : 0u);
 }
 
 // 16 latent columns (16 wg .. 16 wg + 15) of sample li of the launch, zero past its
@@ -686,8 +693,6 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
     // ---- latents (gathered at kernel start): thread (wg, s) has columns 16 wg .. 16 wg + 15 of z_s
     {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) st_bf16(S, L::ZT + tc_off(16 * wg + j, s, kSampC), zv[j]);
-#pragma unroll
         for (int h = 0; h < 2; ++h)
             *reinterpret_cast<uint4 *>(S + L::Z + tc_off(s, 16 * wg + 8 * h, kLat)) =
                 make_uint4(pack_bf16(zv[8 * h], zv[8 * h + 1]), pack_bf16(zv[8 * h + 2], zv[8 * h + 3]),
@@ -696,12 +701,12 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
     // ---- layer 1, latent block: H1 = Z W1z^T (M 128, N 64, K 32)
     tc_publish();
     if (tid == 0) {
-        tc_gemm(tm + L::cH1, S + L::Z, S + L::W1z, kLat, umma::idesc_bf16(128, kHid));
+        tc_gemm(tm + L::cH1, S, TcOp{L::Z, kLat, false}, TcOp{L::W1z, kLat, false}, kHid, kLat);
         umma::commit(bar);
     }
     if (!tc_wait(bar, phase, A.wait_probe && first ? idle : nullptr)) return false;
 #pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {  // A1 = silu(H1 + W1u u + b1) over the Z region (its MMAs are done)
+    for (int hh = 0; hh < 2; ++hh) {  // A1 = silu(H1 + W1u u + b1)
         const int c = c0 + 16 * hh;
         float h1[16];
         load_h1(c, h1);
@@ -709,10 +714,7 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
         for (int q = 0; q < 2; ++q) {
             float a[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                a[j] = silu1(h1[8 * q + j]);
-                st_bf16(S, L::A1T + tc_off(c + 8 * q + j, s, kSampC), a[j]);
-            }
+            for (int j = 0; j < 8; ++j) a[j] = silu1(h1[8 * q + j]);
             *reinterpret_cast<uint4 *>(S + L::A1 + tc_off(s, c + 8 * q, kHid)) =
                 make_uint4(pack_bf16(a[0], a[1]), pack_bf16(a[2], a[3]), pack_bf16(a[4], a[5]), pack_bf16(a[6], a[7]));
         }
@@ -720,7 +722,7 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
     // ---- layer 2: H2 = A1 W2^T (M 128, N 64, K 64); layer 3 in FP32
     tc_publish();
     if (tid == 0) {
-        tc_gemm(tm + L::cH2, S + L::A1, S + L::W2, kHid, umma::idesc_bf16(128, kHid));
+        tc_gemm(tm + L::cH2, S, TcOp{L::A1, kHid, false}, TcOp{L::W2, kHid, false}, kHid, kHid);
         umma::commit(bar);
     }
     if (!tc_wait(bar, phase)) return false;
@@ -784,8 +786,7 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
             ws[2] = first ? lsum : ws[2] + lsum;
         }
     }
-    // ---- dh2 = (dy W3) silu'(h2) over the A1 region (layer 2's MMAs are done); FP32
-    // column sums for b2 and W3
+    // ---- dh2 = (dy W3) silu'(h2) into units 0..63 of DH; FP32 column sums for b2 and W3
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh) {
         const int c = c0 + 16 * hh;
@@ -804,9 +805,8 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
                 const float a2 = silu2(h2[jj]);
                 w0[jj] = dy0 * a2;
                 w1[jj] = dy1 * a2;
-                st_bf16(S, L::ST + tc_off(c + jj, s, kSampC), d[j]);
             }
-            *reinterpret_cast<uint4 *>(S + L::DH2 + tc_off(s, c + 8 * q, kHid)) =
+            *reinterpret_cast<uint4 *>(S + L::DH + tc_off(s, c + 8 * q, 2 * kHid)) =
                 make_uint4(pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]), pack_bf16(d[6], d[7]));
         }
         const float r0 = warp_colsum16(v), r1 = warp_colsum16(w0), r2 = warp_colsum16(w1);
@@ -816,11 +816,11 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
             slot_add(2 * 32 + 16 * hh + lane, r2);
         }
     }
-    // ---- da1 = dh2 W2 (M 128, N 64, K 64) over H2's columns; dh1 = da1 silu'(h1) over
-    // the dH2 region; sums for b1 and W1u
+    // ---- da1 = dh2 W2 (M 128, N 64, K 64: W2 read MN-major) over H2's columns; dh1 =
+    // da1 silu'(h1) into units 64..127 of DH; sums for b1 and W1u
     tc_publish();
     if (tid == 0) {
-        tc_gemm(tm + L::cDA1, S + L::DH2, S + L::W2T, kHid, umma::idesc_bf16(128, kHid));
+        tc_gemm(tm + L::cDA1, S, TcOp{L::DH, 2 * kHid, false}, TcOp{L::W2, kHid, true}, kHid, kHid);
         umma::commit(bar);
     }
     if (!tc_wait(bar, phase)) return false;
@@ -841,9 +841,8 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
                 da1[jj] = d[j];
                 g0[jj] = d[j] * ux;
                 g1[jj] = d[j] * uy;
-                st_bf16(S, L::ST + tc_off(kHid + c + jj, s, kSampC), d[j]);
             }
-            *reinterpret_cast<uint4 *>(S + L::DH1 + tc_off(s, c + 8 * q, kHid)) =
+            *reinterpret_cast<uint4 *>(S + L::DH + tc_off(s, kHid + c + 8 * q, 2 * kHid)) =
                 make_uint4(pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]), pack_bf16(d[6], d[7]));
         }
         const float r3 = warp_colsum16(da1), r4 = warp_colsum16(g0), r5 = warp_colsum16(g1);
@@ -853,13 +852,14 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
             slot_add(5 * 32 + 16 * hh + lane, r5);
         }
     }
-    // ---- dz = dh1 W1z (N 32, K 64) over dA1's columns; dW2 += dh2^T a1 and dW1z +=
-    // dh1^T z from the stacked [dh2^T; dh1^T] (M 128 units, K 128 samples)
+    // ---- dz = dh1 W1z (N 32, K 64: W1z read MN-major) over dA1's columns; dW2 += dh2^T a1
+    // and dW1z += dh1^T z from the stacked [dh2 | dh1], A1 and Z read MN-major (M 128
+    // units, K 128 samples)
     tc_publish();
     if (tid == 0) {
-        tc_gemm(tm + L::cDZ, S + L::DH1, S + L::W1zT, kHid, umma::idesc_bf16(128, kLat));
-        tc_gemm(tm + L::cDW2, S + L::ST, S + L::A1T, kSampC, umma::idesc_bf16(128, kHid), !first);
-        tc_gemm(tm + L::cDW1z, S + L::ST, S + L::ZT, kSampC, umma::idesc_bf16(128, kLat), !first);
+        tc_gemm(tm + L::cDZ, S, TcOp{L::DH + kHid / 8 * 128, 2 * kHid, false}, TcOp{L::W1z, kLat, true}, kLat, kHid);
+        tc_gemm(tm + L::cDW2, S, TcOp{L::DH, 2 * kHid, true}, TcOp{L::A1, kHid, true}, kHid, kSampC, !first);
+        tc_gemm(tm + L::cDW1z, S, TcOp{L::DH, 2 * kHid, true}, TcOp{L::Z, kLat, true}, kLat, kSampC, !first);
         umma::commit(bar);
     }
     if (!last) load_latents(A, cbase + kSampC + s, wg, zv);  // the next chunk's, in flight during the MMAs
@@ -912,7 +912,7 @@ __device__ __forceinline__ bool train_step(const TrainArgs &A, unsigned char *S,
 }
 
 // Training (backward = 1) or validation step over 256 samples per CTA in two
-// chunks of 128 (two CTAs per SM: ~113 KB of shared memory, 256 tensor-memory
+// chunks of 128 (two CTAs per SM: ~85 KB of shared memory, 256 tensor-memory
 // columns each): the layer-1 latent block, layer 2 and the four backward products
 // on the fifth-generation tensor cores (tcgen05.mma, BF16 operands in shared
 // memory, FP32 accumulators in tensor memory, mbarrier completion with bounded
@@ -1039,7 +1039,7 @@ static cudaError_t launch_pdl(void (*k)(P...), dim3 grid, dim3 block, size_t sme
 
 cudaError_t ff_train_step(const TrainArgs &t, int64_t nsamples, cudaStream_t s, bool pdl)
 {
-    // two CTAs of ~113 KB per SM: the largest shared-memory carveout
+    // two CTAs of ~85 KB per SM (tensor memory allows no more): the largest shared-memory carveout
     cudaError_t e = cudaFuncSetAttribute(k_ff_train, cudaFuncAttributeMaxDynamicSharedMemorySize, TrainTc::bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_ff_train, cudaFuncAttributePreferredSharedMemoryCarveout,

@@ -1,6 +1,6 @@
 // umma.cuh -- Blackwell fifth-generation tensor-core helpers (tcgen05, inline
 // PTX): tensor-memory allocation, shared-memory matrix descriptors for K-major
-// operands without swizzle, the BF16 -> FP32 MMA, its commit to an mbarrier,
+// and MN-major operands without swizzle, the BF16 -> FP32 MMA, its commit to an mbarrier,
 // a bounded wait, and accumulator loads.
 //
 // Operand layout ("core matrices"): a K-major [R][64] BF16 operand is stored as
@@ -9,6 +9,15 @@
 // In descriptor terms the leading-dimension (K) offset is 128 bytes and the
 // stride-dimension (M/N) offset 1024 bytes; one MMA consumes K = 16, i.e. the
 // next two core matrices along K (+256 bytes per step).
+//
+// An MN-major operand (instruction-descriptor transpose bit) has core matrices of
+// 8 K-rows x 16 bytes along M/N.  Without swizzle its descriptor takes the same
+// roles as a K-major one: the leading-dimension offset is the stride between core
+// matrices along K and the stride-dimension offset the stride along M/N (measured
+// on GB300 with an M = 128, N = 64, K = 16 product against a host reference: the
+// other assignment gives a different product).  So a row-major block of 8 x 8
+// core matrices [rows][cols] serves both as a K-major operand over its columns
+// and as an MN-major operand over its rows.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -31,11 +40,12 @@ __device__ __forceinline__ uint64_t desc(uint32_t addr, uint32_t lbo, uint32_t s
            ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, shape M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n)
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, shape
+// M x N; A and B K-major unless a_mn / b_mn (MN-major).
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n, bool a_mn = false, bool b_mn = false)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
 // Whole warp: allocate ncols tensor-memory columns, address written to *dst.
