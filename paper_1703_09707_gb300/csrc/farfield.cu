@@ -1217,17 +1217,18 @@ cudaError_t ff_flags(const unsigned *maxerr, int nrc, float tol, int *flags, cud
 
 // ================================================ learned shooting kernel
 struct LearnSmem {
-    __align__(128) unsigned char w2cm[kHid * kHid * 2];  // W2 [out][in], BF16, core-matrix layout (B operand)
+    __align__(128) unsigned char w2cm[kHid * kHid * 2];  // W2 / 2 [out][in], BF16, core-matrix layout (B operand)
     uint64_t mbar[2];     // per warpgroup: completion of its tensor-core MMAs
     uint64_t idle;        // an mbarrier nothing arrives on (the wait probe, a test aid)
     uint32_t tmem;        // tensor-memory base: 128 columns, 64 per warpgroup
     int wg_ok[8];         // per warp: the last wait completed
     int tc_dead[2];       // per warpgroup: a wait gave up; no more MMAs
     uint32_t pending[2];  // the phase a dead warpgroup still waits for
-    // per pair of hidden units (c, c + 1), c = 2 P, in the order packed f32x2 operations take them:
-    float4 l1p[kHid / 2];  // {e_c, e_c+1 (this tile's cell), W1u[c][0], W1u[c+1][0]}
-    float2 l1q[kHid / 2];  // {W1u[c][1], W1u[c+1][1]}
-    float4 l2p[kHid / 2];  // {b2[c], b2[c+1], W3[0][c], W3[0][c+1]}
+    // per pair of hidden units (c, c + 1), c = 2 P, in the order packed f32x2 operations take them
+    // (the constants of a pre-activation halved: the block forms v / 2, SiLU's argument):
+    float4 l1p[kHid / 2];  // {e_c, e_c+1 (this tile's cell), W1u[c][0], W1u[c+1][0]} / 2
+    float2 l1q[kHid / 2];  // {W1u[c][1], W1u[c+1][1]} / 2
+    float4 l2p[kHid / 2];  // {b2[c] / 2, b2[c+1] / 2, W3[0][c], W3[0][c+1]}
     float2 l2q[kHid / 2];  // {W3[1][c], W3[1][c+1]}
     float b3[2];
     float coef[kCoefStride];
@@ -1239,12 +1240,13 @@ struct LearnSmem {
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 
-// SiLU of two hidden units at once, as silu_hw: h = v / 2, h + h tanh(h) with the
-// hardware tanh (packed FP32 for the multiply and the FMA).
+// SiLU of two hidden units at once, as silu_hw, from h = v / 2: h + h tanh(h) with
+// the hardware tanh (one packed FMA).  The learned kernel forms h directly: every
+// constant that enters a pre-activation (e_c, W1u, W2, b2) is staged halved, and
+// halving is exact, so h equals 0.5 v of the unhalved evaluation bit for bit.
 static_assert(kLayer2Hw, "the packed network block uses the hardware-tanh SiLU in both layers");
-__device__ __forceinline__ float2 silu_hw2(float2 v)
+__device__ __forceinline__ float2 silu_half2(float2 h)
 {
-    const float2 h = __fmul2_rn(v, make_float2(0.5f, 0.5f));
     return __ffma2_rn(h, make_float2(tanh_hw(h.x), tanh_hw(h.y)), h);
 }
 
@@ -1313,7 +1315,8 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
         const float im = L.coef[(int64_t)rc * kCoefStride + 5 + 2 * tid];
         ls.coef2[tid] = make_float4(re, re, im, im);
     }
-    if (tid < kHid) reinterpret_cast<float *>(&ls.l1p[tid >> 1])[tid & 1] = L.ec ? L.ec[(int64_t)rc * kHid + tid] : 0.0f;
+    if (tid < kHid)  // e_c / 2 (exact)
+        reinterpret_cast<float *>(&ls.l1p[tid >> 1])[tid & 1] = L.ec ? 0.5f * L.ec[(int64_t)rc * kHid + tid] : 0.0f;
     __syncthreads();
 
     // ray offsets from the tile centre: the high parts here, the low parts (LO) formed
@@ -1442,10 +1445,10 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
                     for (int q = 0; q < 4; ++q) {  // units 8 k8 + 2 q and + 1
                         const float4 pa = ls.l1p[4 * k8 + q];
                         const float2 pb = ls.l1q[4 * k8 + q];
-                        // e_c + W1u[.][0] ux + W1u[.][1] uy, then SiLU, for both units
+                        // (e_c + W1u[.][0] ux + W1u[.][1] uy) / 2, then SiLU, for both units
                         float2 v = __ffma2_rn(make_float2(pa.z, pa.w), uxx, make_float2(pa.x, pa.y));
                         v = __ffma2_rn(pb, uyy, v);
-                        const float2 a = silu_hw2(v);
+                        const float2 a = silu_half2(v);
                         pk[q] = pack_bf16(a.x, a.y);
                     }
                     *reinterpret_cast<uint4 *>(abuf + umma::cm_offset(t, k8 * 8)) =
@@ -1485,7 +1488,7 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
                         for (int j = 0; j < 16; j += 2) {
                             const float4 qa = ls.l2p[(c0 + j) >> 1];
                             const float2 qb = ls.l2q[(c0 + j) >> 1];
-                            const float2 a2 = silu_hw2(__fadd2_rn(
+                            const float2 a2 = silu_half2(__fadd2_rn(
                                 make_float2(__uint_as_float(acc[j]), __uint_as_float(acc[j + 1])), make_float2(qa.x, qa.y)));
                             y0p = __ffma2_rn(make_float2(qa.z, qa.w), a2, y0p);
                             y1p = __ffma2_rn(qb, a2, y1p);
@@ -1623,7 +1626,8 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
 template <int NRP, bool NET, bool LO>
 // Three CTAs per SM (80 registers, ~100 bytes of spills per thread): six warps per
 // scheduler hide the latency of the 128 hardware tanh per ray better than four
-// (0.060 s -> 0.056 s per 32768^2-ray map at two CTAs per SM and 128 registers).
+// (0.056 s against 0.060 s per 32768^2-ray map at two CTAs per SM and 128 registers
+// when first measured; 0.051 s against 0.056 s with the packed network block).
 __global__ void __launch_bounds__(kThreads, 3) k_shoot_learned(LearnedArgs L)
 {
     __shared__ __align__(16) ShootSmem<256> sm;
@@ -1635,12 +1639,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_shoot_learned(LearnedArgs L)
     uint32_t phase = 0;  // completed MMA batches of this thread's warpgroup, mod 2
     if (NET) {
         for (int i = tid; i < kHid * kHid; i += kThreads)
-            *reinterpret_cast<__nv_bfloat16 *>(ls.w2cm + umma::cm_offset(i / kHid, i % kHid)) = L.w2b[i];
+            *reinterpret_cast<__nv_bfloat16 *>(ls.w2cm + umma::cm_offset(i / kHid, i % kHid)) =
+                __float2bfloat16_rn(0.5f * __bfloat162float(L.w2b[i]));  // W2 / 2 (exact)
         if (tid < kHid) {
             const int P = tid >> 1, h = tid & 1;
-            reinterpret_cast<float *>(&ls.l1p[P])[2 + h] = L.params[oW1u + 2 * tid];
-            reinterpret_cast<float *>(&ls.l1q[P])[h] = L.params[oW1u + 2 * tid + 1];
-            reinterpret_cast<float *>(&ls.l2p[P])[h] = L.params[ob2 + tid];
+            reinterpret_cast<float *>(&ls.l1p[P])[2 + h] = 0.5f * L.params[oW1u + 2 * tid];
+            reinterpret_cast<float *>(&ls.l1q[P])[h] = 0.5f * L.params[oW1u + 2 * tid + 1];
+            reinterpret_cast<float *>(&ls.l2p[P])[h] = 0.5f * L.params[ob2 + tid];
             reinterpret_cast<float *>(&ls.l2p[P])[2 + h] = L.params[oW3 + tid];
             reinterpret_cast<float *>(&ls.l2q[P])[h] = L.params[oW3 + kHid + tid];
         }
@@ -1699,8 +1704,8 @@ static cudaError_t learned_attributes(K kernel)
 cudaError_t ff_learned_grid(int *grid)
 {
     // The persistent grid takes the resident CTAs per SM of the kernel without
-    // tensor-core code (two: registers, launch-bounded to 128 per thread).  The
-    // tensor-core variant has the same register and shared-memory limits (ncu: 2
+    // tensor-core code (three: launch-bounded to 80 registers per thread).  The
+    // tensor-core variant has the same register and shared-memory limits (ncu: 3
     // by registers, 3 by shared memory), though the occupancy query reports one
     // for it; CTAs beyond those resident only find the shared work queue empty.
     int per_sm = 0, per_sm1 = 0;
