@@ -333,11 +333,13 @@ def bench_binning(M, torch, steps: int, warmup: int, flush):
 
 
 # ------------------------------------------------------------ light curves
-def bench_lightcurve(M, torch, steps: int, warmup: int, flush):
+def bench_lightcurve(M, torch, steps: int, warmup: int, flush, peak_fp32_fma: float):
     """The paper field's 8192^2 rays binned into a 4096^2 map (the learned workload's
     map size) and convolved with a Gaussian source (sigma = 0.05 theta_E, 10 pixels)
     and a uniform disk (R = 0.1 theta_E, 20 pixels), then a 4096-point light curve
-    across it; CUDA events, L2 flushed before each timed call."""
+    across it; CUDA events, L2 flushed before each timed call.  The Gaussian's two
+    separable passes are bound by FP32 multiply-adds (2K + 1 per pixel and pass), so
+    its fraction is also stated against the FP32 FMA rate."""
     wl = W.config("paper")
     f, rays = wl.fields[0], wl.rays[0]
     src = W.Grid(-10.0, 10.0, -10.0, 10.0, 4096, 4096)
@@ -375,6 +377,14 @@ def bench_lightcurve(M, torch, steps: int, warmup: int, flush):
         gbs = 8.0 * src.n / (ms / 1e3) / 1e9
         out[key] = {"ms": ms, "pixels_per_s": src.n / (ms / 1e3), "min_bytes_gbs": gbs, "hbm_frac": gbs / peak,
                     "note": "asynchronous call with a caller workspace: setup kernel and passes"}
+        if prof == M.MLENS_PROFILE_GAUSSIAN:
+            # taps per axis: the library's half-width is ceil(4 sigma / pixel)
+            kx = math.ceil(4.0 * size / ((src.x1 - src.x0) / src.nx))
+            ky = math.ceil(4.0 * size / ((src.y1 - src.y0) / src.ny))
+            fmas = src.n * ((2 * kx + 1) + (2 * ky + 1))
+            out[key].update({"taps": [2 * kx + 1, 2 * ky + 1], "fma_per_s": fmas / (ms / 1e3),
+                             "fma_frac": fmas / (ms / 1e3) / peak_fp32_fma,
+                             "fma_peak_basis": "FP32 FMA: 128 per SM per clock x SMs x max SM clock"})
         del work
     ms = timed(lambda: M.mlens_light_curve(conv, src, (-8.0, -3.0), (8.0, 4.0), 4096, curve))
     out["light_curve_4096_points_ms"] = ms
@@ -802,7 +812,8 @@ def run_mine(args):
             bn["fused_epilogue"]["share_of_paper_step"] = bn["fused_epilogue"]["ms"] / kernel_ms
             line["binning"] = bn
         if "lightcurve" in extras:
-            line["lightcurve"] = bench_lightcurve(M, torch, max(3, min(args.steps, 10)), 2, flush)
+            line["lightcurve"] = bench_lightcurve(M, torch, max(3, min(args.steps, 10)), 2, flush,
+                                                  n_sm * 128 * SM_MAX_MHZ * 1e6)
         if "split" in extras:
             line["split"] = bench_split(M, torch, flush, peak)
         if "learned" in extras:
