@@ -395,7 +395,8 @@ def bench_lightcurve(M, torch, steps: int, warmup: int, flush, peak_fp32_fma: fl
 def bench_split(M, torch, flush, peak):
     """10^7 stars on ray grids of 256^2 and 512^2 rays (32 and 128 tiles of 64 x 32
     rays, fewer than the GPU's 152 SMs): each tile's star sum split over clusters of
-    1, 2, 4 and 8 CTAs, one CUDA-event-timed map per setting after a warm-up map."""
+    1, 2, 4 and 8 CTAs and, through global memory, over the automatic choice's number
+    of CTAs; one CUDA-event-timed map per setting after a warm-up map."""
     wl = W.config("large_n")
     f, rays0, src = wl.fields[0], wl.rays[0], wl.srcs[0]
     stream = torch.cuda.current_stream()
@@ -408,7 +409,7 @@ def bench_split(M, torch, flush, peak):
         auto = M.mlens_star_split_for(ctx, rays)
         inter = rays.n * f.n
         by = {}
-        for split in (1, 2, 4, 8):
+        for split in sorted({1, 2, 4, 8, auto}):
             M.mlens_set_star_split(ctx, split)
             M.mlens_shoot(ctx, rays, src, counts)
             flush.fill_(float(split))

@@ -119,17 +119,21 @@ int mlens_set_tuning(mlens_ctx *ctx, int32_t rays_per_thread, int32_t star_stage
  * FP32 re-centred kernel (MLENS_PREC_FP32 with the default 256-star stage and
  * fma_pairs = 0; other settings never split).  The paper's closing discussion
  * of very large star fields proposes splitting the bending-angle sum of one
- * image position over several threads; here split = 2, 4 or 8 CTAs form a
- * thread-block cluster on the tile, each sums one of `split` consecutive
- * 32-star-aligned slices of the stars with the same compensated loop, and the
- * first CTA folds the others' partial sums (read through distributed shared
- * memory, in slice order) into its own before beta and binning.  That keeps the
- * GPU full when a grid has few tiles for its star count.  split = 1 never
- * splits; 0 (the default) chooses per call from the number of tiles, the SM
- * count and the star count (at least 2048 stars per slice).  The sum's order
- * depends on the split, so beta may differ in its last bits between splits
- * (never by more than the error bar); a given split is deterministic.
- * Errors: MLENS_ERR_ARG.
+ * image position over several threads; here each of `split` CTAs sums one of
+ * `split` consecutive 32-star-aligned slices of the stars with the same
+ * compensated loop, and the slices' partial sums are folded in slice order
+ * before beta and binning.  split = 2 .. 8: the CTAs form a thread-block
+ * cluster and the first folds the others' partials, read through distributed
+ * shared memory.  split = 9 .. 4096: each CTA stores its partials in global
+ * memory (a context workspace of up to 256 MB, allocated on first use and kept
+ * until mlens_destroy; tile rows are taken in passes that fit it) and a second
+ * kernel folds them per tile.  That keeps the GPU full when a grid has few tiles
+ * for its star count.  split = 1 never splits; 0 (the default) chooses per call
+ * from the number of tiles, the SM count and the star count (at least 2048
+ * stars per slice).  The sum's order depends on the split, so beta may differ in
+ * its last bits between splits (never by more than the error bar); a given split
+ * is deterministic.  Errors: MLENS_ERR_ARG; MLENS_ERR_NOMEM if the workspace
+ * cannot be allocated (at the shoot call).
  */
 int mlens_set_star_split(mlens_ctx *ctx, int32_t split);
 

@@ -122,6 +122,9 @@ int read_stats(unsigned long long *d_stats, uint64_t total, mlens_stats *st, cud
 // Ray rows per tile of the FP32 kernels (the FP64 kernel's 4-row blocks divide it).
 int tile_rows_of(const mlens_ctx *ctx) { return 8 * ctx->pairs_per_thread; }
 
+// The global split's partials per pass (tile rows are taken in passes that fit).
+constexpr size_t kGsplitBytes = size_t(256) << 20;
+
 // CTAs per tile for the FP32 re-centred kernel: the split star sum runs with the
 // default stage and MUFU reciprocals only.
 int effective_split(const mlens_ctx *ctx, const RayGrid &r)
@@ -168,13 +171,29 @@ int shoot_impl(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid *src, ui
     const int split = effective_split(ctx, a.rays);
     const int th = tile_rows_of(ctx);  // divides MLENS_ROW_ALIGN
     if (row1 > row0) {
-        if (ctx->precision == MLENS_PREC_FP64)
+        const int ty0 = row0 / th, ty1 = (row1 + th - 1) / th;
+        if (ctx->precision == MLENS_PREC_FP64) {
             e = launch_shoot_fp64(a, s, row0, row1);
-        else if (split > 1)
-            e = launch_shoot_split(a, ctx->pairs_per_thread, split, s, row0 / th, (row1 + th - 1) / th);
-        else
+        } else if (split > kMaxClusterSplit) {
+            // partials of up to kGsplitBytes per pass (at least one tile row), in a
+            // context workspace grown on demand
+            const int rpp = std::min(gsplit_rows_per_pass(a.rays, ctx->pairs_per_thread, split, kGsplitBytes),
+                                     ty1 - ty0);
+            const size_t need = gsplit_part_bytes(a.rays, ctx->pairs_per_thread, split, rpp);
+            if (ctx->gpart_bytes < need) {
+                if (ctx->d_gpart) dfree(ctx->d_gpart);
+                ctx->d_gpart = nullptr;
+                ctx->gpart_bytes = 0;
+                MLENS_CUDA(dmalloc(&ctx->d_gpart, need), "cudaMalloc(split partials)");
+                ctx->gpart_bytes = need;
+            }
+            e = launch_shoot_gsplit(a, ctx->pairs_per_thread, split, ctx->d_gpart, rpp, s, ty0, ty1);
+        } else if (split > 1) {
+            e = launch_shoot_split(a, ctx->pairs_per_thread, split, s, ty0, ty1);
+        } else {
             e = launch_shoot_fp32(a, ctx->pairs_per_thread, ctx->precision == MLENS_PREC_FP32_NAIVE, s,
-                                  ctx->star_stage, ctx->fma_pairs, row0 / th, (row1 + th - 1) / th);
+                                  ctx->star_stage, ctx->fma_pairs, ty0, ty1);
+        }
     }
     if (e != cudaSuccess) return cuda_fail(e, "shoot kernel launch");
     if (stats) return read_stats(ctx->d_stats, (uint64_t)rays->nx * (uint64_t)(row1 - row0), stats, s);
@@ -444,8 +463,8 @@ int mlens_set_tuning(mlens_ctx *ctx, int32_t rays_per_thread, int32_t star_stage
 int mlens_set_star_split(mlens_ctx *ctx, int32_t split)
 {
     if (!ctx) return fail(MLENS_ERR_ARG, "context is NULL");
-    if (split != 0 && split != 1 && split != 2 && split != 4 && split != 8)
-        return fail(MLENS_ERR_ARG, "split must be 0 (automatic), 1, 2, 4 or 8");
+    if (split < 0 || split > kMaxSplit)
+        return fail(MLENS_ERR_ARG, "split must be 0 (automatic) or 1 .. 4096");
     ctx->star_split = split;
     return MLENS_OK;
 }
@@ -527,6 +546,7 @@ void mlens_destroy(mlens_ctx *ctx)
     mlens_free_far_field(ctx);
     if (ctx->d_stars) dfree(ctx->d_stars);
     if (ctx->d_stats) dfree(ctx->d_stats);
+    if (ctx->d_gpart) dfree(ctx->d_gpart);
     if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
     delete ctx;
 }

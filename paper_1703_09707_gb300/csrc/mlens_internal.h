@@ -60,6 +60,8 @@ struct ShootArgs {
     uint32_t *counts;
     unsigned long long *stats;  // [binned, out, nan]
     void *beta_out;         // nullable: float4 pairs or double2 (FP64)
+    float4 *gpart;          // global split: 2 NP float4 per thread per (tile, slice) (launch_shoot_gsplit)
+    int gslices;            // global split: slices per tile
 };
 
 struct BinArgs {
@@ -105,6 +107,17 @@ constexpr int64_t kMinSplitStars = 2048;
 cudaError_t launch_shoot_split(const ShootArgs &a, int pairs_per_thread, int split, cudaStream_t s, int ty0 = 0,
                                int ty1 = -1);
 int auto_star_split(const RayGrid &r, int pairs_per_thread, int64_t nstars, int nsm);
+// The split star sum through global memory (splits above kMaxClusterSplit): each of
+// `split` CTAs per tile sums one slice of the stars and stores its partials in
+// `part` (a workspace of gsplit_part_bytes); a second kernel folds them in slice
+// order and bins.  Tile rows go in passes of rows_per_pass (gsplit_rows_per_pass for
+// a workspace of `bytes`).
+constexpr int kMaxClusterSplit = 8;
+constexpr int kMaxSplit = 4096;
+size_t gsplit_part_bytes(const RayGrid &r, int pairs_per_thread, int split, int tile_rows_per_pass);
+int gsplit_rows_per_pass(const RayGrid &r, int pairs_per_thread, int split, size_t bytes);
+cudaError_t launch_shoot_gsplit(const ShootArgs &a, int pairs_per_thread, int split, float4 *part, int rows_per_pass,
+                                cudaStream_t s, int ty0 = 0, int ty1 = -1);
 // Tiles of a list (tile = by * tiles_x + bx; 8 rays per thread), one cluster of
 // `split` CTAs per tile; fallback_star_split is the split used for the learned
 // far field's fallback tiles: the largest of 8, 4, 2 leaving kMinSplitStars
@@ -151,7 +164,9 @@ struct mlens_ctx {
     int pairs_per_thread = 4;
     int star_stage = 256;
     int fma_pairs = 0;
-    int star_split = 0;     // 0 = automatic, else 1, 2, 4 or 8 CTAs per tile
+    int star_split = 0;     // 0 = automatic, else CTAs per tile (1 .. 8: clusters; above: through global memory)
+    float4 *d_gpart = nullptr;  // the global split's partials (grown on demand)
+    size_t gpart_bytes = 0;
     int nsm = 0;            // SMs of the context's device
     FarState *ff = nullptr;
 };

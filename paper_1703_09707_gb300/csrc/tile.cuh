@@ -130,11 +130,20 @@ __device__ __forceinline__ float2 rcp_nr2(float2 x)
 // LOM: how the tile learns whether the ray offsets need low parts: 0 = from the grid
 // at run time (RayGrid lo, both loops compiled), 1 = never, 2 = always (callers
 // that have chosen already).
-template <int NP, int SC, bool NAIVE, int NRP = 0, int SPLIT = 1, int LOM = 0>
+//
+// GS (re-centred FP32 only, SPLIT = 1): the split star sum through global memory.
+// GS = 1: the CTA sums slice `gslice` of a.gslices consecutive 32-aligned slices of
+// the stars (the same slices as a cluster split of that many CTAs) and stores its
+// partials (S, C) as 2 NP float4 per thread at a.gpart, block gtile * a.gslices +
+// gslice, then returns.  GS = 2: the CTA sums no stars; it takes slice 0's partials
+// as its own, folds the others in slice order (two Kahan steps each, S_r then -C_r,
+// as the cluster fold does) and goes on to beta and binning.
+template <int NP, int SC, bool NAIVE, int NRP = 0, int SPLIT = 1, int LOM = 0, int GS = 0>
 __device__ __forceinline__ void shoot_tile(const ShootArgs &a, int bx, int by, ShootSmem<SC> &sm, TileShared &ts,
-                                           float4 *part = nullptr)
+                                           float4 *part = nullptr, int64_t gtile = 0, int gslice = 0)
 {
     static_assert(SPLIT == 1 || !NAIVE, "the split sum is for the re-centred kernel");
+    static_assert(GS == 0 || (!NAIVE && SPLIT == 1), "the global split is for the re-centred kernel");
     constexpr int kTileY = tile_rows(NP);
     constexpr int kLoads = (SC + kThreads - 1) / kThreads;
     const int tid = threadIdx.x;
@@ -239,6 +248,13 @@ __device__ __forceinline__ void shoot_tile(const ShootArgs &a, int bx, int by, S
         stars += s0;
         nst = min(chunk, nst - s0);
     }
+    if (GS == 1) {
+        const int64_t chunk = ((nst + a.gslices - 1) / a.gslices + kKahan - 1) / kKahan * kKahan;
+        const int64_t s0 = min(nst, (int64_t)gslice * chunk);
+        stars += s0;
+        nst = min(chunk, nst - s0);
+    }
+    if (GS == 2) nst = 0;
     const int nstage = (int)((nst + SC - 1) / SC);
     float4 nxt[kLoads];
     auto stage_load = [&](int s) {
@@ -317,6 +333,39 @@ __device__ __forceinline__ void shoot_tile(const ShootArgs &a, int bx, int by, S
             chunks(std::false_type{});
         if (s + 1 < nstage) stage_store(buf ^ 1);
         __syncthreads();
+    }
+
+    if constexpr (GS == 1) {
+        float4 *dst = a.gpart + (gtile * a.gslices + gslice) * (int64_t)(2 * NP * kThreads);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            dst[(2 * p) * kThreads + tid] = make_float4(Sx[p].x, Sx[p].y, Sy[p].x, Sy[p].y);
+            dst[(2 * p + 1) * kThreads + tid] = make_float4(Cx[p].x, Cx[p].y, Cy[p].x, Cy[p].y);
+        }
+        return;
+    }
+    if constexpr (GS == 2) {
+        const float4 *src = a.gpart + gtile * a.gslices * (int64_t)(2 * NP * kThreads);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const float4 s0 = src[(2 * p) * kThreads + tid], c0 = src[(2 * p + 1) * kThreads + tid];
+            Sx[p] = f2(s0.x, s0.y);
+            Sy[p] = f2(s0.z, s0.w);
+            Cx[p] = f2(c0.x, c0.y);
+            Cy[p] = f2(c0.z, c0.w);
+        }
+#pragma unroll 1
+        for (int r = 1; r < a.gslices; ++r) {
+            const float4 *rp = src + (int64_t)r * (2 * NP * kThreads);
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const float4 sr = rp[(2 * p) * kThreads + tid], cr = rp[(2 * p + 1) * kThreads + tid];
+                kahan2(Sx[p], Cx[p], f2(sr.x, sr.y));
+                kahan2(Sy[p], Cy[p], f2(sr.z, sr.w));
+                kahan2(Sx[p], Cx[p], f2(-cr.x, -cr.y));
+                kahan2(Sy[p], Cy[p], f2(-cr.z, -cr.w));
+            }
+        }
     }
 
     if constexpr (SPLIT > 1) {

@@ -1,7 +1,8 @@
 """mlens_shoot_rows, one process's part of a map shot by several (Section 2.2's MPI
 tasks): bands of ray rows on tile boundaries give exactly the rows of the whole-grid
 shot (beta bit for bit) and their maps add up to the whole map bit for bit, in every
-precision, with the star sum split over clusters, and on a ragged grid.  The sum over
+precision, with the star sum split over clusters or through global memory, and on a
+ragged grid.  The sum over
 processes itself (an all-reduce of the maps) is tested with gloo ranks on the CPU."""
 import numpy as np
 import pytest
@@ -31,6 +32,7 @@ CASES = [
     ("paper", 1 / 8, M.MLENS_PREC_FP32_NAIVE, None, 4),
     ("paper", 1 / 16, M.MLENS_PREC_FP64, None, 3),
     ("paper", 1 / 8, M.MLENS_PREC_FP32, 4, 5),      # star sum split over 4-CTA clusters
+    ("paper", 1 / 8, M.MLENS_PREC_FP32, 24, 3),     # ... over 24 CTAs through global memory
     ("tiny", 0.333, M.MLENS_PREC_FP32, None, 4),     # 333 x 333: the last band is ragged
 ]
 
