@@ -80,6 +80,8 @@ __global__ void __launch_bounds__(kThr) k_gauss_rows(const uint32_t *__restrict_
             const float4 *wq = sm4;  // (w_2n, w_2n, w_2n+1, w_2n+1)
             float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
             float2 x0 = b[0], x1 = b[P], x2 = b[2 * P];
+            // (unrolled so that the next steps' loads issue ahead of this step's FFMA2s)
+#pragma unroll 8
             for (int m = 0; m < Kp / 4; ++m) {
                 const float4 qa = wq[2 * m], qb = wq[2 * m + 1];
                 const float2 w0 = make_float2(qa.x, qa.y), w1 = make_float2(qa.z, qa.w);
@@ -153,6 +155,7 @@ __global__ void __launch_bounds__(kThr) k_gauss_cols(const float *__restrict__ i
             for (int q = 0; q < 8; ++q) a[q] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int q = 0; q < 7; ++q) x[q] = T[q * S];
+#pragma unroll 4
             for (int k = 0; k < Kp; k += 4) {
                 const float4 qa = sm4[k >> 1], qb = sm4[(k >> 1) + 1];
                 const float2 w0 = make_float2(qa.x, qa.y), w1 = make_float2(qa.z, qa.w);
