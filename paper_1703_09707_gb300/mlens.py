@@ -275,7 +275,7 @@ def mlens_set_tuning(ctx: Ctx, rays_per_thread: int, star_stage: int = 0, fma_pa
 
 
 def mlens_set_star_split(ctx: Ctx, split: int):
-    """0 = automatic, 1 = never, 2/4/8 CTAs per tile."""
+    """0 = automatic, 1 = never, 2 .. 8 CTAs per tile in a cluster, 9 .. 4096 through global memory."""
     _check(load().mlens_set_star_split(ctx.handle, int(split)))
 
 
