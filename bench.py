@@ -45,6 +45,22 @@ import workloads as W  # noqa: E402
 METRIC = "ray-star interactions/s (direct-sum deflection + binning, one map per step)"
 N_SM_GB300 = 152
 MUFU_RCP_PER_SM_CLK = 16  # MUFU.RCP issue rate per SM per clock (one reciprocal per interaction)
+# fma_pairs = 1 takes 10 of every 128 reciprocals from Newton-Raphson on the FMA pipe
+FMA_RCP_SHARE = 10.0 / 128.0
+
+
+def interaction_bound(fma_pairs: int):
+    """(interactions per SM per clock, basis) of the direct sum's binding pipe.  Every
+    interaction needs one reciprocal: from the MUFU unit (16 per SM per clock), or for
+    the share FMA_RCP_SHARE (fma_pairs = 1) from three Newton-Raphson steps on the
+    FMA pipe.  The FMA pipe (128 lane-ops per SM per clock) carries ~5.5 lane-ops per
+    interaction plus ~6.5 per Newton reciprocal: 21 interactions per clock at that
+    share, so MUFU still binds, at 16 / (1 - share) = 17.36."""
+    if fma_pairs:
+        r = MUFU_RCP_PER_SM_CLK / (1.0 - FMA_RCP_SHARE)
+        return r, (f"MUFU.RCP {MUFU_RCP_PER_SM_CLK}/SM/clk for the {100 * (1 - FMA_RCP_SHARE):.1f} % of interactions "
+                   f"whose reciprocal it forms ({r:.2f} interactions/SM/clk; the FMA pipe allows ~21)")
+    return float(MUFU_RCP_PER_SM_CLK), f"MUFU.RCP {MUFU_RCP_PER_SM_CLK}/SM/clk (one reciprocal per interaction)"
 SM_MAX_MHZ = 2070.0
 L2_FLUSH_BYTES = 256 << 20
 
@@ -59,8 +75,8 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_naive", "fp64"])
     ap.add_argument("--rays-per-thread", type=int, default=8, choices=[4, 8])
     ap.add_argument("--star-stage", type=int, default=256, choices=[128, 256, 512])
-    ap.add_argument("--fma-pairs", type=int, default=0, choices=[0, 1],
-                    help="ray pairs per thread whose reciprocal runs on the FMA pipe (Newton-Raphson)")
+    ap.add_argument("--fma-pairs", type=int, default=1, choices=[0, 1],
+                    help="1: a share (7.8 %%) of the reciprocals from Newton-Raphson on the FMA pipe; 0: MUFU only")
     ap.add_argument("--rays-scale", type=float, default=1.0,
                     help="shrink the ray grid per axis (same field, boxes and map) for profiling runs")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
@@ -767,17 +783,18 @@ def run_mine(args):
     # ----------------------------------------------------------------- roofline
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
-    peak = n_sm * MUFU_RCP_PER_SM_CLK * SM_MAX_MHZ * 1e6
+    per_clk, basis = interaction_bound(args.fma_pairs)
+    peak = n_sm * per_clk * SM_MAX_MHZ * 1e6
     achieved = n_inter / (kernel_ms / 1e3)
     key = f"shoot_fp32_{args.workload}_rpt{args.rays_per_thread}_fma{args.fma_pairs}"
     traffic, _ = profile_traffic(key) if args.precision != "fp64" else (None, None)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "interactions/s", "frac": achieved / peak,
             "traffic": traffic,
-            "peak_basis": f"MUFU.RCP {MUFU_RCP_PER_SM_CLK}/SM/clk x {n_sm} SMs x {SM_MAX_MHZ:.0f} MHz (max SM clock)",
+            "peak_basis": f"{basis} x {n_sm} SMs x {SM_MAX_MHZ:.0f} MHz (max SM clock)",
             "kernel": "k_shoot_fp32" if args.precision != "fp64" else "k_fp64",
             "kernel_ms": kernel_ms}
     if clk and clk.get("sm_mhz"):
-        roof["frac_at_measured_clock"] = achieved / (n_sm * MUFU_RCP_PER_SM_CLK * clk["sm_mhz"] * 1e6)
+        roof["frac_at_measured_clock"] = achieved / (n_sm * per_clk * clk["sm_mhz"] * 1e6)
 
     line = {
         "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
@@ -805,7 +822,7 @@ def run_mine(args):
     if not args.no_extras and world == 1 and args.workload == "paper" and args.rays_scale == 1.0:
         if "batched" in extras:
             bt = bench_batched(M, torch, max(2, min(args.steps, 5)), 2, flush)
-            peak_b = n_sm * MUFU_RCP_PER_SM_CLK * SM_MAX_MHZ * 1e6
+            peak_b = n_sm * interaction_bound(bt["tuned"]["fma_pairs"])[0] * SM_MAX_MHZ * 1e6
             bt["roofline_frac"] = bt["interactions_per_s"] / peak_b
             line["batched"] = bt
         if "binning" in extras:

@@ -105,19 +105,22 @@ int mlens_set_precision(mlens_ctx *ctx, int32_t precision);
  * mlens_set_tuning -- launch shape of the FP32 kernels for later calls on this
  * context: rays_per_thread in {4, 8} (tile 64 x 16 or 64 x 32 rays per CTA of
  * 256 threads), star_stage in {128, 256, 512} stars staged through shared
- * memory at a time (0 = 256), and fma_pairs in {0, 1}: how many of a thread's
- * ray pairs take their reciprocals from Newton-Raphson iterations on the FMA
- * pipe instead of the MUFU unit (which is the bound).  The stage size never
- * changes the arithmetic; the tile shape (it moves the tile centres) and the
- * reciprocal source change beta in its last bits (never by more than the error
- * bar).  A given setting is deterministic.  Defaults: 8, 256, 0.
+ * memory at a time (0 = 256), and fma_pairs in {0, 1}: 0 takes every
+ * reciprocal 1/r^2 from the MUFU unit (16 per SM per clock, the bound of the
+ * direct sum); 1 takes a share of them (a thread's first ray pair on every third
+ * star, 7.8 %) from Newton-Raphson iterations on the FMA pipe instead, which
+ * balances the two units (4.84e12 against 4.67e12 interactions/s on GB300).  The
+ * stage size never changes the arithmetic; the tile shape (it moves the tile
+ * centres) and the reciprocal source change beta in its last bits (never by
+ * more than the error bar).  A given setting is deterministic.  Defaults: 8,
+ * 256, 1.
  */
 int mlens_set_tuning(mlens_ctx *ctx, int32_t rays_per_thread, int32_t star_stage, int32_t fma_pairs);
 
 /*
  * mlens_set_star_split -- how many CTAs share one ray tile's star sum in the
- * FP32 re-centred kernel (MLENS_PREC_FP32 with the default 256-star stage and
- * fma_pairs = 0; other settings never split).  The paper's closing discussion
+ * FP32 re-centred kernel (MLENS_PREC_FP32 with the default 256-star stage, with
+ * either fma_pairs; other settings never split).  The paper's closing discussion
  * of very large star fields proposes splitting the bending-angle sum of one
  * image position over several threads; here each of `split` CTAs sums one of
  * `split` consecutive 32-star-aligned slices of the stars with the same
@@ -315,8 +318,9 @@ int mlens_magnification_scale(const mlens_grid *rays, const mlens_grid *src, dou
  * the device, and the only working memory is a fixed array compiled into the
  * library.
  * The paper has no counterpart; it is a deployment variant of the same FP32
- * kernel (MLENS_PREC_FP32, 8 rays per thread, no star split), so it produces the
- * same map as mlens_create + mlens_shoot (split 1) on the same float32 stars.
+ * kernel (MLENS_PREC_FP32, 8 rays per thread, 256-star stages, fma_pairs = 1, no
+ * star split: a context's default tuning), so it produces the same map as
+ * mlens_create + mlens_shoot (split 1) on the same float32 stars.
  *   stars_dev  n records float4 {x, y, m, unused} on the current device,
  *              16-byte aligned, caller-owned.  The values are not checked:
  *              non-finite entries give non-finite beta for the rays they touch.
@@ -366,7 +370,7 @@ typedef struct mlens_batch mlens_batch;
  *   flags                0 or MLENS_ACCUMULATE.
  * Contexts and maps must stay alive, and unchanged in size, while the batch exists.
  * Allocates about 300 bytes per field of device tables and one private stream.
- * Launch shape starts at 8 rays per thread and 256-star stages.
+ * Launch shape starts at 8 rays per thread, 256-star stages and fma_pairs = 1.
  */
 int mlens_batch_create(mlens_batch **out, mlens_ctx *const *ctxs, int32_t nfields, const mlens_grid *rays,
                        const mlens_grid *srcs, uint32_t *const *counts_dev, uint32_t flags);
@@ -476,7 +480,7 @@ int mlens_fit_far_field(mlens_ctx *ctx, const mlens_grid *rays, const mlens_fit_
  * `rays` (which must be the grid of the fit).  Near stars exact, far field from
  * the series and the network, flagged cells exact: their tiles run first as the
  * plain sum split over clusters of 8, 4 or 2 CTAs (the largest leaving 2048 stars
- * per slice; none below 4096 stars or with fma_pairs = 1), so they equal
+ * per slice; none below 4096 stars), so they equal
  * mlens_shoot with that mlens_set_star_split bit for bit; then one persistent
  * launch takes the learned tiles.
  * beta_dev as for mlens_shoot_beta (NULL to skip); other arguments as mlens_shoot.

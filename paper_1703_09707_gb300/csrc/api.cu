@@ -126,10 +126,10 @@ int tile_rows_of(const mlens_ctx *ctx) { return 8 * ctx->pairs_per_thread; }
 constexpr size_t kGsplitBytes = size_t(256) << 20;
 
 // CTAs per tile for the FP32 re-centred kernel: the split star sum runs with the
-// default stage and MUFU reciprocals only.
+// default stage (and either reciprocal split).
 int effective_split(const mlens_ctx *ctx, const RayGrid &r)
 {
-    if (ctx->precision != MLENS_PREC_FP32 || ctx->star_stage != kSplitStage || ctx->fma_pairs) return 1;
+    if (ctx->precision != MLENS_PREC_FP32 || ctx->star_stage != kSplitStage) return 1;
     if (ctx->star_split) return ctx->star_split;
     return auto_star_split(r, ctx->pairs_per_thread, ctx->n_pad, ctx->nsm);
 }
@@ -187,9 +187,9 @@ int shoot_impl(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid *src, ui
                 MLENS_CUDA(dmalloc(&ctx->d_gpart, need), "cudaMalloc(split partials)");
                 ctx->gpart_bytes = need;
             }
-            e = launch_shoot_gsplit(a, ctx->pairs_per_thread, split, ctx->d_gpart, rpp, s, ty0, ty1);
+            e = launch_shoot_gsplit(a, ctx->pairs_per_thread, split, ctx->d_gpart, rpp, s, ty0, ty1, ctx->fma_pairs);
         } else if (split > 1) {
-            e = launch_shoot_split(a, ctx->pairs_per_thread, split, s, ty0, ty1);
+            e = launch_shoot_split(a, ctx->pairs_per_thread, split, s, ty0, ty1, ctx->fma_pairs);
         } else {
             e = launch_shoot_fp32(a, ctx->pairs_per_thread, ctx->precision == MLENS_PREC_FP32_NAIVE, s,
                                   ctx->star_stage, ctx->fma_pairs, ty0, ty1);

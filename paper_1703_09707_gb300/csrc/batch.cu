@@ -40,7 +40,7 @@ struct mlens_batch {
     unsigned long long *d_stats = nullptr;  // 3 per field
     int pairs_per_thread = 4;
     int star_stage = 256;
-    int fma_pairs = 0;
+    int fma_pairs = kDefaultFmaPairs;
     int64_t total = 0;
     int grid = 0;
     cudaStream_t cap = nullptr;

@@ -515,9 +515,9 @@ int mlens_shoot_learned(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid
     // Fallback tiles (each a full plain tile over all stars) run first, each split
     // over a cluster of CTAs so that a few flagged cells do not set the map's
     // time; the persistent learned kernel then takes the learned tiles.
-    const int split = ctx->fma_pairs ? 1 : fallback_star_split(ctx->n_pad);
+    const int split = fallback_star_split(ctx->n_pad);
     if (split > 1 && nheavy > 0) {
-        FCUDA(launch_shoot_split_list(L.plain, items, nheavy, split, s), "fallback tiles launch");
+        FCUDA(launch_shoot_split_list(L.plain, items, nheavy, split, s, ctx->fma_pairs), "fallback tiles launch");
         L.items = items + nheavy;
         L.nitems = nitems - nheavy;
     }

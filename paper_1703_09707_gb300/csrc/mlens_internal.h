@@ -86,7 +86,8 @@ struct BatchLaunch {
 
 // launchers (defined in the .cu files)
 // pairs_per_thread in {2, 4} (4 or 8 rays per thread); stage in {128, 256, 512} stars
-// fma_pairs in {0, 1}: ray pairs per thread whose reciprocal runs on the FMA pipe
+// fma_pairs in {0, 1}: 1 takes a share of the reciprocals (pair 0 on every third
+// star, 7.8 %) from the FMA pipe, 0 every reciprocal from the MUFU unit
 // [ty0, ty1): the tile rows to shoot (tile_rows(pairs_per_thread) ray rows each;
 // ty1 < 0 = through the last)
 cudaError_t launch_shoot_fp32(const ShootArgs &a, int pairs_per_thread, bool naive, cudaStream_t s,
@@ -99,13 +100,13 @@ int64_t tiles_of(const RayGrid &r, int pairs_per_thread);
 cudaError_t launch_shoot_fp64(const ShootArgs &a, cudaStream_t s, int row0 = 0, int row1 = -1);
 cudaError_t launch_trace_fp64(const float4 *stars, int64_t nstars, const LensTerms &lens, const double2 *theta,
                               double2 *beta, int64_t k, cudaStream_t s);
-// Split star sum (re-centred FP32, 256-star stages, MUFU reciprocals): clusters
-// of `split` in {2, 4, 8} CTAs per tile.  auto_star_split picks the split for a
-// grid (1 = none) from the wave efficiency on `nsm` SMs.
+// Split star sum (shoot_split.cu; re-centred FP32, 256-star stages, either
+// reciprocal split): clusters of `split` in 2 .. 8 CTAs per tile.  auto_star_split
+// picks the split for a grid (1 = none) from the wave efficiency on `nsm` SMs.
 constexpr int kSplitStage = 256;
 constexpr int64_t kMinSplitStars = 2048;
-cudaError_t launch_shoot_split(const ShootArgs &a, int pairs_per_thread, int split, cudaStream_t s, int ty0 = 0,
-                               int ty1 = -1);
+cudaError_t launch_shoot_split(const ShootArgs &a, int pairs_per_thread, int split, cudaStream_t s, int ty0, int ty1,
+                               int fma_pairs);
 int auto_star_split(const RayGrid &r, int pairs_per_thread, int64_t nstars, int nsm);
 // The split star sum through global memory (splits above kMaxClusterSplit): each of
 // `split` CTAs per tile sums one slice of the stars and stores its partials in
@@ -113,16 +114,18 @@ int auto_star_split(const RayGrid &r, int pairs_per_thread, int64_t nstars, int 
 // order and bins.  Tile rows go in passes of rows_per_pass (gsplit_rows_per_pass for
 // a workspace of `bytes`).
 constexpr int kMaxClusterSplit = 8;
+constexpr int kDefaultFmaPairs = 1;  // the reciprocal split a context and the no-allocation entry start with
 constexpr int kMaxSplit = 4096;
 size_t gsplit_part_bytes(const RayGrid &r, int pairs_per_thread, int split, int tile_rows_per_pass);
 int gsplit_rows_per_pass(const RayGrid &r, int pairs_per_thread, int split, size_t bytes);
 cudaError_t launch_shoot_gsplit(const ShootArgs &a, int pairs_per_thread, int split, float4 *part, int rows_per_pass,
-                                cudaStream_t s, int ty0 = 0, int ty1 = -1);
+                                cudaStream_t s, int ty0, int ty1, int fma_pairs);
 // Tiles of a list (tile = by * tiles_x + bx; 8 rays per thread), one cluster of
 // `split` CTAs per tile; fallback_star_split is the split used for the learned
 // far field's fallback tiles: the largest of 8, 4, 2 leaving kMinSplitStars
 // stars per slice, else 1 (no split).
-cudaError_t launch_shoot_split_list(const ShootArgs &a, const int *tiles, int64_t ntiles, int split, cudaStream_t s);
+cudaError_t launch_shoot_split_list(const ShootArgs &a, const int *tiles, int64_t ntiles, int split, cudaStream_t s,
+                                    int fma_pairs);
 int fallback_star_split(int64_t nstars);
 cudaError_t launch_bin(const BinArgs &a, cudaStream_t s);
 
@@ -163,7 +166,7 @@ struct mlens_ctx {
     int precision = MLENS_PREC_FP32;
     int pairs_per_thread = 4;
     int star_stage = 256;
-    int fma_pairs = 0;
+    int fma_pairs = mlens::kDefaultFmaPairs;
     int star_split = 0;     // 0 = automatic, else CTAs per tile (1 .. 8: clusters; above: through global memory)
     float4 *d_gpart = nullptr;  // the global split's partials (grown on demand)
     size_t gpart_bytes = 0;

@@ -124,7 +124,8 @@ extern "C" int mlens_shoot_noalloc(const void *stars_dev, int64_t n, double kapp
     a.counts = counts_dev;
     a.stats = sc->stats;
     a.beta_out = nullptr;
-    if ((e = launch_shoot_fp32(a, 4, false, s, 256, 0)) != cudaSuccess) return cuda_error(e, "no-alloc shoot kernel launch");
+    if ((e = launch_shoot_fp32(a, 4, false, s, 256, kDefaultFmaPairs)) != cudaSuccess)
+        return cuda_error(e, "no-alloc shoot kernel launch");
     if (stats_host) {
         unsigned long long h[3];
         if ((e = cudaMemcpyAsync(h, sc->stats, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess)

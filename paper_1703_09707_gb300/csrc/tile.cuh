@@ -99,8 +99,8 @@ constexpr int tile_rows(int np) { return kGroups * 2 * np; }
 // relative error <= 5.1%) refined by three Newton-Raphson steps
 // y <- y + y (1 - x y), each squaring the relative error (5.1e-2 -> 2.6e-3 ->
 // 6.5e-6 -> 4e-11, below float32 resolution).  x = 0 gives a non-finite result,
-// as the hardware reciprocal does.  Used for some ray pairs so that the FMA pipe
-// takes part of the reciprocal load off the MUFU unit.
+// as the hardware reciprocal does.  Used for a share of the interactions so that
+// the FMA pipe takes part of the reciprocal load off the MUFU unit.
 constexpr int kRcpSeed = 0x7EF311C2;
 
 __device__ __forceinline__ float2 rcp_nr2(float2 x)
@@ -118,8 +118,12 @@ __device__ __forceinline__ float2 rcp_nr2(float2 x)
 
 // One tile (bx, by) of the ray grid of `a`, start to finish: prologue, star
 // stages, beta, binning, counters.  Every thread of the CTA must call it.
-// NRP of the NP ray pairs take their reciprocals from rcp_nr2 (FMA pipe), the
-// others from the MUFU unit.
+// NRP = 1: ray pair 0 takes its reciprocals from rcp_nr2 (FMA pipe) on every third
+// star of a 32-star chunk (stars 2, 5, .., 29: 10 of the 128 reciprocals a thread
+// forms per chunk, 7.8 %); all others come from the MUFU unit.  That share
+// balances the two pipes best on GB300 (measured: 4.84e12 interactions/s against
+// 4.67e12 with MUFU alone, 4.79e12 at 1/8 and 4.39e12 at 1/4 of the reciprocals).
+// NRP = 0: MUFU alone.
 //
 // SPLIT > 1 (re-centred FP32 only): the CTA is rank r of a cluster of SPLIT CTAs
 // that share the tile; it sums the r-th of SPLIT consecutive 32-aligned slices
@@ -307,7 +311,8 @@ __device__ __forceinline__ void shoot_tile(const ShootArgs &a, int bx, int by, S
                     for (int p = 0; p < NP; ++p) {
                         const float2 dy = LO ? __fadd2_rn(__fadd2_rn(ry[p], nyv), ryl[p]) : __fadd2_rn(ry[p], nyv);
                         const float2 r2 = __ffma2_rn(dy, dy, dx2);
-                        const float2 inv = p < NRP ? rcp_nr2(r2) : f2(rcp_approx(r2.x), rcp_approx(r2.y));
+                        const float2 inv = NRP > 0 && p == 0 && (k - k0) % 3 == 2 ? rcp_nr2(r2)
+                                                                                 : f2(rcp_approx(r2.x), rcp_approx(r2.y));
                         const float2 f = __fmul2_rn(m2, inv);
                         px[p] = __ffma2_rn(f, dx, px[p]);
                         py[p] = __ffma2_rn(f, dy, py[p]);

@@ -270,7 +270,7 @@ def mlens_set_precision(ctx: Ctx, precision):
     _check(load().mlens_set_precision(ctx.handle, int(precision)))
 
 
-def mlens_set_tuning(ctx: Ctx, rays_per_thread: int, star_stage: int = 0, fma_pairs: int = 0):
+def mlens_set_tuning(ctx: Ctx, rays_per_thread: int, star_stage: int = 0, fma_pairs: int = 1):
     _check(load().mlens_set_tuning(ctx.handle, int(rays_per_thread), int(star_stage), int(fma_pairs)))
 
 
@@ -430,7 +430,7 @@ def mlens_batch_create(ctxs, rays, srcs, counts, flags: int = 0) -> Batch:
     return Batch(h.value, (list(ctxs), list(counts)))
 
 
-def mlens_batch_set_tuning(b: Batch, rays_per_thread: int, star_stage: int = 0, fma_pairs: int = 0):
+def mlens_batch_set_tuning(b: Batch, rays_per_thread: int, star_stage: int = 0, fma_pairs: int = 1):
     _check(load().mlens_batch_set_tuning(b.handle, int(rays_per_thread), int(star_stage), int(fma_pairs)))
 
 

@@ -152,13 +152,14 @@ def test_automatic_split_policy():
         g = W.Grid(rays.x0, rays.x1, rays.y0, rays.y1, int(rays.nx * scale), int(rays.ny * scale))
         tiles = math.ceil(g.nx / 64) * math.ceil(g.ny / 32)
         assert M.mlens_star_split_for(ctx, g) == _expected_auto(tiles, n_pad, nsm), scale
-    # only the re-centred kernel with its default stage and MUFU reciprocals splits
+    # only the re-centred kernel with its default stage splits (with either reciprocal source)
     small = W.Grid(rays.x0, rays.x1, rays.y0, rays.y1, 256, 256)
     assert M.mlens_star_split_for(ctx, small) > 1
     M.mlens_set_tuning(ctx, 8, 512)
     assert M.mlens_star_split_for(ctx, small) == 1
-    M.mlens_set_tuning(ctx, 8, 256, 1)
-    assert M.mlens_star_split_for(ctx, small) == 1
+    for fma in (0, 1):
+        M.mlens_set_tuning(ctx, 8, 256, fma)
+        assert M.mlens_star_split_for(ctx, small) > 1
     M.mlens_set_tuning(ctx, 8)
     M.mlens_set_precision(ctx, M.MLENS_PREC_FP32_NAIVE)
     assert M.mlens_star_split_for(ctx, small) == 1
