@@ -602,7 +602,7 @@ def bench_fit(M, torch, fit_stars: int, tol: float, order: int, peak_fp32_lane_o
     theta_E) with `fit_stars` stars at the same density (10^6: the learned section's
     field): its time split into the series coefficients, the training and the
     validation, the training step time, and the coefficient kernel's pair rate
-    against its FP32 bound (about 254 FP32 lane operations per (cell, far star)
+    against its FP32 bound (about 249 FP32 lane operations per (cell, far star)
     pair)."""
     wl = W.config("learned")
     f, rays = wl.fields[0], wl.rays[0]
@@ -616,7 +616,7 @@ def bench_fit(M, torch, fit_stars: int, tol: float, order: int, peak_fp32_lane_o
     ctx.close()
     pairs = rep["cells"] * f.n  # (cell, star) pairs; the near stars (~1e-5 of them) are counted too
     coef_s = rep["seconds_coefficients"]
-    lane_ops = 254.0
+    lane_ops = 249.0
     return {"stars": f.n, "cells": rep["cells"], "fit_s": fit_s,
             "seconds": {"coefficients": coef_s, "train": rep["seconds_train"], "validate": rep["seconds_validate"]},
             "train_steps": rep["train_steps"], "train_step_us": 1e6 * rep["seconds_train"] / max(rep["train_steps"], 1),

@@ -112,11 +112,11 @@ cudaError_t ff_build_csr(const float4 *stars, int64_t n, const CellGrid &cg, int
 // ===================================================== series coefficients
 // One warp per ray cell, eight cells per CTA sharing each staged chunk of stars.
 // b_0 (the far field's value at the centre, ~30 theta_E, needed to ~1e-9) is
-// formed per star in double-float arithmetic (below) and accumulated in FP64 once
-// per stage.  For p >= 1 the terms -(m/s) w^(p+1) are formed in FP32 (relative
+// formed per star in double-float arithmetic (below) and accumulated in
+// double-float.  For p >= 1 the terms -(m/s) w^(p+1) are formed in FP32 (relative
 // error ~p 6e-8 per term, far below what the series needs), summed per lane in
-// FP32 over a stage and accumulated in FP64, so the sums keep FP64 accuracy while
-// the per-term work runs on the FP32 pipe.
+// FP32 over a stage and accumulated in double-float, so the sums keep ~48 bits while
+// all the work runs on the FP32 pipe.
 // Double-float arithmetic (an unevaluated pair of floats, ~48 significant bits) on
 // the FP32 pipe: Knuth's TwoSum, the FMA form of Dekker's TwoProduct, and one
 // Newton step for the reciprocal.  Used for the order-0 far-field term, which
@@ -149,12 +149,36 @@ __device__ __forceinline__ DF df_mulf(DF a, float b)
     const float p = __fmul_rn(a.h, b), e = __fmaf_rn(a.h, b, -p);
     return df_norm(p, __fmaf_rn(a.l, b, e));
 }
+// The order-0 term's steps, shortened for their operands:
+// x^2 + y^2: the two high products' sum by TwoSum; their rounding errors (exact, by
+// FMA) and the cross terms 2 x_h x_l, 2 y_h y_l go into the low part (x_l^2 and
+// y_l^2, 2^-48 of the result, are left out).
+__device__ __forceinline__ DF df_sq_sum(DF x, DF y)
+{
+    const float px = __fmul_rn(x.h, x.h), ex = __fmaf_rn(x.h, x.h, -px);
+    const float py = __fmul_rn(y.h, y.h), ey = __fmaf_rn(y.h, y.h, -py);
+    const DF s = df_two_sum(px, py);
+    const float lx = __fmaf_rn(__fadd_rn(x.h, x.h), x.l, ex), ly = __fmaf_rn(__fadd_rn(y.h, y.h), y.l, ey);
+    return df_norm(s.h, __fadd_rn(s.l, __fadd_rn(lx, ly)));
+}
+// 1 / a: the hardware reciprocal y (relative error ~2^-23) and one Newton step,
+// y (1 + r) with r = 1 - a y; 1 - (a y)_h is exact (Sterbenz: (a y)_h is within
+// 2^-22 of 1), so r costs two subtractions.  Relative error ~r^2 + 2^-46, below
+// 2^-43.
 __device__ __forceinline__ DF df_rcp(DF a)
 {
-    const float y = __frcp_rn(a.h);           // relative error <= 2^-24
-    const DF ay = df_mulf(a, y);              // ~1
-    const DF r = df_add({1.0f, 0.0f}, {-ay.h, -ay.l});  // 1 - a y, ~2^-24
-    return df_norm(y, __fmul_rn(y, r.h));     // y (1 + r): relative error below 2^-45
+    const float y = rcp_approx(a.h);
+    const DF ay = df_mulf(a, y);
+    const float r = __fsub_rn(__fsub_rn(1.0f, ay.h), ay.l);
+    return df_norm(y, __fmul_rn(y, r));
+}
+// Compensated running sum of double-float terms: s.h collects the terms' high
+// parts with TwoSum, s.l their low parts and the TwoSum errors (normalised with
+// df_norm when read).
+__device__ __forceinline__ void df_acc(DF &s, DF t)
+{
+    const DF u = df_two_sum(s.h, t.h);
+    s = {u.h, __fadd_rn(s.l, __fadd_rn(u.l, t.l))};
 }
 
 __device__ __forceinline__ float2 f2c(float x, float y) { return make_float2(x, y); }
@@ -170,7 +194,7 @@ __device__ __forceinline__ FarTerm far_term(float4 q, float zxh, float zxl, floa
     FarTerm t;
     const DF dx = df_add(df_two_sum(q.x, -zxh), {-zxl, 0.0f});
     const DF dy = df_add(df_two_sum(q.y, -zyh), {-zyl, 0.0f});
-    const DF inv = df_rcp(df_add(df_mul(dx, dx), df_mul(dy, dy)));
+    const DF inv = df_rcp(df_sq_sum(dx, dy));
     const DF mi = df_mulf(inv, q.z);
     t.tr = df_mul(mi, dx);
     t.ti = df_mul(mi, dy);
@@ -276,10 +300,10 @@ __global__ void __launch_bounds__(256, 2) k_coeffs(const float4 *stars, const in
             const bool near_b = abs(cb.x - ex) <= 1 && abs(cb.y - ey) <= 1;
             const FarTerm A = far_term(near_a ? pad : sq[ka], zxh, zxl, zyh, zyl, fscale);
             const FarTerm B = far_term(near_b ? pad : sq[kb], zxh, zxl, zyh, zyl, fscale);
-            sr = df_add(sr, {-A.tr.h, -A.tr.l});
-            si = df_add(si, A.ti);
-            sr = df_add(sr, {-B.tr.h, -B.tr.l});
-            si = df_add(si, B.ti);
+            df_acc(sr, {-A.tr.h, -A.tr.l});
+            df_acc(si, A.ti);
+            df_acc(sr, {-B.tr.h, -B.tr.l});
+            df_acc(si, B.ti);
             float2 fr = f2c(-A.tr.h, -B.tr.h), fi = f2c(A.ti.h, B.ti.h);
             const float2 wr = f2c(A.wr, B.wr), wi = f2c(A.wi, B.wi), nwi = f2c(-A.wi, -B.wi);
 #pragma unroll
@@ -291,8 +315,8 @@ __global__ void __launch_bounds__(256, 2) k_coeffs(const float4 *stars, const in
                 pi[p] += __fadd_rn(fi.x, fi.y);
             }
         }
-        b0r = df_add(b0r, sr);
-        b0i = df_add(b0i, si);
+        b0r = df_add(b0r, df_norm(sr.h, sr.l));
+        b0i = df_add(b0i, df_norm(si.h, si.l));
         // the stage's sums over the warp, scattered: afterwards lane q holds the sum of
         // order q (q = 1 .. kPtMax) of the stage (reduce-scatter, 31 shuffles per part)
         const float r = warp_scatter_orders(pr), i = warp_scatter_orders(pi);

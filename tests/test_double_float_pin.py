@@ -1,11 +1,12 @@
 """CPU pin of the double-float arithmetic the far-field coefficient kernel uses for the
-order-0 term (farfield.cu: df_two_sum, df_add, df_mul, df_mulf, df_rcp): the same
-float32 operation sequences, evaluated with IEEE float32 arithmetic in numpy, against
-float64 results.  The FMAs are the device's: a*b + c rounded once to float32 (the
+order-0 term (farfield.cu: df_two_sum, df_add, df_mul, df_mulf, df_sq_sum, df_rcp,
+df_acc): the same float32 operation sequences, evaluated with IEEE float32 arithmetic
+in numpy, against float64 results.  The FMAs are the device's: a*b + c rounded once to float32 (the
 product is exact in float64; the sum is carried exactly as a float64 pair and rounded
 once, checked against exact rational arithmetic).  Pins the accuracy the design relies
-on: TwoSum exact, a product to ~2^-44, the reciprocal below 2^-45 (one Newton step on
-the correctly rounded float reciprocal)."""
+on: TwoSum exact, a product to ~2^-44, the reciprocal below 2^-45 from the correctly
+rounded float reciprocal and below 2^-43 from any float within one ulp of it (the
+hardware approximation the kernel starts from), one Newton step either way."""
 from fractions import Fraction
 
 import numpy as np
@@ -60,11 +61,29 @@ def df_mulf(a, b):
     return df_norm(p, fma32(a[1], b, e))
 
 
-def df_rcp(a):
-    y = (1.0 / a[0].astype(np.float64)).astype(f32)  # the correctly rounded float reciprocal
+def df_sq_sum(x, y):
+    """x^2 + y^2 as the kernel forms it (df_sq_sum)."""
+    px = (x[0] * x[0]).astype(f32)
+    ex = fma32(x[0], x[0], -px)
+    py = (y[0] * y[0]).astype(f32)
+    ey = fma32(y[0], y[0], -py)
+    sh, sl = two_sum(px, py)
+    lx = fma32((x[0] + x[0]).astype(f32), x[1], ex)
+    ly = fma32((y[0] + y[0]).astype(f32), y[1], ey)
+    return df_norm(sh, (sl + (lx + ly).astype(f32)).astype(f32))
+
+
+def df_rcp_from(a, y):
+    """1/a as the kernel forms it from a float approximation y of 1/a_h (df_rcp)."""
     ay = df_mulf(a, y)
-    r = df_add((np.ones_like(y), np.zeros_like(y)), (-ay[0], -ay[1]))
-    return df_norm(y, (y * r[0]).astype(f32))
+    r = ((np.ones_like(y) - ay[0]).astype(f32) - ay[1]).astype(f32)
+    return df_norm(y, (y * r).astype(f32))
+
+
+def df_acc(s, t):
+    """The kernel's compensated running sum step (df_acc)."""
+    uh, ul = two_sum(s[0], t[0])
+    return uh, (s[1] + (ul + t[1]).astype(f32)).astype(f32)
 
 
 def value(a):
@@ -92,7 +111,7 @@ def test_double_float_product_and_reciprocal_accuracy():
     prod = df_mul(a, b)
     rel = np.abs(value(prod) - value(a) * value(b)) / np.abs(value(a) * value(b))
     assert rel.max() < 2.0 ** -44
-    rcp = df_rcp(a)
+    rcp = df_rcp_from(a, (1.0 / a[0].astype(np.float64)).astype(f32))  # the correctly rounded start
     rel = np.abs(value(rcp) - 1.0 / value(a)) * np.abs(value(a))
     assert rel.max() < 2.0 ** -45
 
@@ -128,3 +147,37 @@ def test_fma32_rounds_once():
     # the midpoint cases do occur, and the double-rounded evaluation misses some of them
     naive = (A.astype(np.float64) * B + Cc).astype(f32)
     assert np.any(naive.view(np.uint32) != want.view(np.uint32))
+
+
+def test_order0_steps_accuracy():
+    """The order-0 term's shortened steps: x^2 + y^2 to 2^-45 (x_l^2 and y_l^2 are left
+    out), the reciprocal from any float within one ulp of 1/a_h (the hardware
+    approximation's bound) to 2^-43 after one Newton step, and the stage sums as the
+    kernel forms them (16 double-float terms per lane and stage by the compensated
+    step, normalised, then added to the running total) to 2^-44 of the sum of the
+    terms' magnitudes over 64 stages."""
+    rng = np.random.default_rng(3)
+    x, y = pairs(rng, 200_000), pairs(rng, 200_000)
+    q = df_sq_sum(x, y)
+    want = value(x) ** 2 + value(y) ** 2
+    assert (np.abs(value(q) - want) / want).max() < 2.0 ** -45
+    a = pairs(rng, 200_000)
+    a = (np.abs(a[0]), np.where(a[0] < 0, -a[1], a[1]).astype(f32))  # r^2 > 0
+    y0 = (1.0 / a[0].astype(np.float64)).astype(f32)
+    for y in (y0, np.nextafter(y0, f32(np.inf)), np.nextafter(y0, f32(0))):
+        rcp = df_rcp_from(a, y)
+        rel = np.abs(value(rcp) - 1.0 / value(a)) * value(a)
+        assert rel.max() < 2.0 ** -43
+    stages, per, lanes = 64, 16, 256
+    terms = pairs(rng, stages * per * lanes)
+    th, tl = terms[0].reshape(stages, per, lanes), terms[1].reshape(stages, per, lanes)
+    total = (np.zeros(lanes, dtype=f32), np.zeros(lanes, dtype=f32))
+    for g in range(stages):
+        s = (np.zeros(lanes, dtype=f32), np.zeros(lanes, dtype=f32))
+        for k in range(per):
+            s = df_acc(s, (th[g, k], tl[g, k]))
+        total = df_add(total, df_norm(s[0], s[1]))
+    exact = th.astype(np.float64).sum((0, 1)) + tl.astype(np.float64).sum((0, 1))
+    mag = np.abs(th.astype(np.float64)).sum((0, 1))
+    got = value(total)
+    assert (np.abs(got - exact) / mag).max() < 2.0 ** -44
