@@ -793,6 +793,9 @@ def run_mine(args):
             "peak_basis": f"{basis} x {n_sm} SMs x {SM_MAX_MHZ:.0f} MHz (max SM clock)",
             "kernel": "k_shoot_fp32" if args.precision != "fp64" else "k_fp64",
             "kernel_ms": kernel_ms}
+    if args.fma_pairs:
+        # context: the same rate against MUFU.RCP alone (every reciprocal on MUFU)
+        roof["frac_of_mufu_only_bound"] = achieved / (n_sm * MUFU_RCP_PER_SM_CLK * SM_MAX_MHZ * 1e6)
     if clk and clk.get("sm_mhz"):
         roof["frac_at_measured_clock"] = achieved / (n_sm * per_clk * clk["sm_mhz"] * 1e6)
 
