@@ -1248,13 +1248,9 @@ struct LearnSmem {
     int wg_ok[8];         // per warp: the last wait completed
     int tc_dead[2];       // per warpgroup: a wait gave up; no more MMAs
     uint32_t pending[2];  // the phase a dead warpgroup still waits for
-    // per pair of hidden units (c, c + 1), c = 2 P, in the order packed f32x2 operations take them
-    // (the constants of a pre-activation halved: the block forms v / 2, SiLU's argument):
-    float4 l1p[kHid / 2];  // {e_c, e_c+1 (this tile's cell), W1u[c][0], W1u[c+1][0]} / 2
-    float2 l1q[kHid / 2];  // {W1u[c][1], W1u[c+1][1]} / 2
-    float4 l2p[kHid / 2];  // {b2[c] / 2, b2[c+1] / 2, W3[0][c], W3[0][c+1]}
-    float2 l2q[kHid / 2];  // {W3[1][c], W3[1][c+1]}
-    float b3[2];
+    // the tile's cell embedding per pair of hidden units (c, c + 1), halved (the block
+    // forms v / 2, SiLU's argument); the shared constants come with the launch (NetConsts)
+    float2 ec2[kHid / 2];  // {e_c, e_c+1} / 2
     float coef[kCoefStride];
     float4 coef2[kPeMax];  // b_q as {Re, Re, Im, Im}: both rays of a pair at once
     float sc;
@@ -1340,7 +1336,7 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
         ls.coef2[tid] = make_float4(re, re, im, im);
     }
     if (tid < kHid)  // e_c / 2 (exact)
-        reinterpret_cast<float *>(&ls.l1p[tid >> 1])[tid & 1] = L.ec ? 0.5f * L.ec[(int64_t)rc * kHid + tid] : 0.0f;
+        reinterpret_cast<float *>(&ls.ec2[tid >> 1])[tid & 1] = L.ec ? 0.5f * L.ec[(int64_t)rc * kHid + tid] : 0.0f;
     __syncthreads();
 
     // ray offsets from the tile centre: the high parts here, the low parts (LO) formed
@@ -1467,11 +1463,11 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
                     uint32_t pk[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {  // units 8 k8 + 2 q and + 1
-                        const float4 pa = ls.l1p[4 * k8 + q];
-                        const float2 pb = ls.l1q[4 * k8 + q];
+                        const float2 e = ls.ec2[4 * k8 + q];
+                        const float4 w = L.net.w1u[4 * k8 + q];
                         // (e_c + W1u[.][0] ux + W1u[.][1] uy) / 2, then SiLU, for both units
-                        float2 v = __ffma2_rn(make_float2(pa.z, pa.w), uxx, make_float2(pa.x, pa.y));
-                        v = __ffma2_rn(pb, uyy, v);
+                        float2 v = __ffma2_rn(make_float2(w.x, w.y), uxx, e);
+                        v = __ffma2_rn(make_float2(w.z, w.w), uyy, v);
                         const float2 a = silu_half2(v);
                         pk[q] = pack_bf16(a.x, a.y);
                     }
@@ -1510,8 +1506,8 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
                         umma::ld16(dcol + lane_base + (uint32_t)c0, acc);
 #pragma unroll
                         for (int j = 0; j < 16; j += 2) {
-                            const float4 qa = ls.l2p[(c0 + j) >> 1];
-                            const float2 qb = ls.l2q[(c0 + j) >> 1];
+                            const float4 qa = L.net.l2p[(c0 + j) >> 1];
+                            const float2 qb = L.net.l2q[(c0 + j) >> 1];
                             const float2 a2 = silu_half2(__fadd2_rn(
                                 make_float2(__uint_as_float(acc[j]), __uint_as_float(acc[j + 1])), make_float2(qa.x, qa.y)));
                             y0p = __ffma2_rn(make_float2(qa.z, qa.w), a2, y0p);
@@ -1530,8 +1526,8 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
                 umma::fence_before();
                 umma::wg_sync(wg);  // accumulators read and A consumed before the next chunk
             }
-            Y[2 * r] = y0 + ls.b3[0];
-            Y[2 * r + 1] = y1 + ls.b3[1];
+            Y[2 * r] = y0 + L.net.b3[0];
+            Y[2 * r + 1] = y1 + L.net.b3[1];
         }
     }
     __syncthreads();
@@ -1665,15 +1661,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_shoot_learned(LearnedArgs L)
         for (int i = tid; i < kHid * kHid; i += kThreads)
             *reinterpret_cast<__nv_bfloat16 *>(ls.w2cm + umma::cm_offset(i / kHid, i % kHid)) =
                 __float2bfloat16_rn(0.5f * __bfloat162float(L.w2b[i]));  // W2 / 2 (exact)
-        if (tid < kHid) {
-            const int P = tid >> 1, h = tid & 1;
-            reinterpret_cast<float *>(&ls.l1p[P])[2 + h] = 0.5f * L.params[oW1u + 2 * tid];
-            reinterpret_cast<float *>(&ls.l1q[P])[h] = 0.5f * L.params[oW1u + 2 * tid + 1];
-            reinterpret_cast<float *>(&ls.l2p[P])[h] = 0.5f * L.params[ob2 + tid];
-            reinterpret_cast<float *>(&ls.l2p[P])[2 + h] = L.params[oW3 + tid];
-            reinterpret_cast<float *>(&ls.l2q[P])[h] = L.params[oW3 + kHid + tid];
-        }
-        if (tid < 2) ls.b3[tid] = L.params[ob3 + tid];
         if (tid < 2) ls.tc_dead[tid] = 0;
         if (tid == 0) {
             umma::mbar_init(&ls.mbar[0], 1);
@@ -1723,6 +1710,21 @@ static cudaError_t learned_attributes(K kernel)
         e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
     return e;
+}
+
+static_assert(kNetPairs * 2 == kHid, "NetConsts holds one entry per pair of hidden units");
+
+void ff_net_consts(const float *p, NetConsts *c)
+{
+    for (int P = 0; P < kNetPairs; ++P) {
+        const int u = 2 * P;
+        c->w1u[P] = make_float4(0.5f * p[oW1u + 2 * u], 0.5f * p[oW1u + 2 * (u + 1)], 0.5f * p[oW1u + 2 * u + 1],
+                                0.5f * p[oW1u + 2 * (u + 1) + 1]);
+        c->l2p[P] = make_float4(0.5f * p[ob2 + u], 0.5f * p[ob2 + u + 1], p[oW3 + u], p[oW3 + u + 1]);
+        c->l2q[P] = make_float2(p[oW3 + kHid + u], p[oW3 + kHid + u + 1]);
+    }
+    c->b3[0] = p[ob3];
+    c->b3[1] = p[ob3 + 1];
 }
 
 cudaError_t ff_learned_grid(int *grid)

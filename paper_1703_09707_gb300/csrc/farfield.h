@@ -39,6 +39,19 @@ struct CellGrid {
 
 __host__ __device__ inline int ext_index(const CellGrid &g, int cx, int cy) { return (cy + 1) * g.nx + (cx + 1); }
 
+// The network constants every learned tile shares, per pair of hidden units
+// (c, c + 1), c = 2 P, in the order the kernel's packed FP32 operations take them.
+// Passed by value with the launch, so the kernel reads them from its constant bank
+// instead of shared memory.  The constants of a pre-activation are halved (exact):
+// the kernel forms SiLU's argument v / 2 directly.
+constexpr int kNetPairs = 32;  // hidden units / 2
+struct NetConsts {
+    float4 w1u[kNetPairs];  // {W1u[c][0], W1u[c+1][0], W1u[c][1], W1u[c+1][1]} / 2
+    float4 l2p[kNetPairs];  // {b2[c] / 2, b2[c+1] / 2, W3[0][c], W3[0][c+1]}
+    float2 l2q[kNetPairs];  // {W3[1][c], W3[1][c+1]}
+    float b3[2];
+};
+
 // Everything the learned shooting kernel reads.
 struct LearnedArgs {
     ShootArgs plain;           // all stars, grids, counts, counters: used by fallback tiles and the epilogue
@@ -58,6 +71,7 @@ struct LearnedArgs {
     unsigned long long *counter;
     int *err;                  // set to 1 if a tensor-core completion wait gave up (results invalid)
     int wait_probe;            // test aid: each warpgroup's first wait polls an mbarrier nothing arrives on
+    NetConsts net;             // the network's shared constants (use_net)
 };
 
 // Sample generation for training / validation (counter-based, SplitMix64).
@@ -142,5 +156,7 @@ cudaError_t ff_flags(const unsigned *maxerr, int nrc, float tol, int *flags, cud
 // fallback tiles use the plain tile function with the context's fma_pairs setting
 cudaError_t ff_shoot_learned(const LearnedArgs &L, int grid, int fma_pairs, cudaStream_t s);
 cudaError_t ff_learned_grid(int *grid);
+// The learned kernel's NetConsts from the flat FP32 parameters (host copy).
+void ff_net_consts(const float *params_host, NetConsts *out);
 
 }  // namespace mlens

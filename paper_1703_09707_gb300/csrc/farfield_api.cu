@@ -47,6 +47,7 @@ struct FarState {
     unsigned long long *counter = nullptr;
     int *d_err = nullptr;  // learned kernel: a tensor-core wait gave up
     int grid = 0;
+    NetConsts net{};  // the network's shared constants, passed with each learned launch
     mlens_fit_report report{};
 };
 
@@ -258,6 +259,13 @@ int schedule(FarState *f, cudaStream_t s)
     f->report.val_max_err_net = f->use_net ? mx_n : -1.0;
     f->report.val_max_err_series = mx_s;
     FCUDA(ff_learned_grid(&f->grid), "occupancy");
+    {
+        std::vector<float> hp(mlp::kParams);
+        FCUDA(cudaMemcpyAsync(hp.data(), f->params, sizeof(float) * mlp::kParams, cudaMemcpyDeviceToHost, s),
+              "memcpy(network parameters)");
+        FCUDA(cudaStreamSynchronize(s), "sync");
+        ff_net_consts(hp.data(), &f->net);
+    }
     return MLENS_OK;
 }
 
@@ -512,6 +520,7 @@ int mlens_shoot_learned(mlens_ctx *ctx, const mlens_grid *rays, const mlens_grid
     L.counter = f->counter;
     L.err = f->d_err;
     L.wait_probe = g_wait_probe.load();
+    L.net = f->net;
     // Fallback tiles (each a full plain tile over all stars) run first, each split
     // over a cluster of CTAs so that a few flagged cells do not set the map's
     // time; the persistent learned kernel then takes the learned tiles.
