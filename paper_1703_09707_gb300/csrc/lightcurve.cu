@@ -254,6 +254,64 @@ __global__ void __launch_bounds__(kThr) k_disk(const int64_t *__restrict__ P, in
     }
 }
 
+// The same sums for disks of moderate size, with the prefix sums a tile needs staged
+// in shared memory once: a CTA takes kDiskTX x kDiskTY outputs and loads rows
+// j0 - H .. j0 + kDiskTY - 1 + H, columns i0 - W - 1 .. i0 + kDiskTX - 1 + W of P
+// (W: the largest half-width), with 0 above and below the map and left of it and
+// P[row][nx - 1] right of it -- exactly the values k_disk's clamps produce, so the
+// integer sums, and the outputs, are identical.  The 2 (2H + 1) loads per output
+// then come from shared memory instead of L2.  Thread (c, g) computes column c of
+// rows 8 g .. 8 g + 7 of the tile.
+constexpr int kDiskTX = 64, kDiskTY = 32;
+constexpr size_t kDiskTileMaxSmem = 100 * 1024;  // above this the plain kernel runs
+
+__host__ __device__ constexpr size_t disk_tile_smem(int H, int W)
+{
+    return (size_t)(kDiskTY + 2 * H) * (size_t)(kDiskTX + 2 * W + 1) * sizeof(int64_t) + (size_t)(2 * H + 1) * sizeof(int);
+}
+
+__global__ void __launch_bounds__(kThr) k_disk_tile(const int64_t *__restrict__ P, int nx, int ny,
+                                                    const int *__restrict__ half, int H, int W, double f,
+                                                    float *__restrict__ out)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    const int rows = kDiskTY + 2 * H, cols = kDiskTX + 2 * W + 1;
+    int64_t *T = reinterpret_cast<int64_t *>(dsm);
+    int *hs = reinterpret_cast<int *>(T + (size_t)rows * cols);
+    const int tid = threadIdx.x, c = tid % kDiskTX, g = tid / kDiskTX;
+    const int i0 = blockIdx.x * kDiskTX;
+    for (int k = tid; k <= 2 * H; k += kThr) hs[k] = min(half[k], W);  // half[k] <= W: a guard only
+    const int64_t tiles_y = ((int64_t)ny + kDiskTY - 1) / kDiskTY;
+    for (int64_t by = blockIdx.y; by < tiles_y; by += gridDim.y) {
+        const int64_t j0 = by * kDiskTY, jbase = j0 - H;
+        const int64_t cbase = (int64_t)i0 - W - 1;
+        __syncthreads();  // the previous tile's reads are done
+        for (int e = tid; e < rows * cols; e += kThr) {
+            const int r = e / cols, q = e % cols;
+            const int64_t jj = jbase + r, col = cbase + q;
+            T[e] = (jj >= 0 && jj < ny && col >= 0) ? P[jj * nx + (col < nx ? col : nx - 1)] : 0;
+        }
+        __syncthreads();
+        const int i = i0 + c;
+        if (i < nx) {
+#pragma unroll 1
+            for (int k = 0; k < kDiskTY / 4; ++k) {
+                const int rt = g * (kDiskTY / 4) + k;  // row within the tile
+                const int64_t j = j0 + rt;
+                if (j >= ny) break;
+                const int64_t *tr = T + (size_t)rt * cols + c + W;  // T row of j - H; tr[0] is column i - 1
+                int64_t sum = 0;
+                for (int d = 0; d <= 2 * H; ++d) {
+                    const int h = hs[d];
+                    sum += tr[h + 1] - tr[-h];
+                    tr += cols;
+                }
+                out[j * nx + i] = __double2float_rn(__dmul_rn((double)sum, f));
+            }
+        }
+    }
+}
+
 // Normalised 1-D Gaussian weights exp(-((k-K) d)^2 / (2 sigma^2)) / sum, one CTA:
 // FP64 terms, a fixed-order tree sum, float results.
 __global__ void __launch_bounds__(kThr) k_gauss_weights(double sigma, double d, int K, float *__restrict__ w)
@@ -377,6 +435,7 @@ namespace {
 struct ConvPlan {
     int Kx = 0, Ky = 0;    // Gaussian half-widths (pixels)
     int Hs = 0;            // disk: support rows |dj| <= Hs
+    int Ws = 0;            // disk: the largest half-width, capped at nx
     int64_t count = 0;     // disk: |K|
     size_t off_map = 0;    // workspace offset of the map-sized buffer
     size_t bytes = 0;      // workspace size
@@ -413,6 +472,7 @@ int plan_convolution(const mlens_grid *src, int32_t profile, double size, ConvPl
             if (h >= 0) {
                 count += 2 * (int64_t)h + 1;
                 Hs = std::max(Hs, std::abs(dj));
+                pl->Ws = std::max(pl->Ws, std::min(h, nx));
             }
         }
         pl->Hs = Hs;
@@ -462,9 +522,19 @@ int run_convolution(const uint32_t *counts_dev, const mlens_grid *src, int32_t p
     k_disk_halves<<<(unsigned)((2 * pl.Hs + 1 + kThr - 1) / kThr), kThr, 0, s>>>(size, dx, dy, pl.Hs, nx, half);
     const unsigned gp = (unsigned)std::min<int64_t>(ny, (int64_t)nsm * 8);
     k_row_prefix<<<gp, kThr, 0, s>>>(counts_dev, nx, ny, P);
-    const dim3 gd((unsigned)((nx + kThr - 1) / kThr), (unsigned)std::min<int64_t>(ny, 65535));
-    k_disk<<<gd, kThr, (size_t)(2 * pl.Hs + 1) * sizeof(int), s>>>(P, nx, ny, half, pl.Hs,
-                                                                    scale / (double)pl.count, out_dev);
+    const size_t tsm = disk_tile_smem(pl.Hs, pl.Ws);
+    if (tsm <= kDiskTileMaxSmem) {
+        if ((e = cudaFuncSetAttribute(k_disk_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm)) !=
+            cudaSuccess)
+            return lc_cuda(e, "cudaFuncSetAttribute");
+        const dim3 gt((unsigned)((nx + kDiskTX - 1) / kDiskTX),
+                      (unsigned)std::min<int64_t>(((int64_t)ny + kDiskTY - 1) / kDiskTY, 65535));
+        k_disk_tile<<<gt, kThr, tsm, s>>>(P, nx, ny, half, pl.Hs, pl.Ws, scale / (double)pl.count, out_dev);
+    } else {
+        const dim3 gd((unsigned)((nx + kThr - 1) / kThr), (unsigned)std::min<int64_t>(ny, 65535));
+        k_disk<<<gd, kThr, (size_t)(2 * pl.Hs + 1) * sizeof(int), s>>>(P, nx, ny, half, pl.Hs,
+                                                                        scale / (double)pl.count, out_dev);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return lc_cuda(e, "disk launches");
     return MLENS_OK;
 }
