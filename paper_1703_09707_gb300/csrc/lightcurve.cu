@@ -184,25 +184,37 @@ __global__ void __launch_bounds__(kThr) k_gauss_cols(const float *__restrict__ i
 }
 
 // Inclusive prefix sums of each row (int64): one CTA per row, 8 elements per thread
-// per chunk, warp shuffles then one shared-memory step across the 8 warps.
+// per chunk, warp shuffles then one shared-memory step across the 8 warps.  A
+// chunk's counts are read, and its sums written, through shared memory so that
+// the global accesses are coalesced (a thread's own 8 elements are consecutive).
 __global__ void __launch_bounds__(kThr) k_row_prefix(const uint32_t *__restrict__ in, int nx, int ny,
                                                      int64_t *__restrict__ P)
 {
+    constexpr int kPer = 8, kChunk = kThr * kPer;
     __shared__ int64_t wsum[kThr / 32];
     __shared__ int64_t carry_s;
+    __shared__ __align__(16) uint32_t cin[kChunk];
+    __shared__ __align__(16) int64_t cout[kChunk + kChunk / kPer];  // element e at e + e / 8: no bank conflicts
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int kPer = 8;
     for (int64_t j = blockIdx.x; j < ny; j += gridDim.x) {
         const uint32_t *row = in + j * nx;
         int64_t *prow = P + j * nx;
         int64_t carry = 0;
-        for (int64_t base = 0; base < nx; base += (int64_t)kThr * kPer) {
+        for (int64_t base = 0; base < nx; base += kChunk) {
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) {
+                const int64_t i = base + k * kThr + tid;
+                cin[k * kThr + tid] = i < nx ? row[i] : 0u;
+            }
+            __syncthreads();
+            const uint4 c0 = reinterpret_cast<const uint4 *>(cin)[2 * tid];
+            const uint4 c1 = reinterpret_cast<const uint4 *>(cin)[2 * tid + 1];
+            const uint32_t cv[kPer] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
             int64_t v[kPer];
             int64_t run = 0;
 #pragma unroll
             for (int k = 0; k < kPer; ++k) {
-                const int64_t i = base + (int64_t)tid * kPer + k;
-                run += (i < nx) ? (int64_t)row[i] : 0;
+                run += (int64_t)cv[k];  // zero past the row's end
                 v[k] = run;
             }
             int64_t x = run;  // inclusive scan of the thread totals across the warp
@@ -217,14 +229,17 @@ __global__ void __launch_bounds__(kThr) k_row_prefix(const uint32_t *__restrict_
             for (int q = 0; q < warp; ++q) before += wsum[q];
             const int64_t off = carry + before + (x - run);
 #pragma unroll
-            for (int k = 0; k < kPer; ++k) {
-                const int64_t i = base + (int64_t)tid * kPer + k;
-                if (i < nx) prow[i] = off + v[k];
-            }
+            for (int k = 0; k < kPer; ++k) cout[tid * (kPer + 1) + k] = off + v[k];
             if (tid == kThr - 1) carry_s = off + run;
             __syncthreads();
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) {
+                const int64_t i = base + k * kThr + tid;
+                const int e = k * kThr + tid;
+                if (i < nx) prow[i] = cout[e + e / kPer];
+            }
             carry = carry_s;
-            __syncthreads();  // wsum and carry_s are reused by the next chunk
+            __syncthreads();  // wsum, carry_s, cin and cout are reused by the next chunk
         }
     }
 }
@@ -263,6 +278,16 @@ __global__ void __launch_bounds__(kThr) k_disk(const int64_t *__restrict__ P, in
 // then come from shared memory instead of L2.  Thread (c, g) computes column c of
 // rows 8 g .. 8 g + 7 of the tile.
 constexpr int kDiskTX = 64, kDiskTY = 32;
+
+// 8-byte asynchronous global -> shared copy (Ampere-style cp.async: no register round
+// trip, so all of a thread's copies are in flight at once); n = 0 writes zeros and
+// reads nothing.
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, int n)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 constexpr size_t kDiskTileMaxSmem = 100 * 1024;  // above this the plain kernel runs
 
 __host__ __device__ constexpr size_t disk_tile_smem(int H, int W)
@@ -286,27 +311,50 @@ __global__ void __launch_bounds__(kThr) k_disk_tile(const int64_t *__restrict__ 
         const int64_t j0 = by * kDiskTY, jbase = j0 - H;
         const int64_t cbase = (int64_t)i0 - W - 1;
         __syncthreads();  // the previous tile's reads are done
-        for (int e = tid; e < rows * cols; e += kThr) {
-            const int r = e / cols, q = e % cols;
-            const int64_t jj = jbase + r, col = cbase + q;
-            T[e] = (jj >= 0 && jj < ny && col >= 0) ? P[jj * nx + (col < nx ? col : nx - 1)] : 0;
+        for (int r = tid / 32; r < rows; r += kThr / 32) {  // a warp per row, its lanes along it
+            const int64_t jj = jbase + r;
+            const bool in = jj >= 0 && jj < ny;
+            for (int q = tid % 32; q < cols; q += 32) {
+                const int64_t col = cbase + q;
+                const bool ok = in && col >= 0;
+                cp_async8(&T[r * cols + q], ok ? P + jj * nx + (col < nx ? col : nx - 1) : P, ok ? 8 : 0);
+            }
         }
+        cp_async_wait_all();
         __syncthreads();
         const int i = i0 + c;
         if (i < nx) {
-#pragma unroll 1
-            for (int k = 0; k < kDiskTY / 4; ++k) {
-                const int rt = g * (kDiskTY / 4) + k;  // row within the tile
-                const int64_t j = j0 + rt;
-                if (j >= ny) break;
-                const int64_t *tr = T + (size_t)rt * cols + c + W;  // T row of j - H; tr[0] is column i - 1
-                int64_t sum = 0;
-                for (int d = 0; d <= 2 * H; ++d) {
-                    const int h = hs[d];
-                    sum += tr[h + 1] - tr[-h];
-                    tr += cols;
+            constexpr int kRows = kDiskTY / 4;  // output rows per thread
+            const int rt0 = g * kRows;          // the thread's first row within the tile
+            int64_t sum[kRows];
+#pragma unroll
+            for (int k = 0; k < kRows; ++k) sum[k] = 0;
+            // T row rt0 + d is row j0 + rt0 - H + d of the map; tr[0] is the column of i - 1.
+            // rs[k]: the run sum of output k at support row d.  Where the next support row
+            // has the same half-width (a warp-uniform test), output k's next run is output
+            // k + 1's current one, so the runs shift by one and only the last is loaded.
+            const int64_t *tr = T + (size_t)rt0 * cols + c + W;
+            int64_t rs[kRows];
+            int hprev = -1;
+            for (int d = 0; d <= 2 * H; ++d) {  // one half-width per support row, for all kRows outputs
+                const int h = hs[d];
+                if (h == hprev) {
+#pragma unroll
+                    for (int k = 0; k < kRows - 1; ++k) rs[k] = rs[k + 1];
+                    rs[kRows - 1] = tr[(kRows - 1) * cols + h + 1] - tr[(kRows - 1) * cols - h];
+                } else {
+#pragma unroll
+                    for (int k = 0; k < kRows; ++k) rs[k] = tr[k * cols + h + 1] - tr[k * cols - h];
                 }
-                out[j * nx + i] = __double2float_rn(__dmul_rn((double)sum, f));
+#pragma unroll
+                for (int k = 0; k < kRows; ++k) sum[k] += rs[k];
+                hprev = h;
+                tr += cols;
+            }
+#pragma unroll
+            for (int k = 0; k < kRows; ++k) {
+                const int64_t j = j0 + rt0 + k;
+                if (j < ny) out[j * nx + i] = __double2float_rn(__dmul_rn((double)sum[k], f));
             }
         }
     }
