@@ -292,7 +292,8 @@ constexpr size_t kDiskTileMaxSmem = 100 * 1024;  // above this the plain kernel 
 
 __host__ __device__ constexpr size_t disk_tile_smem(int H, int W)
 {
-    return (size_t)(kDiskTY + 2 * H) * (size_t)(kDiskTX + 2 * W + 1) * sizeof(int64_t) + (size_t)(2 * H + 1) * sizeof(int);
+    return ((size_t)kDiskTY + 2 * (size_t)H) * ((size_t)kDiskTX + 2 * (size_t)W + 1) * sizeof(int64_t) +
+           (2 * (size_t)H + 1) * sizeof(int);  // size_t throughout: W can be as large as nx
 }
 
 __global__ void __launch_bounds__(kThr) k_disk_tile(const int64_t *__restrict__ P, int nx, int ny,
