@@ -1713,6 +1713,7 @@ static cudaError_t learned_attributes(K kernel)
 }
 
 static_assert(kNetPairs * 2 == kHid, "NetConsts holds one entry per pair of hidden units");
+static_assert(sizeof(LearnedArgs) <= 4096, "the learned kernel's parameters (NetConsts included) stay within 4 KB");
 
 void ff_net_consts(const float *p, NetConsts *c)
 {
