@@ -1280,7 +1280,8 @@ template <bool NET>
 constexpr int kNearChunk = NET ? 4 : 2;
 constexpr int kTcChunk = 128;                            // rays per tensor-core MMA (M)
 constexpr int kTcABytes = kTcChunk * kHid * 2;           // one warpgroup's A operand (16 KB)
-constexpr int kTcSmem = 2 * kTcABytes;                   // dynamic shared memory of the learned kernel
+constexpr int kTcSmem = 2 * kTcABytes;                   // the two A operands
+constexpr size_t kLearnedDynSmem = kTcSmem > sizeof(ShootSmem<256>) ? kTcSmem : sizeof(ShootSmem<256>);
 
 // LO: the ray offsets carry low parts (grids whose offsets are not exact floats,
 // RayGrid lo); a separate instance so that the exact-offset tiles keep their
@@ -1435,7 +1436,8 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
     __syncthreads();  // star stages dead; the region now holds the network outputs
 
     // ---- network residual for the tile's 2048 rays (warp w: rays 256w .. 256w+255)
-    float *Y = reinterpret_cast<float *>(sm.hist);
+    // the network's outputs (+ b3) for this thread's own rays, ray k at yv[2 k], yv[2 k + 1]
+    float yv[4 * NP];
     const int ioff = (bx % cg.ktx) * kTileX, joff = (by % cg.kty) * kTileY;
     const float inv_cx = 1.0f / (float)(kTileX * cg.ktx), inv_cy = 1.0f / (float)(kTileY * cg.kty);
     if (NET) {
@@ -1451,12 +1453,13 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
         const uint32_t dcol = ls.tmem + (uint32_t)(wg * kHid);
         const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
         constexpr uint32_t idesc = umma::idesc_bf16(kTcChunk, kHid);
-        for (int ch = wg; ch < 2048 / kTcChunk; ch += 2) {
-            const int r = ch * kTcChunk + t;  // ray of the tile (row-major 64 x 32)
+#pragma unroll 1
+        for (int k = 0; k < 2 * NP; ++k) {  // chunk k: ray k of each thread of the warpgroup
+            const int row = tg * 2 * NP + k;  // the ray's row in the tile (its column is tx)
             float y0 = 0.0f, y1 = 0.0f;
             if (!ls.tc_dead[wg]) {
-                const float ux = (float)(2 * (ioff + (r & 63)) + 1) * inv_cx - 1.0f;
-                const float uy = (float)(2 * (joff + (r >> 6)) + 1) * inv_cy - 1.0f;
+                const float ux = (float)(2 * (ioff + tx) + 1) * inv_cx - 1.0f;
+                const float uy = (float)(2 * (joff + row) + 1) * inv_cy - 1.0f;
                 const float2 uxx = make_float2(ux, ux), uyy = make_float2(uy, uy);
 #pragma unroll
                 for (int k8 = 0; k8 < kHid / 8; ++k8) {
@@ -1526,11 +1529,10 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
                 umma::fence_before();
                 umma::wg_sync(wg);  // accumulators read and A consumed before the next chunk
             }
-            Y[2 * r] = y0 + L.net.b3[0];
-            Y[2 * r + 1] = y1 + L.net.b3[1];
+            yv[2 * k] = y0 + L.net.b3[0];
+            yv[2 * k + 1] = y1 + L.net.b3[1];
         }
     }
-    __syncthreads();
 
     // ---- far field and beta per ray, the two rays of each pair (rows 2p and 2p + 1 of
     // column tx) in the two lanes of f32x2 registers: the same operations per ray as a
@@ -1562,9 +1564,8 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
             // imaginary parts for the two rays
             float2 ar = make_float2(0.f, 0.f), ai = make_float2(0.f, 0.f);
             if (L.use_net) {
-                const int ray0 = jl * kTileX + tx, ray1 = ray0 + kTileX;
-                ar = make_float2(ls.sc * Y[2 * ray0], ls.sc * Y[2 * ray1]);
-                ai = make_float2(ls.sc * Y[2 * ray0 + 1], ls.sc * Y[2 * ray1 + 1]);
+                ar = make_float2(ls.sc * yv[4 * p], ls.sc * yv[4 * p + 2]);
+                ai = make_float2(ls.sc * yv[4 * p + 1], ls.sc * yv[4 * p + 3]);
             }
             auto cmul2 = [&]() {  // (ar + i ai) (vx + i vy)
                 const float2 t = __fmul2_rn(ar, vx), u = __fmul2_rn(ar, vy);
@@ -1648,13 +1649,16 @@ template <int NRP, bool NET, bool LO>
 // scheduler hide the latency of the 128 hardware tanh per ray better than four
 // (0.056 s against 0.060 s per 32768^2-ray map at two CTAs per SM and 128 registers
 // when first measured; 0.051 s against 0.056 s with the packed network block).
-__global__ void __launch_bounds__(kThreads, 3) k_shoot_learned(LearnedArgs L)
+__global__ void __launch_bounds__(kThreads, 4) k_shoot_learned(LearnedArgs L)
 {
-    __shared__ __align__(16) ShootSmem<256> sm;
     __shared__ TileShared ts;
     __shared__ __align__(128) LearnSmem ls;
     __shared__ long long s_item;
-    extern __shared__ __align__(128) unsigned char tc_abuf[];  // two A operands, kTcSmem bytes
+    // dynamic: the star stage and window of the tile phases without tensor-core work,
+    // and (NET) the two A operands of the network phase in the same bytes
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    ShootSmem<256> &sm = *reinterpret_cast<ShootSmem<256> *>(dyn_smem);
+    unsigned char *tc_abuf = dyn_smem;
     const int tid = threadIdx.x;
     uint32_t phase = 0;  // completed MMA batches of this thread's warpgroup, mod 2
     if (NET) {
@@ -1705,7 +1709,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_shoot_learned(LearnedArgs L)
 template <class K>
 static cudaError_t learned_attributes(K kernel)
 {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLearnedDynSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
@@ -1736,9 +1740,11 @@ cudaError_t ff_learned_grid(int *grid)
     // by registers, 3 by shared memory), though the occupancy query reports one
     // for it; CTAs beyond those resident only find the shared work queue empty.
     int per_sm = 0, per_sm1 = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shoot_learned<0, false, false>, kThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shoot_learned<0, false, false>, kThreads,
+                                                                  sizeof(ShootSmem<256>));
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, k_shoot_learned<1, false, false>, kThreads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, k_shoot_learned<1, false, false>, kThreads,
+                                                      sizeof(ShootSmem<256>));
     if (e != cudaSuccess) return e;
     per_sm = per_sm < per_sm1 ? per_sm : per_sm1;
     int dev = 0, nsm = 0;
@@ -1754,9 +1760,9 @@ static cudaError_t launch_learned_t(const LearnedArgs &L, unsigned g, cudaStream
     if (L.use_net) {
         cudaError_t e = learned_attributes(k_shoot_learned<NRP, true, LO>);
         if (e != cudaSuccess) return e;
-        k_shoot_learned<NRP, true, LO><<<g, kThreads, kTcSmem, s>>>(L);
+        k_shoot_learned<NRP, true, LO><<<g, kThreads, kLearnedDynSmem, s>>>(L);
     } else {
-        k_shoot_learned<NRP, false, LO><<<g, kThreads, 0, s>>>(L);
+        k_shoot_learned<NRP, false, LO><<<g, kThreads, sizeof(ShootSmem<256>), s>>>(L);
     }
     return cudaGetLastError();
 }
