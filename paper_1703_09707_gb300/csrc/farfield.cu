@@ -1641,14 +1641,15 @@ __device__ __forceinline__ void learned_tile(const LearnedArgs &L, int bx, int b
     stats_add_block(nb, no, nn, ts.sred, a.stats);
 }
 
-// NET: the network on the tensor cores (tcgen05; tensor memory and kTcSmem bytes
-// of dynamic shared memory); without it (the series alone) the kernel carries no
-// tensor-core code and no dynamic shared memory.
+// NET: the network on the tensor cores (tcgen05; 128 tensor-memory columns and the
+// two A operands in dynamic shared memory, in the same bytes as the star stage and
+// window); without it (the series alone) the kernel carries no tensor-core code.
 template <int NRP, bool NET, bool LO>
-// Three CTAs per SM (80 registers, ~100 bytes of spills per thread): six warps per
-// scheduler hide the latency of the 128 hardware tanh per ray better than four
-// (0.056 s against 0.060 s per 32768^2-ray map at two CTAs per SM and 128 registers
-// when first measured; 0.051 s against 0.056 s with the packed network block).
+// Four CTAs per SM (64 registers, ~280 bytes of spills per thread; tensor memory
+// holds four CTAs' 128 columns): eight warps per scheduler hide the latency of the
+// 128 hardware tanh per ray.  Measured per 32768^2-ray map: two CTAs per SM 0.060 s,
+// three 0.056 s (when first measured); three 44.8 ms, four 44.0 ms with the current
+// network block, and 13.2 -> 11.8 ms for the order-16 series alone.
 __global__ void __launch_bounds__(kThreads, 4) k_shoot_learned(LearnedArgs L)
 {
     __shared__ TileShared ts;
@@ -1735,10 +1736,10 @@ void ff_net_consts(const float *p, NetConsts *c)
 cudaError_t ff_learned_grid(int *grid)
 {
     // The persistent grid takes the resident CTAs per SM of the kernel without
-    // tensor-core code (three: launch-bounded to 80 registers per thread).  The
-    // tensor-core variant has the same register and shared-memory limits (ncu: 3
-    // by registers, 3 by shared memory), though the occupancy query reports one
-    // for it; CTAs beyond those resident only find the shared work queue empty.
+    // tensor-core code (four: launch-bounded to 64 registers per thread).  The
+    // tensor-core variant has the same register limit and fits four CTAs in shared
+    // and tensor memory, though the occupancy query has reported fewer for it; CTAs
+    // beyond those resident only find the shared work queue empty.
     int per_sm = 0, per_sm1 = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shoot_learned<0, false, false>, kThreads,
                                                                   sizeof(ShootSmem<256>));
